@@ -1,0 +1,49 @@
+"""FP64 CPU oracle -- certificates used to pin the solver's output.
+
+TEST INFRASTRUCTURE ONLY (imported by ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py``).
+
+  * lambda_min(C - A^T y): the dual-infeasibility measure of Appendix B (its "sigma_min"
+    of a symmetric matrix read as the smallest eigenvalue); dense LAPACK for small n,
+    ARPACK Lanczos otherwise.
+  * exhaustive max cut for n <= 20 (the Goemans-Williamson sandwich
+    0.878 SDP <= maxcut <= SDP needs nonnegative weights).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .sdp import SDP
+
+
+def min_eig_dual_slack(sdp: SDP, y, dense_limit: int = 2500) -> float:
+    S = sdp.dual_slack(y)
+    if sdp.n <= dense_limit:
+        Sd = S.toarray() if sp.issparse(S) else np.asarray(S)
+        return float(np.linalg.eigvalsh(0.5 * (Sd + Sd.T))[0])
+    vals = spla.eigsh(S, k=1, which="SA", tol=1e-10, maxiter=20000, return_eigenvectors=False)
+    return float(vals[0])
+
+
+def exhaustive_maxcut(n: int, edges, w) -> float:
+    """max over x in {-1,1}^n of sum_{(i,j)} w_ij (1 - x_i x_j)/2, with x_0 fixed."""
+    if n > 22:
+        raise ValueError("exhaustive max cut is for tiny graphs only")
+    edges = np.asarray(edges, dtype=np.int64)
+    w = np.asarray(w, dtype=np.float64)
+    best = -np.inf
+    # enumerate the 2^(n-1) cuts with vertex 0 on side +1, in chunks
+    free = n - 1
+    chunk_bits = min(free, 16)
+    low = np.arange(1 << chunk_bits, dtype=np.int64)
+    for hi in range(1 << (free - chunk_bits)):
+        codes = (hi << chunk_bits) | low
+        bits = (codes[:, None] >> np.arange(free)[None, :]) & 1
+        x = np.concatenate([np.ones((len(codes), 1)), 1.0 - 2.0 * bits], axis=1)
+        cut = ((1.0 - x[:, edges[:, 0]] * x[:, edges[:, 1]]) * 0.5) @ w
+        best = max(best, float(cut.max()))
+    return best

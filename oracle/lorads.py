@@ -1,0 +1,510 @@
+"""FP64 CPU oracle -- LoRADS (Algorithm 2) with LRALM (Phase I) and LRADMM + CG (Phase II).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this module; the CUDA library never calls it.
+
+The method is an iteration, so this file restates its steps in the paper's order and
+notation, one function per step, with no fusion or reordering:
+
+  * Phase I (Section 4.1): the augmented Lagrangian method on the Burer-Monteiro problem
+    (eq. prob:BM), each subproblem by L-BFGS with an exact line search, plus the dynamic
+    rank rule of Section 4.3.
+  * Switch (Algorithm 2): U = V = U_BM, lambda = the Phase I multiplier, rho <- h * rho
+    (Section 5.1, "The heuristic factor").
+  * Phase II (Algorithm 1): U-step and V-step are the linear systems eq. linU / eq. linV,
+    each solved by unpreconditioned CG warm-started from the other factor (Section 4.4);
+    then lambda += rho (A(U V^T) - b); rho *= 1.2 every 5 iterations up to 5000
+    (Section 5.1, "The control of penalty factor").
+  * Output: U_hat = (U + V)/2, X = U_hat U_hat^T, y = -lambda.
+
+Readings of points the paper leaves open are parameters of ``Params`` (their defaults
+are the readings the CUDA library uses as well):
+  * gamma is never given a value; gamma = ||C||_inf (largest absolute row sum of C);
+  * the multiplier enters eq. ALF with a plus sign, so the SDP dual is y = -lambda;
+  * with phi's multiplier normalised as in eq. ALF, the switch takes lambda_0 = lambda_hat
+    (the paper's 1/2 factor belongs to the normalisation of eq. def:eKKT);
+  * CG stops at ||R|| <= max(1e-3 ||R_0||, 1e-13 ||G||), R_0 the residual of the warm
+    start, at most cg_max_iter steps;
+  * the CG for the V-step starts from U^{k+1};
+  * Phase II stops on eq. stop (primal infeasibility of U V^T and gamma ||dV||) with the
+    output U_hat U_hat^T also primal feasible to tol; dual stationarity, the duality gap
+    and lambda_min(C - A^T y) are reported, not tested;
+  * Phase I: sigma_0 = 1/(1+||b||_inf), sigma *= 2 when r_P fails to fall 4x in an outer
+    step, L-BFGS memory 4, inner stop at ||grad||_F/(1+||C||_F) <= min(0.1, 10 r_P), rank growth
+    when an inner solve needs more than 300 iterations (switch test first).
+
+Random draws (the initial factor and the columns added by rank growth) come from a
+counter-based SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014) followed by the
+Box-Muller transform (Box and Muller, 1958); the CUDA library implements the same
+generator independently.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field, asdict
+from typing import Callable, List, Optional
+
+import numpy as np
+
+from .sdp import SDP
+
+
+# ======================================================================================
+# parameters
+# ======================================================================================
+@dataclass
+class Params:
+    r0: int = 0                   # 0 -> rule below
+    rank_rule: str = "log2"       # "log2": ceil(log2 m); "paper": round(2 ln m) (Table 2)
+    rank_max: int = 0             # 0 -> min(floor(sqrt(2 m)), n, 256)
+    rank_factor: float = 1.5      # Section 4.3 / 5.1
+    tol: float = 1e-6             # final tolerance
+    switch_tol: float = 1e-2      # Section 5.1: 1e-2 for MaxCut, 1e-3 otherwise
+    h: float = 10.0               # Section 5.1: heuristic factor (10 for MaxCut)
+    rho_max: float = 5000.0       # Section 5.1
+    rho_growth: float = 1.2       # Section 5.1
+    rho_every: int = 5            # Section 5.1
+    gamma_scale: float = 1.0      # gamma = gamma_scale * ||C||_inf (paper silent) ...
+    gamma_fixed: float = 0.0      # ... unless gamma_fixed > 0
+    max_admm_iter: int = 5000     # Section 5.2
+    cg_max_iter: int = 1000
+    cg_rel_tol: float = 1e-3      # ||R|| <= cg_rel_tol ||R_0|| (R_0: warm-start residual)
+    cg_abs_floor: float = 1e-13   # ... or ||R|| <= cg_abs_floor ||G||
+    lbfgs_mem: int = 4
+    inner_max_iter: int = 300     # K_in: rank-growth trigger
+    inner_tol_factor: float = 10.0
+    inner_tol_max: float = 0.1
+    inner_tol_abs: float = 1e-12
+    max_outer: int = 500
+    sigma_factor: float = 2.0
+    sigma_decrease: float = 0.25
+    new_col_std: float = 1e-2
+    seed: int = 1
+    phase1: bool = True           # False: caller supplies U0 / lambda0 / rho0
+
+
+# ======================================================================================
+# counter-based random numbers: SplitMix64 + Box-Muller
+# ======================================================================================
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64_mix(z):
+    """The SplitMix64 output function applied to uint64 state(s) z."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def splitmix64_at(key, i):
+    """i-th output (i = 0, 1, ...) of the SplitMix64 stream seeded with ``key``."""
+    i = np.asarray(i, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return splitmix64_mix(np.uint64(key) + (i + np.uint64(1)) * _GAMMA)
+
+
+def stream_key(seed: int, stream: int) -> np.uint64:
+    """Key of sub-stream ``stream``: stream 0 draws U_0, stream g draws the g-th rank growth."""
+    return np.uint64(splitmix64_at(np.uint64(seed), np.uint64(stream)))
+
+
+def uniform_open01(key, i):
+    """Uniform in (0, 1) from the top 53 bits of output i."""
+    x = splitmix64_at(key, i)
+    return ((x >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
+
+
+def normal_matrix(key, rows: int, cols: int) -> np.ndarray:
+    """rows x cols standard normals; entry e = j*cols + c uses outputs 2e and 2e+1."""
+    e = np.arange(rows * cols, dtype=np.uint64)
+    u1 = uniform_open01(key, 2 * e)
+    u2 = uniform_open01(key, 2 * e + np.uint64(1))
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return z.reshape(rows, cols)
+
+
+# ======================================================================================
+# rank rules (Sections 4.3 and 5.1)
+# ======================================================================================
+def initial_rank(m: int, n: int, p: Params) -> int:
+    if p.r0 > 0:
+        r = p.r0
+    elif p.rank_rule == "paper":
+        r = int(round(2.0 * math.log(m)))          # Table 2, "2 log(m)" column
+    else:
+        r = int(math.ceil(math.log2(max(m, 2))))
+    return max(1, min(r, n, rank_cap(m, n, p)))
+
+
+def rank_cap(m: int, n: int, p: Params) -> int:
+    if p.rank_max > 0:
+        return min(p.rank_max, n)
+    return max(1, min(int(math.floor(math.sqrt(2.0 * m))), n, 256))
+
+
+def next_rank(r: int, cap: int, p: Params) -> int:
+    """Dynamic rank rule: multiply by the factor (1.5), round up, cap."""
+    return min(int(math.ceil(p.rank_factor * r - 1e-9)), cap)
+
+
+def paper_rank_sequence(m: int, steps: int, factor: float = 1.5) -> List[int]:
+    """Table 2's ranks: round(2 ln m) at start, then floor(2 ln m * factor^k), capped at
+    round(sqrt(2 m)) (the table's sqrt(2m) column)."""
+    cap = int(round(math.sqrt(2.0 * m)))
+    out = [int(round(2.0 * math.log(m)))]
+    for k in range(1, steps + 1):
+        out.append(min(int(math.floor(2.0 * math.log(m) * factor ** k)), cap))
+    return out
+
+
+# ======================================================================================
+# residual measures
+# ======================================================================================
+def primal_infeasibility(sdp: SDP, U, V) -> float:
+    """||A(U V^T) - b||_2 / (1 + ||b||_inf)  (Section 5.2)."""
+    return float(np.linalg.norm(sdp.A_of(U, V) - sdp.b) / (1.0 + sdp.b_inf))
+
+
+def dual_stationarity(sdp: SDP, Uh, lam) -> float:
+    """||(C + A^T(lambda)) U_hat||_F / (1 + ||C||_F): first line of eq. def:eKKT with
+    f = <C, .> and multiplier 2 lambda (Theorem 1), i.e. y = -lambda."""
+    S_U = sdp.C_times(Uh) + sdp.At_times(lam, Uh)
+    return float(np.linalg.norm(S_U) / (1.0 + sdp.C_fro))
+
+
+def augmented_lagrangian(sdp: SDP, U, V, lam, rho, gamma) -> float:
+    """L_rho(U, V, lambda) of eq. ALF with f(U V^T) = <C, U V^T>."""
+    e = sdp.A_of(U, V) - sdp.b
+    return (sdp.C_inner(U, V) + 0.5 * gamma * float(np.sum((U - V) ** 2))
+            + float(lam @ e) + 0.5 * rho * float(e @ e))
+
+
+# ======================================================================================
+# Phase II pieces: the linear systems eq. linU / eq. linV and CG (Section 4.4)
+# ======================================================================================
+def hessian_apply(sdp: SDP, W, P, rho, gamma):
+    """(rho sum_i vec(A_i W) vec(A_i W)^T + gamma I) vec(P), W the fixed factor.
+
+    <vec(A_i W), vec(P)> = <A_i, P W^T>, so this is rho A^T(A(P W^T)) W + gamma P.
+    """
+    q = sdp.A_of(P, W)
+    return rho * sdp.At_times(q, W) + gamma * P
+
+
+def subproblem_rhs(sdp: SDP, W, lam, rho, gamma):
+    """Right-hand side of eq. linU (W = V^k) / eq. linV (W = U^{k+1}):
+    -(C W - gamma W + A^T(lambda) W - rho A^T(b) W) = (A^T(rho b - lambda) - C) W + gamma W."""
+    return sdp.At_times(rho * sdp.b - lam, W) - sdp.C_times(W) + gamma * W
+
+
+def conjugate_gradient(apply_H: Callable, G, X0, rel_tol: float, abs_floor: float,
+                       max_iter: int):
+    """Textbook unpreconditioned CG on H X = G from the warm start X0.
+
+    Stops at ||R|| <= max(rel_tol ||R_0||, abs_floor ||G||), R_0 = G - H X0."""
+    X = X0.copy()
+    R = G - apply_H(X)
+    P = R.copy()
+    rr = float(np.vdot(R, R))
+    target = max(rel_tol * math.sqrt(rr), abs_floor * float(np.linalg.norm(G)))
+    it = 0
+    while math.sqrt(rr) > target and it < max_iter:
+        HP = apply_H(P)
+        alpha = rr / float(np.vdot(P, HP))
+        X = X + alpha * P
+        R = R - alpha * HP
+        rr_new = float(np.vdot(R, R))
+        it += 1
+        if math.sqrt(rr_new) <= target:
+            rr = rr_new
+            break
+        P = R + (rr_new / rr) * P
+        rr = rr_new
+    return X, it
+
+
+def penalty_gamma(sdp: SDP, p: Params) -> float:
+    """gamma of eq. prob:penalty.  The paper fixes no value; the U-step moves U along
+    -(C + A^T lambda) V / gamma, so gamma is tied to the scale of C through the row-sum
+    norm ||C||_inf = max_j sum_k |C_jk| (an upper bound on ||C||_2)."""
+    if p.gamma_fixed > 0:
+        return p.gamma_fixed
+    cinf = sdp.C_rowsum_max
+    return p.gamma_scale * (cinf if cinf > 0 else 1.0)
+
+
+@dataclass
+class AdmmState:
+    U: np.ndarray
+    V: np.ndarray
+    lam: np.ndarray
+    rho: float
+    k: int = 0
+    cg_iters: int = 0
+    rp: float = math.inf
+
+
+def admm_iteration(sdp: SDP, st: AdmmState, p: Params) -> dict:
+    """One pass of Algorithm 1 (U-step, V-step, dual step) plus the penalty schedule."""
+    rho = st.rho
+    gamma = penalty_gamma(sdp, p)
+    # U-step: eq. linU, CG warm-started from V^k
+    V = st.V
+    G = subproblem_rhs(sdp, V, st.lam, rho, gamma)
+    U, itU = conjugate_gradient(lambda X: hessian_apply(sdp, V, X, rho, gamma), G, V,
+                                p.cg_rel_tol, p.cg_abs_floor, p.cg_max_iter)
+    # V-step: eq. linV, CG warm-started from U^{k+1}
+    G = subproblem_rhs(sdp, U, st.lam, rho, gamma)
+    V, itV = conjugate_gradient(lambda X: hessian_apply(sdp, U, X, rho, gamma), G, U,
+                                p.cg_rel_tol, p.cg_abs_floor, p.cg_max_iter)
+    # dual step: lambda^{k+1} = lambda^k + rho (A(U^{k+1} V^{k+1 T}) - b)
+    e = sdp.A_of(U, V) - sdp.b
+    lam = st.lam + rho * e
+    rp = float(np.linalg.norm(e) / (1.0 + sdp.b_inf))
+    Uh = 0.5 * (U + V)
+    rp_hat = primal_infeasibility(sdp, Uh, Uh)
+    # second term of eq. stop: gamma ||V^{k+1} - V^k||_F / (1 + ||V^k||_F)
+    rs = gamma * float(np.linalg.norm(V - st.V)) / (1.0 + float(np.linalg.norm(st.V)))
+    st.U, st.V, st.lam, st.rp = U, V, lam, rp
+    st.k += 1
+    st.cg_iters += itU + itV
+    info = dict(k=st.k, rho=rho, gamma=gamma, rp=rp, rp_hat=rp_hat, rs=rs, cg_u=itU, cg_v=itV)
+    # penalty schedule
+    if st.k % p.rho_every == 0:
+        st.rho = min(st.rho * p.rho_growth, p.rho_max)
+    return info
+
+
+def lradmm(sdp: SDP, U0, V0, lam0, rho0: float, p: Params, trace: Optional[list] = None):
+    """Algorithm 1 until eq. stop holds and the output U_hat U_hat^T is feasible too:
+    max(r_P(U V^T), gamma ||V^{k+1}-V^k||_F/(1+||V^k||_F), r_P(U_hat U_hat^T)) <= tol."""
+    st = AdmmState(U=U0.copy(), V=V0.copy(), lam=lam0.copy(), rho=rho0,
+                   rp=primal_infeasibility(sdp, U0, V0))
+    converged = False
+    while st.k < p.max_admm_iter:
+        info = admm_iteration(sdp, st, p)
+        if trace is not None:
+            trace.append(info)
+        if max(info["rp"], info["rs"], info["rp_hat"]) <= p.tol:
+            converged = True
+            break
+    return st, converged
+
+
+# ======================================================================================
+# Phase I pieces: LRALM on the BM problem (Section 4.1)
+# ======================================================================================
+def bm_objective_and_gradient(sdp: SDP, U, lam, sigma):
+    """phi(U) = <C, U U^T> + <lam, A(U U^T) - b> + sigma/2 ||A(U U^T) - b||^2 and
+    grad phi = 2 (C + A^T(lam + sigma e)) U, e = A(U U^T) - b."""
+    e = sdp.A_of(U, U) - sdp.b
+    phi = sdp.C_inner(U, U) + float(lam @ e) + 0.5 * sigma * float(e @ e)
+    grad = 2.0 * (sdp.C_times(U) + sdp.At_times(lam + sigma * e, U))
+    return phi, grad, e
+
+
+def quartic_coefficients(sdp: SDP, U, D, lam, sigma, e0):
+    """phi(U + tD) - phi(U) = a1 t + a2 t^2 + a3 t^3 + a4 t^4, using
+    A((U+tD)(U+tD)^T) - b = e0 + t e1 + t^2 e2."""
+    e1 = sdp.A_of(U, D) + sdp.A_of(D, U)
+    e2 = sdp.A_of(D, D)
+    c1 = sdp.C_inner(U, D) + sdp.C_inner(D, U)
+    c2 = sdp.C_inner(D, D)
+    a1 = c1 + lam @ e1 + sigma * (e0 @ e1)
+    a2 = c2 + lam @ e2 + 0.5 * sigma * (e1 @ e1 + 2.0 * (e0 @ e2))
+    a3 = sigma * (e1 @ e2)
+    a4 = 0.5 * sigma * (e2 @ e2)
+    return float(a1), float(a2), float(a3), float(a4)
+
+
+def exact_line_search(a1, a2, a3, a4) -> float:
+    """argmin over t > 0 of a1 t + a2 t^2 + a3 t^3 + a4 t^4 (0 if none decreases)."""
+    poly = lambda t: ((a4 * t + a3) * t + a2) * t * t + a1 * t
+    deriv = [4.0 * a4, 3.0 * a3, 2.0 * a2, a1]
+    while len(deriv) > 1 and deriv[0] == 0.0:
+        deriv = deriv[1:]
+    if len(deriv) == 1:
+        return 0.0
+    roots = np.roots(deriv)
+    cands = [float(z.real) for z in roots if abs(z.imag) <= 1e-10 * (1.0 + abs(z.real))
+             and z.real > 0.0]
+    if not cands:
+        return 0.0
+    best = min(cands, key=poly)
+    return best if poly(best) < 0.0 else 0.0
+
+
+def lbfgs_direction(g, S: list, Y: list):
+    """-H g by the L-BFGS two-loop recursion (Nocedal and Wright, Algorithm 7.4)."""
+    q = g.copy()
+    alphas = []
+    for s, y in zip(reversed(S), reversed(Y)):
+        rho_i = 1.0 / float(np.vdot(y, s))
+        a = rho_i * float(np.vdot(s, q))
+        q = q - a * y
+        alphas.append((rho_i, a))
+    if S:
+        s, y = S[-1], Y[-1]
+        q = (float(np.vdot(s, y)) / float(np.vdot(y, y))) * q
+    for (s, y), (rho_i, a) in zip(zip(S, Y), reversed(alphas)):
+        beta = rho_i * float(np.vdot(y, q))
+        q = q + (a - beta) * s
+    return -q
+
+
+def diagonal_row_scaling(sdp: SDP):
+    """If every constraint is a single diagonal entry a e_j e_j^T on distinct rows with
+    b / a > 0 (MaxCut: X_jj = 1), return (rows, target norms) so that rows of U can be
+    scaled onto the constraint set; otherwise None."""
+    if sdp.R1 is not None or len(sdp.A_con) != sdp.m:
+        return None
+    if np.any(sdp.A_off) or len(np.unique(sdp.A_con)) != sdp.m:
+        return None
+    if len(np.unique(sdp.A_row)) != sdp.m:
+        return None
+    ratio = sdp.b[sdp.A_con] / sdp.A_val
+    if np.any(ratio <= 0):
+        return None
+    return sdp.A_row, np.sqrt(ratio)
+
+
+def initial_factor(sdp: SDP, r: int, seed: int):
+    """U_0 = N(0,1)/sqrt(r) (stream 0), rows scaled onto diagonal constraints if any."""
+    U = normal_matrix(stream_key(seed, 0), sdp.n, r) / math.sqrt(r)
+    sc = diagonal_row_scaling(sdp)
+    if sc is not None:
+        rows, target = sc
+        nrm = np.linalg.norm(U[rows], axis=1)
+        U[rows] = U[rows] * (target / nrm)[:, None]
+    return U
+
+
+def grow_rank(U, r_new: int, seed: int, growth_index: int, std: float):
+    """Append r_new - r columns drawn N(0, std^2) from stream ``growth_index``."""
+    n, r = U.shape
+    extra = std * normal_matrix(stream_key(seed, growth_index), n, r_new - r)
+    return np.concatenate([U, extra], axis=1)
+
+
+def lralm(sdp: SDP, U0, p: Params, trace: Optional[list] = None):
+    """Phase I: augmented Lagrangian on eq. prob:BM, L-BFGS inner solves, dynamic rank."""
+    U = U0.copy()
+    lam = np.zeros(sdp.m)
+    sigma = 1.0 / (1.0 + sdp.b_inf)
+    cap = rank_cap(sdp.m, sdp.n, p)
+    rp_prev = math.inf
+    growths = 0
+    inner_total = 0
+    rp = primal_infeasibility(sdp, U, U)
+    outer = 0
+    for outer in range(1, p.max_outer + 1):
+        S: list = []
+        Y: list = []
+        phi, g, e = bm_objective_and_gradient(sdp, U, lam, sigma)
+        it = 0
+        stalled = False
+        while True:
+            rp = float(np.linalg.norm(e) / (1.0 + sdp.b_inf))
+            grel = float(np.linalg.norm(g) / (1.0 + sdp.C_fro))
+            if grel <= max(p.inner_tol_abs, min(p.inner_tol_max, p.inner_tol_factor * rp)):
+                break
+            if it >= p.inner_max_iter:
+                stalled = True
+                break
+            D = lbfgs_direction(g, S, Y)
+            if float(np.vdot(D, g)) >= 0.0:
+                D = -g
+                S, Y = [], []
+            a1, a2, a3, a4 = quartic_coefficients(sdp, U, D, lam, sigma, e)
+            t = exact_line_search(a1, a2, a3, a4)
+            if t <= 0.0:
+                if S:                       # retry once along the steepest descent
+                    S, Y = [], []
+                    continue
+                break
+            U_new = U + t * D
+            phi_new, g_new, e_new = bm_objective_and_gradient(sdp, U_new, lam, sigma)
+            s = U_new - U
+            y = g_new - g
+            if float(np.vdot(s, y)) > 0.0:
+                S.append(s)
+                Y.append(y)
+                if len(S) > p.lbfgs_mem:
+                    S.pop(0)
+                    Y.pop(0)
+            U, phi, g, e = U_new, phi_new, g_new, e_new
+            it += 1
+        inner_total += it
+        r = U.shape[1]
+        if trace is not None:
+            trace.append(dict(outer=outer, inner=it, rp=rp, sigma=sigma, rank=r, stalled=stalled))
+        if rp <= p.switch_tol:
+            lam = lam + sigma * e
+            break
+        if stalled and r < cap:
+            # Section 4.3: stop the subproblem, raise the rank, carry on
+            growths += 1
+            U = grow_rank(U, next_rank(r, cap, p), p.seed, growths, p.new_col_std)
+            continue
+        lam = lam + sigma * e
+        if rp > p.sigma_decrease * rp_prev:
+            sigma *= p.sigma_factor
+        rp_prev = rp
+    return dict(U=U, lam=lam, sigma=sigma, outer=outer, inner=inner_total, growths=growths,
+                rp=rp)
+
+
+# ======================================================================================
+# Algorithm 2 (LoRADS) and the KKT report
+# ======================================================================================
+def kkt_report(sdp: SDP, Uh, y, min_eig: Optional[float] = None) -> dict:
+    """Appendix B measures plus BM stationarity.  y is the SDP dual (y = -lambda)."""
+    pobj = sdp.C_inner(Uh, Uh)
+    dobj = float(sdp.b @ y)
+    rep = dict(
+        objective=pobj, dual_objective=dobj,
+        r_P=primal_infeasibility(sdp, Uh, Uh),
+        r_D=dual_stationarity(sdp, Uh, -y),
+        gap=(pobj - dobj) / (1.0 + abs(pobj) + abs(dobj)),
+    )
+    if min_eig is not None:
+        rep["r_S"] = max(0.0, -min_eig) / (1.0 + sdp.c_one)
+    return rep
+
+
+def lorads(sdp: SDP, p: Params = Params(), U0=None, lam0=None, rho0=None,
+           trace: Optional[dict] = None) -> dict:
+    """Algorithm 2.  Returns U, V, U_hat, lambda, y and the KKT report."""
+    t0 = time.perf_counter()
+    tr1: list = []
+    tr2: list = []
+    if p.phase1:
+        r = initial_rank(sdp.m, sdp.n, p)
+        U_init = initial_factor(sdp, r, p.seed) if U0 is None else U0
+        ph1 = lralm(sdp, U_init, p, tr1)
+        U_bm, lam_bm, sigma = ph1["U"], ph1["lam"], ph1["sigma"]
+        rho = min(p.h * sigma, p.rho_max)
+    else:
+        ph1 = dict(outer=0, inner=0, growths=0, rp=math.nan)
+        U_bm = U0
+        lam_bm = np.zeros(sdp.m) if lam0 is None else lam0
+        rho = 100.0 if rho0 is None else rho0
+    t1 = time.perf_counter()
+    st, converged = lradmm(sdp, U_bm, U_bm, lam_bm, rho, p, tr2)
+    t2 = time.perf_counter()
+    Uh = 0.5 * (st.U + st.V)
+    y = -st.lam
+    rep = kkt_report(sdp, Uh, y)
+    if trace is not None:
+        trace["phase1"] = tr1
+        trace["phase2"] = tr2
+    return dict(U=st.U, V=st.V, U_hat=Uh, lam=st.lam, y=y, rank=Uh.shape[1],
+                converged=converged, admm_iters=st.k, cg_iters=st.cg_iters, rho=st.rho,
+                alm_outer=ph1["outer"], lbfgs_iters=ph1["inner"], growths=ph1["growths"],
+                t_phase1=t1 - t0, t_phase2=t2 - t1, **rep)

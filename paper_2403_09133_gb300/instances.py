@@ -1,0 +1,229 @@
+"""Seeded synthetic SDP instances shaped like the paper's workloads.
+
+This module only *generates problem data* (graphs, weights, samples) and writes
+them as the linear-SDP triple (C, {A_i}, b) of Section 1 (eq. prob:linear-SDP).
+It holds none of the solver's arithmetic, so both the CUDA library's tests and
+the FP64 CPU oracle can draw identical inputs from it.
+
+Conventions (shared by the C ABI and the oracle):
+  * symmetric matrices are given as upper triplets (row <= col); an off-diagonal
+    triplet (i, j, a) stands for both (i, j) and (j, i), so
+    <A, X> = sum_diag a_ii X_ii + 2 sum_{i<j} a_ij X_ij;
+  * constraint k is the set of triplets whose ``con`` equals k.
+
+Workload families:
+  * MaxCut SDP (Section 5.3): C = -L(G, w)/4, A_i = e_i e_i^T, b = 1.  The paper
+    states the max form <L/4, X>; the min form used here has objective
+    -(SDP value).
+  * Matrix completion (Section 5.4): X in S^{n1+n2}, constraint k fixes the entry
+    (p, n1+q) of the off-diagonal block through <A_k, X> = 2 X_{p,n1+q} = 2 M_pq,
+    C = I.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+
+@dataclass
+class SDPInstance:
+    """Linear SDP data as upper-triangular triplets (see module docstring)."""
+
+    n: int
+    m: int
+    C_row: np.ndarray
+    C_col: np.ndarray
+    C_val: np.ndarray
+    A_con: np.ndarray
+    A_row: np.ndarray
+    A_col: np.ndarray
+    A_val: np.ndarray
+    b: np.ndarray
+    # rank-one terms: A_con += scale * a a^T with a given sparsely by (idx, vals)
+    rank1: List[Tuple[int, np.ndarray, np.ndarray, float]] = field(default_factory=list)
+    kind: str = "general"          # "maxcut" | "mc" | "general"
+    name: str = ""
+    # graph data kept for certificates (MaxCut only)
+    edges: Optional[np.ndarray] = None
+    weights: Optional[np.ndarray] = None
+    # matrix-completion ground truth (MC only)
+    mc_P: Optional[np.ndarray] = None
+    mc_Q: Optional[np.ndarray] = None
+    mc_n1: int = 0
+
+    def __post_init__(self):
+        self.C_row = np.ascontiguousarray(self.C_row, dtype=np.int32)
+        self.C_col = np.ascontiguousarray(self.C_col, dtype=np.int32)
+        self.C_val = np.ascontiguousarray(self.C_val, dtype=np.float64)
+        self.A_con = np.ascontiguousarray(self.A_con, dtype=np.int32)
+        self.A_row = np.ascontiguousarray(self.A_row, dtype=np.int32)
+        self.A_col = np.ascontiguousarray(self.A_col, dtype=np.int32)
+        self.A_val = np.ascontiguousarray(self.A_val, dtype=np.float64)
+        self.b = np.ascontiguousarray(self.b, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------------------
+# graphs
+# --------------------------------------------------------------------------------------
+def erdos_renyi_edges(n: int, num_edges: int, rng: np.random.Generator) -> np.ndarray:
+    """G(n, M): ``num_edges`` distinct unordered pairs drawn uniformly (i < j)."""
+    total = n * (n - 1) // 2
+    if num_edges > total:
+        raise ValueError("too many edges for G(n, M)")
+    chosen = np.empty(0, dtype=np.int64)
+    while chosen.size < num_edges:
+        need = num_edges - chosen.size
+        i = rng.integers(0, n, size=2 * need + 16, dtype=np.int64)
+        j = rng.integers(0, n, size=2 * need + 16, dtype=np.int64)
+        keep = i != j
+        lo = np.minimum(i[keep], j[keep])
+        hi = np.maximum(i[keep], j[keep])
+        chosen = np.unique(np.concatenate([chosen, lo * n + hi]))
+    # a uniformly random M-subset of the distinct pairs found
+    pick = rng.permutation(chosen.size)[:num_edges]
+    codes = np.sort(chosen[pick])
+    return np.stack([codes // n, codes % n], axis=1).astype(np.int64)
+
+
+def torus_edges(a: int, b: int) -> np.ndarray:
+    """Edges of the a x b toroidal grid (Cartesian product of two cycles), i < j."""
+    idx = np.arange(a * b).reshape(a, b)
+    right = np.stack([idx.ravel(), np.roll(idx, -1, axis=1).ravel()], axis=1)
+    down = np.stack([idx.ravel(), np.roll(idx, -1, axis=0).ravel()], axis=1)
+    e = np.concatenate([right, down])
+    e = np.stack([e.min(1), e.max(1)], axis=1)
+    e = np.unique(e, axis=0)          # a or b equal to 2 would create duplicates
+    return e[e[:, 0] != e[:, 1]]
+
+
+def cycle_edges(n: int) -> np.ndarray:
+    i = np.arange(n)
+    e = np.stack([i, (i + 1) % n], axis=1)
+    e = np.stack([e.min(1), e.max(1)], axis=1)
+    return np.unique(e, axis=0)
+
+
+def complete_edges(n: int) -> np.ndarray:
+    i, j = np.triu_indices(n, 1)
+    return np.stack([i, j], axis=1).astype(np.int64)
+
+
+# --------------------------------------------------------------------------------------
+# MaxCut SDP (Section 5.3)
+# --------------------------------------------------------------------------------------
+def maxcut_sdp(n: int, edges: np.ndarray, w: np.ndarray, name: str = "") -> SDPInstance:
+    """min <C,X> with C = -L(G,w)/4, X_ii = 1 (A_i = e_i e_i^T, b_i = 1)."""
+    edges = np.asarray(edges, dtype=np.int64)
+    w = np.asarray(w, dtype=np.float64)
+    deg = np.zeros(n)
+    np.add.at(deg, edges[:, 0], w)
+    np.add.at(deg, edges[:, 1], w)
+    # Laplacian: L_ii = sum_k w_ik, L_ij = -w_ij  ->  C = -L/4
+    diag_rows = np.arange(n)
+    C_row = np.concatenate([diag_rows, edges[:, 0]])
+    C_col = np.concatenate([diag_rows, edges[:, 1]])
+    C_val = np.concatenate([-deg / 4.0, w / 4.0])
+    keep = C_val != 0.0
+    return SDPInstance(
+        n=n, m=n,
+        C_row=C_row[keep], C_col=C_col[keep], C_val=C_val[keep],
+        A_con=np.arange(n), A_row=np.arange(n), A_col=np.arange(n), A_val=np.ones(n),
+        b=np.ones(n), kind="maxcut", name=name, edges=edges, weights=w,
+    )
+
+
+def maxcut_er(n: int, avg_degree: float, seed: int, name: str = "") -> SDPInstance:
+    """Erdos-Renyi G(n, M = floor(n d / 2)) with unit weights."""
+    rng = np.random.default_rng(seed)
+    M = int(np.floor(n * avg_degree / 2))
+    e = erdos_renyi_edges(n, M, rng)
+    return maxcut_sdp(n, e, np.ones(len(e)), name or f"er_n{n}_d{avg_degree:g}_s{seed}")
+
+
+def maxcut_torus(a: int, b: int, seed: Optional[int], name: str = "") -> SDPInstance:
+    """a x b toroidal grid; weights uniform in {-1,+1} (seed given) or all 1 (seed None)."""
+    e = torus_edges(a, b)
+    if seed is None:
+        w = np.ones(len(e))
+    else:
+        rng = np.random.default_rng(seed)
+        w = rng.choice(np.array([-1.0, 1.0]), size=len(e))
+    return maxcut_sdp(a * b, e, w, name or f"torus_{a}x{b}_s{seed}")
+
+
+def maxcut_complete(n: int) -> SDPInstance:
+    e = complete_edges(n)
+    return maxcut_sdp(n, e, np.ones(len(e)), f"K{n}")
+
+
+def maxcut_cycle(n: int) -> SDPInstance:
+    e = cycle_edges(n)
+    return maxcut_sdp(n, e, np.ones(len(e)), f"C{n}")
+
+
+# --------------------------------------------------------------------------------------
+# Matrix completion SDP (Section 5.4)
+# --------------------------------------------------------------------------------------
+def matrix_completion(n1: int, n2: int, rank: int, num_samples: int, seed: int,
+                      name: str = "") -> SDPInstance:
+    """Z block fixed to samples of M = P Q^T, P, Q i.i.d. N(0,1); C = I.
+
+    Sampled positions are distinct, uniform over the n1*n2 grid, sorted row-major.
+    """
+    rng = np.random.default_rng(seed)
+    P = rng.standard_normal((n1, rank))
+    Q = rng.standard_normal((n2, rank))
+    total = n1 * n2
+    if num_samples > total:
+        raise ValueError("more samples than entries")
+    codes = np.empty(0, dtype=np.int64)
+    while codes.size < num_samples:
+        need = num_samples - codes.size
+        draw = rng.integers(0, total, size=need + need // 8 + 16, dtype=np.int64)
+        codes = np.unique(np.concatenate([codes, draw]))
+    codes = np.sort(codes[rng.permutation(codes.size)[:num_samples]])
+    p = codes // n2
+    q = codes % n2
+    Mpq = np.einsum("ij,ij->i", P[p], Q[q])
+    n = n1 + n2
+    m = num_samples
+    return SDPInstance(
+        n=n, m=m,
+        C_row=np.arange(n), C_col=np.arange(n), C_val=np.ones(n),
+        A_con=np.arange(m), A_row=p, A_col=n1 + q, A_val=np.ones(m),
+        b=2.0 * Mpq, kind="mc", name=name or f"mc_{n1}x{n2}_r{rank}_m{m}_s{seed}",
+        mc_P=P, mc_Q=Q, mc_n1=n1,
+    )
+
+
+# --------------------------------------------------------------------------------------
+# Named workloads
+# --------------------------------------------------------------------------------------
+def workload_er500() -> SDPInstance:
+    """MaxCut, Erdos-Renyi n=500, average degree 8 (M=2000), unit weights, seed 1."""
+    return maxcut_er(500, 8.0, seed=1, name="maxcut_er_n500_d8")
+
+
+def workload_torus141() -> SDPInstance:
+    """MaxCut, 141x141 toroidal grid (n=m=19,881), weights uniform in {-1,+1}, seed 2."""
+    return maxcut_torus(141, 141, seed=2, name="maxcut_torus_141x141_pm1")
+
+
+def workload_batch(count: int = 512, seed0: int = 1000, n_lo: int = 64, n_hi: int = 2048,
+                   d_lo: float = 3.0, d_hi: float = 12.0) -> List[SDPInstance]:
+    """Uneven batch of ER MaxCuts: n ~ U[n_lo, n_hi], degree ~ U[d_lo, d_hi], seeds seed0+i."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        n = int(rng.integers(n_lo, n_hi + 1))
+        d = float(rng.uniform(d_lo, d_hi))
+        out.append(maxcut_er(n, d, seed=seed0 + i, name=f"batch_{i}"))
+    return out
+
+
+def workload_mc(n1: int = 20000, n2: int = 20000, rank: int = 5,
+                num_samples: int = 15_694_167, seed: int = 5) -> SDPInstance:
+    """Matrix completion, n = n1 + n2; the full size is n = 40,000 with 15,694,167 samples."""
+    return matrix_completion(n1, n2, rank, num_samples, seed, name=f"mc_{n1 + n2}")
