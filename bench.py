@@ -1,0 +1,321 @@
+"""Benchmark: LoRADS solves of the 141x141 +-1 toroidal MaxCut SDP on the GPU.
+
+One step = one whole solve (Algorithm 2: Phase I, Phase II with CG, output and residuals)
+of the workload with its data already resident on the device, in the chosen (mixed
+FP32/FP64) form; the plain FP64 form is timed on the same workload for comparison.
+
+Prints one JSON line (see README of the repository for the keys):
+  value       solves per second over all ranks (device-resident inputs, CUDA events)
+  e2e         the same metric through the C ABI from host buffers (upload + solve + download)
+  roofline    the solver kernel's algorithmic bytes / its CUDA-event time vs measured HBM peak
+  cpu_baseline  the FP64 CPU oracle timed on a bounded sample of the same workload
+
+`--impl reference` times the CPU oracle alone (the reference arm for this workload).
+Multi-GPU (torchrun): every rank solves its own copy (replicas, weak scaling); rank 0
+prints max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-KKT<=1e-6 & CG-operator HBM GB/s: chosen form vs plain FP64, 1 GB300"
+WORKLOAD = "maxcut_torus_141x141_pm1"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lorads", choices=["lorads", "reference"])
+    ap.add_argument("--oracle-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD)
+    return ap.parse_args()
+
+
+def make_instance(name):
+    from paper_2403_09133_gb300 import instances as I
+    if name == WORKLOAD:
+        return I.workload_torus141()
+    if name == "maxcut_er_n500_d8":
+        return I.workload_er500()
+    raise ValueError(name)
+
+
+# --------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# --------------------------------------------------------------------------------- CPU oracle
+def oracle_sample(inst, seconds, admm_iters_gpu):
+    """Times the FP64 CPU oracle on a bounded sample: Phase I in full, then Phase II
+    iterations until `seconds` elapse; scales to one solve with the GPU's iteration count."""
+    from oracle import SDP, Params
+    import oracle.lorads as OL
+    sdp = SDP.from_instance(inst)
+    p = Params()
+    t0 = time.perf_counter()
+    r = OL.initial_rank(sdp.m, sdp.n, p)
+    ph1 = OL.lralm(sdp, OL.initial_factor(sdp, r, p.seed), p)
+    t1 = time.perf_counter()
+    st = OL.AdmmState(U=ph1["U"].copy(), V=ph1["U"].copy(), lam=ph1["lam"].copy(),
+                      rho=min(p.h * ph1["sigma"], p.rho_max), rp=ph1["rp"])
+    k = 0
+    while time.perf_counter() - t1 < seconds and k < admm_iters_gpu:
+        OL.admm_iteration(sdp, st, p)
+        k += 1
+    t2 = time.perf_counter()
+    per_iter = (t2 - t1) / max(k, 1)
+    solve_s = (t1 - t0) + per_iter * admm_iters_gpu
+    cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"Phase I in full ({t1 - t0:.2f} s) + {k} Phase II iterations "
+                      f"({per_iter * 1e3:.2f} ms each), scaled to {admm_iters_gpu} iterations",
+            "seconds_per_solve": solve_s}
+
+
+# --------------------------------------------------------------------------------- GPU arm
+def algorithmic_bytes(res, n, s, ld):
+    """Algorithmic HBM bytes of one solve's CG operators (roofline section):
+    per CG iteration the Hessian apply reads P and W and writes HP, the update reads delta,
+    P, R, HP and writes delta and R, the direction step reads R, P and writes P:
+    12 n ld s bytes; each warm-start residual pass reads W (FP64) and writes R, P, delta."""
+    cg = res["cg_iters"]
+    r0 = res["hessian_applies"] - cg
+    return cg * 12 * n * ld * s + r0 * n * ld * (8 + 3 * s)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2403_09133_gb300 import lorads as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    inst = make_instance(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    prob = L.Problem(inst)
+    results = {}
+    for form, prec in (("mixed", L.LORADS_PREC_MIXED), ("fp64", L.LORADS_PREC_FP64)):
+        prm = prob.params(precision=prec)
+        times = []
+        res = None
+        for it in range(args.warmup + args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(it))          # L2 flush outside the timed region
+            stream.synchronize()
+            if it == args.warmup:
+                barrier()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            r = L.lorads_solve(prob.handle, prm, stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            if it >= args.warmup:
+                times.append(ev0.elapsed_time(ev1) * 1e-3)
+            res = r.as_dict()
+        barrier()
+        results[form] = dict(res=res, times=times)
+    # clocks: one more timed pass of the chosen form under the sampler
+    sampler = ClockSampler(local)
+    sampler.start()
+    prm = prob.params(precision=L.LORADS_PREC_MIXED)
+    t_cl = []
+    for _ in range(max(1, args.steps)):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        L.lorads_solve(prob.handle, prm, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        t_cl.append(ev0.elapsed_time(ev1) * 1e-3)
+    clocks = sampler.stop()
+    # end to end: host buffers through the C ABI, every step
+    e2e_times = []
+    h2d = (len(inst.C_row) * 16 + len(inst.A_con) * 20 + inst.m * 8)
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = L.Problem(inst)
+        r2 = p2.solve(precision=L.LORADS_PREC_MIXED)
+        sol = p2.solution()
+        p2.close()
+        t1 = time.perf_counter()
+        if it >= args.warmup:
+            e2e_times.append(t1 - t0)
+    d2h = sol["U"].nbytes * 3 + sol["y"].nbytes
+    prob.close()
+
+    t_mixed = max(statistics.median(results["mixed"]["times"]), 1e-12)
+    t_fp64 = max(statistics.median(results["fp64"]["times"]), 1e-12)
+    t_e2e = statistics.median(e2e_times)
+    if world > 1:
+        tt = torch.tensor([t_mixed, t_fp64, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_mixed, t_fp64, t_e2e = tt.tolist()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+    rm, rf = results["mixed"]["res"], results["fp64"]["res"]
+    ld = (rm["rank"] + 3) // 4 * 4
+    bytes_mixed = algorithmic_bytes(rm, inst.n, 4, ld)
+    bytes_fp64 = algorithmic_bytes(rf, inst.n, 8, (rf["rank"] + 3) // 4 * 4)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    ach = bytes_mixed / t_mixed / 1e9
+    line = {
+        "metric": METRIC,
+        "value": world / t_mixed,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_mixed * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 CG operators / f64 masters",
+        "data": "synthetic (seeded generator shaped like the paper's MaxCut workloads)",
+        "config": {"workload": args.workload, "n": inst.n, "m": inst.m,
+                   "r0": rm["rank"], "form": "mixed", "parallelism": "replicas",
+                   "l2": "256 MB buffer written between timed solves"},
+        "solve": {k: rm[k] for k in ("status", "objective", "r_P", "r_P_split", "r_stop", "r_D",
+                                    "gap", "admm_iters", "cg_iters", "hessian_applies",
+                                    "alm_outer", "lbfgs_iters", "rank")},
+        "kkt_reached": rm["status"] == 0,
+        "plain_fp64": {"ms_per_solve": t_fp64 * 1e3, "status": rf["status"],
+                       "objective": rf["objective"], "admm_iters": rf["admm_iters"],
+                       "cg_iters": rf["cg_iters"],
+                       "cg_operator_gbs": bytes_fp64 / t_fp64 / 1e9},
+        "mixed_speedup_vs_fp64": t_fp64 / t_mixed,
+        "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "traffic": None,
+                     "kernel": "lorads::solve_grid_kernel<float>",
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(inst, args.oracle_seconds, rm["admm_iters"])
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    inst = make_instance(args.workload)
+    iters = 5000
+    vals = []
+    last = None
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        last = oracle_sample(inst, args.oracle_seconds / max(1, args.steps), iters)
+        t1 = time.perf_counter()
+        if it >= args.warmup:
+            vals.append(last["value"])
+    v = statistics.median(vals)
+    return {
+        "metric": METRIC, "impl": "reference", "value": v, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": inst.n, "m": inst.m, "form": "oracle"},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": last["cores"],
+                         "kind": "oracle", "sample": last["sample"]},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * lorads.h -- C ABI of the GB300 (sm_103a) LoRADS library.
+ *
+ * LoRADS solves the linear SDP of Section 1 (eq. prob:linear-SDP)
+ *
+ *     min <C, X>   s.t.   A(X) = b,   X PSD,     A(X)_i = <A_i, X>,  i = 1..m,
+ *
+ * with a Burer-Monteiro warm start (Phase I, Section 4.1) followed by the low-rank ADMM
+ * splitting X = U V^T (Phase II, Algorithm 1), whose U- and V-subproblems are the linear
+ * systems eq. linU / eq. linV solved by warm-started conjugate gradients (Section 4.4).
+ * The output is U_hat = (U + V)/2 (Algorithm 2), X = U_hat U_hat^T, and the dual y.
+ *
+ * Conventions shared by every call
+ *   - Symmetric matrices (C and each A_i) are passed as upper triplets (row <= col).  An
+ *     off-diagonal triplet (i, j, a) stands for a at (i, j) and at (j, i), so
+ *     <A, X> = sum_diag a_ii X_ii + 2 sum_{i<j} a_ij X_ij.  Duplicates add up.
+ *   - Dense factors are row-major n x ld with ld >= r; the library pads r to a multiple of 4.
+ *   - Indices are 0-based int32; sizes are int64.
+ *   - Every call returns LORADS_OK (0) or a negative status; none aborts, throws or prints.
+ *     lorads_status_string() names a status.
+ *   - Host arrays passed to lorads_set_* / lorads_add_* are copied; the caller keeps them.
+ *   - The library owns its device memory (one CUDA device: the current device at
+ *     lorads_create).  Calls on one problem must not run concurrently from several threads.
+ *   - The multiplier lambda of the augmented Lagrangian (eq. ALF) enters with a plus sign;
+ *     the SDP dual returned here is y = -lambda, so that S = C - A^T(y) is PSD at an optimum.
+ */
+#ifndef LORADS_H
+#define LORADS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+  LORADS_OK = 0,
+  LORADS_ERR_ARG = -1,          /* bad argument (null pointer, index out of range, size) */
+  LORADS_ERR_STATE = -2,        /* call out of order (e.g. solve before set_b)            */
+  LORADS_ERR_CUDA = -3,         /* a CUDA runtime call failed                             */
+  LORADS_ERR_NOMEM = -4,        /* device or host allocation failed                       */
+  LORADS_ERR_MAXITER = -5,      /* iteration cap reached before the tolerance             */
+  LORADS_ERR_TIMEOUT = -6,      /* time limit reached before the tolerance                */
+  LORADS_ERR_NAN = -7,          /* a NaN or Inf appeared in the iterates or the input     */
+  LORADS_ERR_UNSUPPORTED = -8,  /* constraint structure this build does not handle        */
+  LORADS_ERR_DEVICE = -9        /* a device-side wait gave up (bounded grid barrier)      */
+};
+
+/* ---------------------------------------------------------------- precision forms */
+enum {
+  LORADS_PREC_FP64 = 0,   /* every operator and vector in FP64                             */
+  LORADS_PREC_MIXED = 1   /* CG operators (SDDMM/SpMM bulk, CG vectors) in FP32; masters   */
+                          /* U, V, lambda, residual norms, CG alpha/beta, objective in FP64 */
+};
+
+/* ---------------------------------------------------------------- parameters
+ * Defaults (lorads_default_params) follow Section 5.1 where the paper states a value and
+ * the readings listed beside each field where it does not.  A negative value marked
+ * "auto" is resolved at solve time from the constraint structure: when every constraint
+ * is a single diagonal entry (MaxCut, Section 5.3) switch_tol = 1e-2 and h = 10,
+ * otherwise switch_tol = 1e-3 and h = 1. */
+typedef struct lorads_params {
+  int32_t r0;              /* initial rank; 0 = ceil(log2 m)                                */
+  int32_t rank_max;        /* cap for rank growth; 0 = min(floor(sqrt(2m)), n, 256)         */
+  double rank_factor;      /* rank growth factor (1.5, Section 4.3)                          */
+  double tol;              /* final tolerance (1e-6)                                         */
+  double switch_tol;       /* Phase I -> II switch on primal infeasibility (auto)            */
+  double h;                /* heuristic factor rho <- h rho at the switch (auto)             */
+  double rho_max;          /* 5000 (Section 5.1)                                             */
+  double rho_growth;       /* 1.2 (Section 5.1)                                              */
+  int32_t rho_every;       /* 5 (Section 5.1)                                                */
+  double gamma_scale;      /* gamma = gamma_scale * max_j sum_k |C_jk| (paper silent): 1     */
+  double gamma_fixed;      /* > 0 overrides gamma                                            */
+  int32_t max_admm_iter;   /* 5000 (Section 5.2)                                             */
+  int32_t cg_max_iter;     /* 1000                                                           */
+  double cg_rel_tol;       /* CG stops at ||R|| <= cg_rel_tol ||R_0|| ... (1e-3)             */
+  double cg_abs_floor;     /* ... or ||R|| <= cg_abs_floor ||G|| (1e-13)                     */
+  int32_t lbfgs_mem;       /* L-BFGS memory in Phase I (4, at most 8)                        */
+  int32_t inner_max_iter;  /* L-BFGS iterations per ALM subproblem before rank growth (300)  */
+  double inner_tol_factor; /* ALM subproblem stop: ||grad||/(1+||C||_F) <= min(max, f r_P)   */
+  double inner_tol_max;    /*   (factor 10, max 0.1)                                         */
+  int32_t max_outer;       /* ALM outer iterations (500)                                     */
+  double sigma_factor;     /* ALM penalty growth when r_P fell less than 4x (2)              */
+  double sigma_decrease;   /* the "4x": 0.25                                                 */
+  double new_col_std;      /* std of columns added by rank growth (1e-2)                     */
+  uint64_t seed;           /* SplitMix64 seed for U_0 and rank growth                        */
+  int32_t precision;       /* LORADS_PREC_FP64 or LORADS_PREC_MIXED                          */
+  int32_t phase1;          /* 1: Phase I from random U_0; 0: start Phase II from lorads_set_start */
+  double time_limit_s;     /* wall-clock cap of one solve on the device (60 s)               */
+  int32_t threads;         /* CTA size of the solver kernels (0 = library choice)            */
+  int32_t grid;            /* solver CTAs (0 = library choice; 1 forces one-CTA scope)       */
+} lorads_params;
+
+/* ---------------------------------------------------------------- result */
+typedef struct lorads_result {
+  int32_t status;          /* LORADS_OK when the final test passed                           */
+  int32_t rank;            /* final r                                                        */
+  double objective;        /* <C, U_hat U_hat^T>                                             */
+  double dual_objective;   /* b^T y                                                          */
+  double r_P;              /* ||A(U_hat U_hat^T) - b||_2 / (1 + ||b||_inf)   (Section 5.2)   */
+  double r_P_split;        /* ||A(U V^T) - b||_2 / (1 + ||b||_inf)                           */
+  double r_stop;           /* gamma ||V^{k+1} - V^k||_F / (1 + ||V^k||_F)  (eq. stop)        */
+  double r_D;              /* ||(C - A^T y) U_hat||_F / (1 + ||C||_F)  (eq. def:eKKT)        */
+  double gap;              /* (<C,X> - b^T y) / (1 + |<C,X>| + |b^T y|)  (Appendix B)        */
+  double rho;              /* final rho                                                      */
+  double gamma;            /* gamma used in Phase II                                         */
+  double sigma;            /* final Phase I penalty                                          */
+  int32_t admm_iters;      /* Phase II iterations                                            */
+  int32_t cg_iters;        /* CG iterations summed over all subproblems                     */
+  int32_t hessian_applies; /* Hessian-vector products (CG iterations + warm-start residuals) */
+  int32_t alm_outer;       /* Phase I outer iterations                                       */
+  int32_t lbfgs_iters;     /* Phase I L-BFGS iterations                                      */
+  int32_t rank_growths;    /* rank increases                                                 */
+  double time_phase1_s;    /* device time of Phase I                                         */
+  double time_phase2_s;    /* device time of Phase II and the output step                    */
+} lorads_result;
+
+typedef struct lorads_problem lorads_problem;
+
+/* ---------------------------------------------------------------- problem set-up */
+
+/* New problem with n (matrix order) and m (constraints) on the current CUDA device.
+ * *out receives an opaque handle owned by the library (release with lorads_destroy). */
+int lorads_create(int64_t n, int64_t m, lorads_problem **out);
+
+/* The objective C (Section 1): nnz upper triplets.  Replaces any earlier C. */
+int lorads_set_C(lorads_problem *p, int64_t nnz, const int32_t *row, const int32_t *col,
+                 const double *val);
+
+/* Adds sparse terms to constraints: for t < nnz, A_{con[t]} gets val[t] at (row[t], col[t])
+ * (and its mirror).  Sparse form of the A_i of eq. prob:linear-SDP. */
+int lorads_add_A_sparse(lorads_problem *p, int64_t nnz, const int32_t *con, const int32_t *row,
+                        const int32_t *col, const double *val);
+
+/* Adds a rank-one term A_con += scale * a a^T with a given by nnz (idx, a) pairs (the
+ * sensor-localisation constraints of Section 2.3).  Accepted and kept; the device solver
+ * of this build returns LORADS_ERR_UNSUPPORTED for problems that use it. */
+int lorads_add_A_rank1(lorads_problem *p, int32_t con, int64_t nnz, const int32_t *idx,
+                       const double *a, double scale);
+
+/* The right-hand side b (length m). */
+int lorads_set_b(lorads_problem *p, const double *b);
+
+/* Defaults described at lorads_params. */
+void lorads_default_params(lorads_params *prm);
+
+/* Phase II start for prm->phase1 == 0 (e.g. a learned warm start): U0 is n x r row-major
+ * (U = V = U0), lambda0 of length m (NULL = 0), rho0 the initial penalty (<= 0: 100). */
+int lorads_set_start(lorads_problem *p, int32_t r, const double *U0, const double *lambda0,
+                     double rho0);
+
+/* ---------------------------------------------------------------- solve */
+
+/* Algorithm 2 on the device.  stream is a cudaStream_t (NULL = the legacy default stream);
+ * the call returns when the solve has finished.  res may be NULL.  The return value is
+ * the solve status (also res->status). */
+int lorads_solve(lorads_problem *p, const lorads_params *prm, void *stream, lorads_result *res);
+
+/* The last solve's factors and dual into caller host buffers: U, V, U_hat as n x r
+ * row-major (r = result rank; any pointer may be NULL), y of length m. */
+int lorads_get_solution(const lorads_problem *p, double *U, double *V, double *U_hat,
+                        double *y, int32_t *r);
+
+/* Releases the problem and its device memory.  NULL is ignored. */
+void lorads_destroy(lorads_problem *p);
+
+const char *lorads_status_string(int code);
+
+/* sizeof(lorads_params) and sizeof(lorads_result) as compiled into the library, so that a
+ * binding can check its mirror of the two structs.  Either pointer may be NULL. */
+void lorads_struct_sizes(int64_t *params_bytes, int64_t *result_bytes);
+
+/* ---------------------------------------------------------------- operators
+ * The linear maps of the method on caller-owned DEVICE arrays (row-major n x ld, ld a
+ * multiple of 4, ld >= r), enqueued on stream; they return after enqueueing.  prec selects
+ * the element type of U, V, P, out: FP64 (double) or MIXED (float); vectors indexed by
+ * constraint are double.  They exist for testing and benchmarking the kernels the solver
+ * is built from. */
+
+/* q_i = <A_i, U V^T>, i = 1..m (the sampled dense-dense product, Algorithm 1 dual step). */
+int lorads_op_sddmm(lorads_problem *p, int32_t prec, int32_t r, int32_t ld, const void *U,
+                    const void *V, double *q, void *stream);
+
+/* out = (A^T(w) - C) V + gamma V (the right-hand side of eq. linU with w = rho b - lambda). */
+int lorads_op_spmm(lorads_problem *p, int32_t prec, int32_t r, int32_t ld, const double *w,
+                   double gamma, const void *V, void *out, void *stream);
+
+/* out = rho A^T(A(P V^T)) V + gamma P (the matrix of eq. linU applied to P, never formed). */
+int lorads_op_hessian(lorads_problem *p, int32_t prec, int32_t r, int32_t ld, double rho,
+                      double gamma, const void *V, const void *P, void *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LORADS_H */

@@ -1,0 +1,736 @@
+// Host runtime of the C ABI declared in include/lorads.h.
+//
+// lorads_problem keeps the caller's triplets on the host until the first solve or operator
+// call, then assembles the device form once (see lorads_device.cuh: constraints in
+// constraint order plus a symmetric CSR of A and of C), resolves the parameters and
+// launches the persistent solver.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/lorads.h"
+#include "lorads_kernels.cuh"
+
+using namespace lorads;
+
+namespace {
+
+struct Rank1Term {
+  int32_t con;
+  std::vector<int32_t> idx;
+  std::vector<double> a;
+  double scale;
+};
+
+// one device allocation carved into 256-byte aligned pieces
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  void release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = used = 0;
+  }
+  int reserve(size_t bytes) {
+    if (bytes <= cap) {
+      used = 0;
+      return LORADS_OK;
+    }
+    release();
+    if (cudaMalloc((void**)&base, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      base = nullptr;
+      return LORADS_ERR_NOMEM;
+    }
+    cap = bytes;
+    used = 0;
+    return LORADS_OK;
+  }
+  template <typename X>
+  X* take(size_t count) {
+    size_t bytes = ((count * sizeof(X) + 255) / 256) * 256;
+    X* p = reinterpret_cast<X*>(base + used);
+    used += bytes;
+    return p;
+  }
+  static size_t need(size_t count, size_t elem) { return ((count * elem + 255) / 256) * 256; }
+};
+
+}  // namespace
+
+struct lorads_problem {
+  int64_t n = 0, m = 0;
+  int device = 0;
+  // host triplets
+  std::vector<int32_t> C_row, C_col;
+  std::vector<double> C_val;
+  std::vector<int32_t> A_con, A_row, A_col;
+  std::vector<double> A_val;
+  std::vector<Rank1Term> rank1;
+  std::vector<double> b;
+  bool has_b = false;
+  // Phase II start (phase1 == 0)
+  int32_t start_r = 0;
+  std::vector<double> start_U, start_lam;
+  double start_rho = 0.0;
+  bool has_start = false;
+  // device problem
+  bool assembled = false;
+  int assemble_status = LORADS_OK;
+  Arena prob_mem;
+  DevProblem dp{};
+  bool diag_separable = false;
+  double C_fro = 0, C_inf = 0, b_inf = 0;
+  // solver state
+  Arena state_mem;
+  double* dU = nullptr;
+  double* dV = nullptr;
+  double* dUh = nullptr;
+  double* dlam = nullptr;
+  void* dargs = nullptr;  // SolverArgs<T> on the device
+  SolveOut* dout = nullptr;
+  GridCtl* dctl = nullptr;
+  double* dpartials = nullptr;
+  int* dqueue = nullptr;
+  int sol_r = 0, sol_ld = 0;
+  bool has_solution = false;
+  lorads_result last{};
+};
+
+// ---------------------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------------------
+static bool is_finite_value(double x) { return std::isfinite(x); }
+
+static int check_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LORADS_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? LORADS_ERR_NOMEM : LORADS_ERR_CUDA;
+}
+
+#define CU(x)                                   \
+  do {                                          \
+    int _s = check_cuda(x);                     \
+    if (_s != LORADS_OK) return _s;             \
+  } while (0)
+
+static void invalidate(lorads_problem* p) {
+  p->assembled = false;
+  p->has_solution = false;
+}
+
+// Symmetric CSR (both triangles) from upper triplets; entry payload carried along.
+struct SymEntry {
+  int32_t row, col, con;
+  double val;
+};
+
+static void build_sym_csr(int64_t n, std::vector<SymEntry>& ent, std::vector<int32_t>& rp,
+                          std::vector<int32_t>& col, std::vector<int32_t>& con,
+                          std::vector<double>& val) {
+  std::sort(ent.begin(), ent.end(), [](const SymEntry& a, const SymEntry& b) {
+    return a.row != b.row ? a.row < b.row : (a.col != b.col ? a.col < b.col : a.con < b.con);
+  });
+  rp.assign(n + 1, 0);
+  for (const auto& e : ent) rp[e.row + 1]++;
+  for (int64_t j = 0; j < n; ++j) rp[j + 1] += rp[j];
+  col.resize(ent.size());
+  con.resize(ent.size());
+  val.resize(ent.size());
+  for (size_t k = 0; k < ent.size(); ++k) {
+    col[k] = ent[k].col;
+    con[k] = ent[k].con;
+    val[k] = ent[k].val;
+  }
+}
+
+// assemble the device form of (C, A, b)
+static int assemble(lorads_problem* p) {
+  if (p->assembled) return p->assemble_status;
+  if (!p->has_b) return LORADS_ERR_STATE;
+  if (cudaSetDevice(p->device) != cudaSuccess) return check_cuda(cudaGetLastError());
+  const int64_t n = p->n, m = p->m;
+  if (!p->rank1.empty()) return LORADS_ERR_UNSUPPORTED;
+  // merge duplicate (con,row,col) triplets, then require one entry per constraint
+  std::vector<int64_t> order(p->A_con.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    if (p->A_con[a] != p->A_con[b]) return p->A_con[a] < p->A_con[b];
+    if (p->A_row[a] != p->A_row[b]) return p->A_row[a] < p->A_row[b];
+    return p->A_col[a] < p->A_col[b];
+  });
+  std::vector<int32_t> con_r(m, -1), con_c(m, -1);
+  std::vector<double> con_a(m, 0.0);
+  for (size_t k = 0; k < order.size(); ++k) {
+    const int64_t t = order[k];
+    const int32_t i = p->A_con[t];
+    if (con_r[i] < 0) {
+      con_r[i] = p->A_row[t];
+      con_c[i] = p->A_col[t];
+      con_a[i] = p->A_val[t];
+    } else if (con_r[i] == p->A_row[t] && con_c[i] == p->A_col[t]) {
+      con_a[i] += p->A_val[t];
+    } else {
+      return LORADS_ERR_UNSUPPORTED;   // a constraint with several entries
+    }
+  }
+  for (int64_t i = 0; i < m; ++i)
+    if (con_r[i] < 0 || con_a[i] == 0.0) return LORADS_ERR_UNSUPPORTED;
+  // A as symmetric CSR
+  std::vector<SymEntry> ent;
+  ent.reserve(2 * m);
+  for (int64_t i = 0; i < m; ++i) {
+    ent.push_back({con_r[i], con_c[i], (int32_t)i, con_a[i]});
+    if (con_r[i] != con_c[i]) ent.push_back({con_c[i], con_r[i], (int32_t)i, con_a[i]});
+  }
+  std::vector<int32_t> A_rp, A_col, A_con;
+  std::vector<double> A_val;
+  build_sym_csr(n, ent, A_rp, A_col, A_con, A_val);
+  // C: merge duplicates, both triangles
+  std::vector<SymEntry> cent;
+  {
+    std::vector<int64_t> co(p->C_row.size());
+    std::iota(co.begin(), co.end(), 0);
+    std::sort(co.begin(), co.end(), [&](int64_t a, int64_t b) {
+      return p->C_row[a] != p->C_row[b] ? p->C_row[a] < p->C_row[b] : p->C_col[a] < p->C_col[b];
+    });
+    std::vector<SymEntry> merged;
+    for (int64_t t : co) {
+      if (!merged.empty() && merged.back().row == p->C_row[t] && merged.back().col == p->C_col[t])
+        merged.back().val += p->C_val[t];
+      else
+        merged.push_back({p->C_row[t], p->C_col[t], 0, p->C_val[t]});
+    }
+    for (const auto& e : merged) {
+      if (e.val == 0.0) continue;
+      cent.push_back(e);
+      if (e.row != e.col) cent.push_back({e.col, e.row, 0, e.val});
+    }
+  }
+  std::vector<int32_t> C_rp, C_col, C_dummy;
+  std::vector<double> C_val;
+  build_sym_csr(n, cent, C_rp, C_col, C_dummy, C_val);
+  // norms of the data
+  double cf = 0.0, cinf = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    double rs = 0.0;
+    for (int32_t q = C_rp[j]; q < C_rp[j + 1]; ++q) {
+      cf += C_val[q] * C_val[q];
+      rs += std::fabs(C_val[q]);
+    }
+    cinf = std::max(cinf, rs);
+  }
+  double binf = 0.0;
+  for (double x : p->b) binf = std::max(binf, std::fabs(x));
+  p->C_fro = std::sqrt(cf);
+  p->C_inf = cinf;
+  p->b_inf = binf;
+  // diagonal-separable constraints: U_0 rows can be scaled onto the constraints
+  std::vector<double> row_norm(n, -1.0);
+  bool dsep = true;
+  for (int64_t i = 0; i < m && dsep; ++i) {
+    const double ratio = p->b[i] / con_a[i];
+    if (con_r[i] != con_c[i] || row_norm[con_r[i]] >= 0.0 || !(ratio > 0.0))
+      dsep = false;
+    else
+      row_norm[con_r[i]] = std::sqrt(ratio);
+  }
+  p->diag_separable = dsep;
+  // upload
+  std::vector<float> A_valf(A_val.begin(), A_val.end()), C_valf(C_val.begin(), C_val.end());
+  size_t bytes = Arena::need(m, 4) * 2 + Arena::need(m, 8) * 2 + Arena::need(n + 1, 4) * 2 +
+                 Arena::need(A_col.size(), 4) * 2 + Arena::need(A_val.size(), 8) +
+                 Arena::need(A_val.size(), 4) + Arena::need(C_col.size(), 4) +
+                 Arena::need(C_val.size(), 8) + Arena::need(C_val.size(), 4) +
+                 Arena::need(n, 8) + 4096;
+  int st = p->prob_mem.reserve(bytes);
+  if (st != LORADS_OK) return st;
+  Arena& a = p->prob_mem;
+  auto up = [](void* d, const void* h, size_t b) {
+    return b ? cudaMemcpy(d, h, b, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  DevProblem dp{};
+  dp.n = (int)n;
+  dp.m = (int)m;
+  int* d_con_r = a.take<int>(m);
+  int* d_con_c = a.take<int>(m);
+  double* d_con_a = a.take<double>(m);
+  double* d_b = a.take<double>(m);
+  int* d_A_rp = a.take<int>(n + 1);
+  int* d_A_col = a.take<int>(A_col.size());
+  int* d_A_con = a.take<int>(A_con.size());
+  double* d_A_val = a.take<double>(A_val.size());
+  float* d_A_valf = a.take<float>(A_val.size());
+  int* d_C_rp = a.take<int>(n + 1);
+  int* d_C_col = a.take<int>(C_col.size());
+  double* d_C_val = a.take<double>(C_val.size());
+  float* d_C_valf = a.take<float>(C_val.size());
+  double* d_row_norm = a.take<double>(n);
+  CU(up(d_con_r, con_r.data(), m * 4));
+  CU(up(d_con_c, con_c.data(), m * 4));
+  CU(up(d_con_a, con_a.data(), m * 8));
+  CU(up(d_b, p->b.data(), m * 8));
+  CU(up(d_A_rp, A_rp.data(), (n + 1) * 4));
+  CU(up(d_A_col, A_col.data(), A_col.size() * 4));
+  CU(up(d_A_con, A_con.data(), A_con.size() * 4));
+  CU(up(d_A_val, A_val.data(), A_val.size() * 8));
+  CU(up(d_A_valf, A_valf.data(), A_valf.size() * 4));
+  CU(up(d_C_rp, C_rp.data(), (n + 1) * 4));
+  CU(up(d_C_col, C_col.data(), C_col.size() * 4));
+  CU(up(d_C_val, C_val.data(), C_val.size() * 8));
+  CU(up(d_C_valf, C_valf.data(), C_valf.size() * 4));
+  CU(up(d_row_norm, row_norm.data(), n * 8));
+  dp.con_r = d_con_r;
+  dp.con_c = d_con_c;
+  dp.con_a = d_con_a;
+  dp.b = d_b;
+  dp.A_rp = d_A_rp;
+  dp.A_col = d_A_col;
+  dp.A_con = d_A_con;
+  dp.A_val = d_A_val;
+  dp.A_valf = d_A_valf;
+  dp.C_rp = d_C_rp;
+  dp.C_col = d_C_col;
+  dp.C_val = d_C_val;
+  dp.C_valf = d_C_valf;
+  dp.row_norm = dsep ? d_row_norm : nullptr;
+  dp.b_inf = binf;
+  dp.C_fro = p->C_fro;
+  dp.C_inf = cinf;
+  p->dp = dp;
+  p->assembled = true;
+  p->assemble_status = LORADS_OK;
+  return LORADS_OK;
+}
+
+static int resolve_rank_cap(const lorads_problem* p, const lorads_params* prm) {
+  if (prm->rank_max > 0) return (int)std::min<int64_t>(prm->rank_max, p->n);
+  int64_t c = (int64_t)std::floor(std::sqrt(2.0 * (double)p->m));
+  c = std::min<int64_t>(std::min<int64_t>(c, p->n), 256);
+  return (int)std::max<int64_t>(c, 1);
+}
+
+static int resolve_r0(const lorads_problem* p, const lorads_params* prm, int cap) {
+  int64_t r = prm->r0 > 0 ? prm->r0
+                          : (int64_t)std::ceil(std::log2((double)std::max<int64_t>(p->m, 2)));
+  r = std::min<int64_t>(std::min<int64_t>(r, p->n), cap);
+  return (int)std::max<int64_t>(r, 1);
+}
+
+template <typename T>
+static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s,
+                     lorads_result* res) {
+  const int64_t n = p->n, m = p->m;
+  DevParams dv{};
+  const int cap = resolve_rank_cap(p, prm);
+  dv.rank_cap = cap;
+  dv.r0 = resolve_r0(p, prm, cap);
+  dv.rank_factor = prm->rank_factor;
+  dv.tol = prm->tol;
+  dv.switch_tol = prm->switch_tol >= 0 ? prm->switch_tol : (p->diag_separable ? 1e-2 : 1e-3);
+  dv.h = prm->h >= 0 ? prm->h : (p->diag_separable ? 10.0 : 1.0);
+  dv.rho_max = prm->rho_max;
+  dv.rho_growth = prm->rho_growth;
+  dv.rho_every = std::max(1, prm->rho_every);
+  dv.gamma = prm->gamma_fixed > 0 ? prm->gamma_fixed
+                                  : prm->gamma_scale * (p->C_inf > 0 ? p->C_inf : 1.0);
+  dv.max_admm_iter = prm->max_admm_iter;
+  dv.cg_max_iter = prm->cg_max_iter;
+  dv.cg_rel_tol = prm->cg_rel_tol;
+  dv.cg_abs_floor = prm->cg_abs_floor;
+  dv.lbfgs_mem = std::min(std::max(prm->lbfgs_mem, 1), MAXMEM);
+  dv.inner_max_iter = prm->inner_max_iter;
+  dv.inner_tol_factor = prm->inner_tol_factor;
+  dv.inner_tol_max = prm->inner_tol_max;
+  dv.max_outer = prm->max_outer;
+  dv.sigma_factor = prm->sigma_factor;
+  dv.sigma_decrease = prm->sigma_decrease;
+  dv.new_col_std = prm->new_col_std;
+  dv.seed = prm->seed;
+  dv.phase1 = prm->phase1 ? 1 : 0;
+  dv.r_start = p->start_r;
+  dv.rho0 = p->start_rho > 0 ? p->start_rho : 100.0;
+  dv.time_limit_ns = (long long)(prm->time_limit_s * 1e9);
+  if (!dv.phase1) {
+    if (!p->has_start) return LORADS_ERR_STATE;
+    if (p->start_r > 256) return LORADS_ERR_ARG;
+  }
+  const int rmax = std::max(cap, dv.phase1 ? 0 : p->start_r);
+  const long long ld_cap = round4(rmax);
+  const size_t NS = (size_t)n * ld_cap;
+  const int ring = dv.lbfgs_mem + 1;
+  const bool mixed = sizeof(T) == 4;
+  // state arena
+  int dev_sms = 0;
+  CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
+  size_t bytes = Arena::need(NS, 8) * 7 + Arena::need(NS, sizeof(T)) * (mixed ? 6 : 4) +
+                 Arena::need(m, 8) * 2 + Arena::need(NS * ring, 8) * 2 +
+                 Arena::need(1, sizeof(SolverArgs<T>)) + Arena::need(1, sizeof(SolveOut)) +
+                 Arena::need(1, sizeof(GridCtl)) + Arena::need((size_t)dev_sms * 8 * MAXRED, 8) +
+                 Arena::need(4, 4) + 4096;
+  int st = p->state_mem.reserve(bytes);
+  if (st != LORADS_OK) return st;
+  Arena& a = p->state_mem;
+  SolverArgs<T> h{};
+  h.P = p->dp;
+  h.prm = dv;
+  h.U = a.take<double>(NS);
+  h.V = a.take<double>(NS);
+  if (mixed) {
+    h.Ut = a.take<T>(NS);
+    h.Vt = a.take<T>(NS);
+  } else {
+    h.Ut = reinterpret_cast<T*>(h.U);
+    h.Vt = reinterpret_cast<T*>(h.V);
+  }
+  h.Dl = a.take<T>(NS);
+  h.R = a.take<T>(NS);
+  h.Pd = a.take<T>(NS);
+  h.HP = a.take<T>(NS);
+  h.lam = a.take<double>(m);
+  h.e = a.take<double>(m);
+  h.grad = a.take<double>(NS);
+  h.grad_old = a.take<double>(NS);
+  h.dir = a.take<double>(NS);
+  h.tmp = a.take<double>(NS);
+  h.S = a.take<double>(NS * ring);
+  h.Y = a.take<double>(NS * ring);
+  h.ld_cap = ld_cap;
+  SolverArgs<T>* dargs = a.take<SolverArgs<T>>(1);
+  p->dout = a.take<SolveOut>(1);
+  h.out = p->dout;
+  p->dctl = a.take<GridCtl>(1);
+  p->dpartials = a.take<double>((size_t)dev_sms * 8 * MAXRED);
+  p->dqueue = a.take<int>(4);
+  p->dU = h.U;
+  p->dV = h.V;
+  p->dUh = h.tmp;
+  p->dlam = h.lam;
+  p->has_solution = false;
+  // Phase II start supplied by the caller
+  if (!dv.phase1) {
+    const int r = p->start_r, ld = round4(r);
+    std::vector<double> Upad((size_t)n * ld, 0.0);
+    for (int64_t j = 0; j < n; ++j)
+      for (int c = 0; c < r; ++c) Upad[(size_t)j * ld + c] = p->start_U[(size_t)j * r + c];
+    CU(cudaMemcpyAsync(h.U, Upad.data(), Upad.size() * 8, cudaMemcpyHostToDevice, s));
+    if (!p->start_lam.empty())
+      CU(cudaMemcpyAsync(h.lam, p->start_lam.data(), m * 8, cudaMemcpyHostToDevice, s));
+    else
+      CU(cudaMemsetAsync(h.lam, 0, m * 8, s));
+  }
+  CU(cudaMemcpyAsync(dargs, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(p->dout, 0, sizeof(SolveOut), s));
+  CU(cudaMemsetAsync(p->dctl, 0, sizeof(GridCtl), s));
+  CU(cudaMemsetAsync(p->dqueue, 0, 16, s));
+  // scope: one CTA for small problems, the whole GPU for large ones
+  int grid = prm->grid;
+  if (grid <= 0) grid = (n < 4096) ? 1 : dev_sms;
+  cudaError_t le;
+  if (grid == 1) {
+    le = Launch<T>::solve_block(dargs, 1, p->dqueue, 1, s);
+  } else {
+    int per_sm = 0;
+    CU(Launch<T>::grid_capacity(&per_sm));
+    const int maxg = std::max(1, per_sm) * dev_sms;
+    grid = std::min(std::min(grid, maxg), dev_sms * 8);
+    const long long spin = 50LL * 1000 * 1000;   // ~ a few seconds of polling
+    le = Launch<T>::solve_grid(dargs, p->dctl, p->dpartials, spin, grid, s);
+  }
+  CU(le);
+  SolveOut out{};
+  CU(cudaMemcpyAsync(&out, p->dout, sizeof(out), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  lorads_result r{};
+  r.status = out.status;
+  r.rank = out.rank;
+  r.objective = out.objective;
+  r.dual_objective = out.dual_objective;
+  r.r_P = out.r_P;
+  r.r_P_split = out.r_P_split;
+  r.r_stop = out.r_stop;
+  r.r_D = out.r_D;
+  r.gap = out.gap;
+  r.rho = out.rho;
+  r.gamma = out.gamma;
+  r.sigma = out.sigma;
+  r.admm_iters = out.admm_iters;
+  r.cg_iters = out.cg_iters;
+  r.hessian_applies = out.hess_applies;
+  r.alm_outer = out.alm_outer;
+  r.lbfgs_iters = out.lbfgs_iters;
+  r.rank_growths = out.growths;
+  r.time_phase1_s = out.t_phase1_ns * 1e-9;
+  r.time_phase2_s = out.t_phase2_ns * 1e-9;
+  p->last = r;
+  p->sol_r = out.rank;
+  p->sol_ld = out.ld;
+  p->has_solution = out.ld > 0;
+  if (res) *res = r;
+  return r.status;
+}
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+int lorads_create(int64_t n, int64_t m, lorads_problem** out) {
+  if (!out) return LORADS_ERR_ARG;
+  *out = nullptr;
+  if (n <= 0 || m <= 0 || n > INT32_MAX / 2 || m > INT32_MAX / 2) return LORADS_ERR_ARG;
+  lorads_problem* p = new (std::nothrow) lorads_problem();
+  if (!p) return LORADS_ERR_NOMEM;
+  p->n = n;
+  p->m = m;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return LORADS_ERR_CUDA;
+  }
+  *out = p;
+  return LORADS_OK;
+}
+
+int lorads_set_C(lorads_problem* p, int64_t nnz, const int32_t* row, const int32_t* col,
+                 const double* val) {
+  if (!p || nnz < 0 || (nnz > 0 && (!row || !col || !val))) return LORADS_ERR_ARG;
+  for (int64_t t = 0; t < nnz; ++t)
+    if (row[t] < 0 || col[t] < row[t] || col[t] >= p->n || !is_finite_value(val[t])) return LORADS_ERR_ARG;
+  p->C_row.assign(row, row + nnz);
+  p->C_col.assign(col, col + nnz);
+  p->C_val.assign(val, val + nnz);
+  invalidate(p);
+  return LORADS_OK;
+}
+
+int lorads_add_A_sparse(lorads_problem* p, int64_t nnz, const int32_t* con, const int32_t* row,
+                        const int32_t* col, const double* val) {
+  if (!p || nnz < 0 || (nnz > 0 && (!con || !row || !col || !val))) return LORADS_ERR_ARG;
+  for (int64_t t = 0; t < nnz; ++t)
+    if (con[t] < 0 || con[t] >= p->m || row[t] < 0 || col[t] < row[t] || col[t] >= p->n ||
+        !is_finite_value(val[t]))
+      return LORADS_ERR_ARG;
+  p->A_con.insert(p->A_con.end(), con, con + nnz);
+  p->A_row.insert(p->A_row.end(), row, row + nnz);
+  p->A_col.insert(p->A_col.end(), col, col + nnz);
+  p->A_val.insert(p->A_val.end(), val, val + nnz);
+  invalidate(p);
+  return LORADS_OK;
+}
+
+int lorads_add_A_rank1(lorads_problem* p, int32_t con, int64_t nnz, const int32_t* idx,
+                       const double* a, double scale) {
+  if (!p || con < 0 || con >= p->m || nnz <= 0 || !idx || !a || !is_finite_value(scale))
+    return LORADS_ERR_ARG;
+  for (int64_t t = 0; t < nnz; ++t)
+    if (idx[t] < 0 || idx[t] >= p->n || !is_finite_value(a[t])) return LORADS_ERR_ARG;
+  p->rank1.push_back({con, std::vector<int32_t>(idx, idx + nnz), std::vector<double>(a, a + nnz),
+                      scale});
+  invalidate(p);
+  return LORADS_OK;
+}
+
+int lorads_set_b(lorads_problem* p, const double* b) {
+  if (!p || !b) return LORADS_ERR_ARG;
+  for (int64_t i = 0; i < p->m; ++i)
+    if (!is_finite_value(b[i])) return LORADS_ERR_ARG;
+  p->b.assign(b, b + p->m);
+  p->has_b = true;
+  invalidate(p);
+  return LORADS_OK;
+}
+
+void lorads_default_params(lorads_params* prm) {
+  if (!prm) return;
+  std::memset(prm, 0, sizeof(*prm));
+  prm->r0 = 0;
+  prm->rank_max = 0;
+  prm->rank_factor = 1.5;
+  prm->tol = 1e-6;
+  prm->switch_tol = -1.0;
+  prm->h = -1.0;
+  prm->rho_max = 5000.0;
+  prm->rho_growth = 1.2;
+  prm->rho_every = 5;
+  prm->gamma_scale = 1.0;
+  prm->gamma_fixed = 0.0;
+  prm->max_admm_iter = 5000;
+  prm->cg_max_iter = 1000;
+  prm->cg_rel_tol = 1e-3;
+  prm->cg_abs_floor = 1e-13;
+  prm->lbfgs_mem = 4;
+  prm->inner_max_iter = 300;
+  prm->inner_tol_factor = 10.0;
+  prm->inner_tol_max = 0.1;
+  prm->max_outer = 500;
+  prm->sigma_factor = 2.0;
+  prm->sigma_decrease = 0.25;
+  prm->new_col_std = 1e-2;
+  prm->seed = 1;
+  prm->precision = LORADS_PREC_FP64;
+  prm->phase1 = 1;
+  prm->time_limit_s = 60.0;
+  prm->threads = 0;
+  prm->grid = 0;
+}
+
+int lorads_set_start(lorads_problem* p, int32_t r, const double* U0, const double* lambda0,
+                     double rho0) {
+  if (!p || r <= 0 || r > p->n || !U0) return LORADS_ERR_ARG;
+  for (int64_t t = 0; t < p->n * r; ++t)
+    if (!is_finite_value(U0[t])) return LORADS_ERR_ARG;
+  p->start_r = r;
+  p->start_U.assign(U0, U0 + p->n * r);
+  if (lambda0)
+    p->start_lam.assign(lambda0, lambda0 + p->m);
+  else
+    p->start_lam.clear();
+  p->start_rho = rho0;
+  p->has_start = true;
+  return LORADS_OK;
+}
+
+static int solve_impl(lorads_problem* p, const lorads_params* prm, void* stream,
+                      lorads_result* res) {
+  if (!p) return LORADS_ERR_ARG;
+  lorads_params defaults;
+  if (!prm) {
+    lorads_default_params(&defaults);
+    prm = &defaults;
+  }
+  if (prm->precision != LORADS_PREC_FP64 && prm->precision != LORADS_PREC_MIXED)
+    return LORADS_ERR_ARG;
+  if (!(prm->tol > 0) || prm->max_admm_iter < 1 || prm->cg_max_iter < 1) return LORADS_ERR_ARG;
+  int st = assemble(p);
+  if (st != LORADS_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (prm->precision == LORADS_PREC_MIXED) return run_solve<float>(p, prm, s, res);
+  return run_solve<double>(p, prm, s, res);
+}
+
+int lorads_solve(lorads_problem* p, const lorads_params* prm, void* stream, lorads_result* res) {
+  if (res) std::memset(res, 0, sizeof(*res));
+  const int st = solve_impl(p, prm, stream, res);
+  if (res) res->status = st;
+  return st;
+}
+
+int lorads_get_solution(const lorads_problem* p, double* U, double* V, double* U_hat, double* y,
+                        int32_t* r) {
+  if (!p) return LORADS_ERR_ARG;
+  if (!p->has_solution) return LORADS_ERR_STATE;
+  if (r) *r = p->sol_r;
+  const int rr = p->sol_r, ld = p->sol_ld;
+  const int64_t n = p->n;
+  std::vector<double> buf((size_t)n * ld);
+  auto fetch = [&](const double* d, double* h) -> int {
+    if (!h) return LORADS_OK;
+    if (cudaMemcpy(buf.data(), d, buf.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return check_cuda(cudaGetLastError());
+    for (int64_t j = 0; j < n; ++j)
+      std::memcpy(h + (size_t)j * rr, buf.data() + (size_t)j * ld, rr * 8);
+    return LORADS_OK;
+  };
+  int st;
+  if ((st = fetch(p->dU, U)) != LORADS_OK) return st;
+  if ((st = fetch(p->dV, V)) != LORADS_OK) return st;
+  if ((st = fetch(p->dUh, U_hat)) != LORADS_OK) return st;
+  if (y) {
+    if (cudaMemcpy(y, p->dlam, p->m * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return check_cuda(cudaGetLastError());
+    for (int64_t i = 0; i < p->m; ++i) y[i] = -y[i];
+  }
+  return LORADS_OK;
+}
+
+void lorads_destroy(lorads_problem* p) {
+  if (!p) return;
+  p->prob_mem.release();
+  p->state_mem.release();
+  delete p;
+}
+
+const char* lorads_status_string(int code) {
+  switch (code) {
+    case LORADS_OK: return "ok";
+    case LORADS_ERR_ARG: return "bad argument";
+    case LORADS_ERR_STATE: return "call out of order";
+    case LORADS_ERR_CUDA: return "CUDA runtime error";
+    case LORADS_ERR_NOMEM: return "out of memory";
+    case LORADS_ERR_MAXITER: return "iteration cap reached";
+    case LORADS_ERR_TIMEOUT: return "time limit reached";
+    case LORADS_ERR_NAN: return "NaN or Inf in the iterates";
+    case LORADS_ERR_UNSUPPORTED: return "constraint structure not supported by the device path";
+    case LORADS_ERR_DEVICE: return "device-side wait gave up";
+    default: return "unknown status";
+  }
+}
+
+void lorads_struct_sizes(int64_t* params_bytes, int64_t* result_bytes) {
+  if (params_bytes) *params_bytes = (int64_t)sizeof(lorads_params);
+  if (result_bytes) *result_bytes = (int64_t)sizeof(lorads_result);
+}
+
+// ---- operators -----------------------------------------------------------------------
+static int op_prepare(lorads_problem* p, int32_t prec, int32_t r, int32_t ld) {
+  if (!p || (prec != LORADS_PREC_FP64 && prec != LORADS_PREC_MIXED)) return LORADS_ERR_ARG;
+  if (r <= 0 || ld < r || (ld % 4) != 0 || team_size_for(ld) * KMAX * CHUNK < ld)
+    return LORADS_ERR_ARG;
+  return assemble(p);
+}
+
+static int op_grid(const lorads_problem* p) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  return sms * 8;
+}
+
+int lorads_op_sddmm(lorads_problem* p, int32_t prec, int32_t r, int32_t ld, const void* U,
+                    const void* V, double* q, void* stream) {
+  int st = op_prepare(p, prec, r, ld);
+  if (st != LORADS_OK) return st;
+  if (!U || !V || !q) return LORADS_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (prec == LORADS_PREC_MIXED)
+    return check_cuda(Launch<float>::op_sddmm(p->dp, ld, (const float*)U, (const float*)V, q,
+                                              op_grid(p), s));
+  return check_cuda(Launch<double>::op_sddmm(p->dp, ld, (const double*)U, (const double*)V, q,
+                                             op_grid(p), s));
+}
+
+int lorads_op_spmm(lorads_problem* p, int32_t prec, int32_t r, int32_t ld, const double* w,
+                   double gamma, const void* V, void* out, void* stream) {
+  int st = op_prepare(p, prec, r, ld);
+  if (st != LORADS_OK) return st;
+  if (!w || !V || !out) return LORADS_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (prec == LORADS_PREC_MIXED)
+    return check_cuda(Launch<float>::op_spmm(p->dp, ld, w, gamma, (const float*)V, (float*)out,
+                                             op_grid(p), s));
+  return check_cuda(Launch<double>::op_spmm(p->dp, ld, w, gamma, (const double*)V, (double*)out,
+                                            op_grid(p), s));
+}
+
+int lorads_op_hessian(lorads_problem* p, int32_t prec, int32_t r, int32_t ld, double rho,
+                      double gamma, const void* V, const void* P, void* out, void* stream) {
+  int st = op_prepare(p, prec, r, ld);
+  if (st != LORADS_OK) return st;
+  if (!V || !P || !out) return LORADS_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (prec == LORADS_PREC_MIXED)
+    return check_cuda(Launch<float>::op_hessian(p->dp, ld, rho, gamma, (const float*)V,
+                                                (const float*)P, (float*)out, op_grid(p), s));
+  return check_cuda(Launch<double>::op_hessian(p->dp, ld, rho, gamma, (const double*)V,
+                                               (const double*)P, (double*)out, op_grid(p), s));
+}
+
+}  // extern "C"

@@ -1,0 +1,427 @@
+// Device building blocks of the LoRADS solver (sm_103a).
+//
+// Layout
+//   * Factors are row-major n x ld, ld = 4 * ceil(r / 4); padding columns are kept at 0.
+//   * A row is processed by a "team" of G lanes (G a power of two <= 32, aligned inside a
+//     warp).  Lane l of a team owns the 4-element chunks c = l, l + G, ... (at most KMAX),
+//     loaded as 128-bit accesses (float4, or two double2 for FP64).
+//   * Every constraint of the device path is a single symmetric entry a (E_rc + E_cr) or
+//     a E_rr (MaxCut: A_i = e_i e_i^T, Section 5.3; matrix completion: Section 5.4).  The
+//     entries are kept twice: in constraint order (con_r, con_c, con_a) for the dual step,
+//     and as a symmetric CSR over rows (both triangles) that carries the constraint id, for
+//     the sparse-times-dense products.
+//   * Reductions are deterministic: fixed shuffle trees inside warps, warps summed in order,
+//     CTAs summed in order by the last CTA to arrive at the grid barrier.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lorads {
+
+constexpr int KMAX = 2;      // chunks per lane
+constexpr int CHUNK = 4;     // elements per chunk (16 B of float, 32 B of double)
+constexpr int MAXRED = 12;   // values per reduction
+constexpr int MAXMEM = 8;    // L-BFGS memory cap
+
+// ------------------------------------------------------------------------------------
+// problem view
+// ------------------------------------------------------------------------------------
+struct DevProblem {
+  int n, m;
+  // constraints in constraint order (single symmetric entry each)
+  const int* con_r;
+  const int* con_c;
+  const double* con_a;
+  const double* b;
+  // A as symmetric CSR over rows; entry e of row j: column A_col[e], constraint A_con[e]
+  const int* A_rp;
+  const int* A_col;
+  const int* A_con;
+  const double* A_val;
+  const float* A_valf;
+  // C as symmetric CSR over rows
+  const int* C_rp;
+  const int* C_col;
+  const double* C_val;
+  const float* C_valf;
+  // row scaling of U_0 onto diagonal constraints (NULL unless every constraint is a single
+  // diagonal entry on its own row with b/a > 0): U_0 row j gets norm row_norm[j] (< 0: keep)
+  const double* row_norm;
+  double b_inf, C_fro, C_inf;
+};
+
+template <typename T> __device__ __forceinline__ const T* cval(const DevProblem& P);
+template <> __device__ __forceinline__ const double* cval<double>(const DevProblem& P) { return P.C_val; }
+template <> __device__ __forceinline__ const float* cval<float>(const DevProblem& P) { return P.C_valf; }
+template <typename T> __device__ __forceinline__ const T* aval(const DevProblem& P);
+template <> __device__ __forceinline__ const double* aval<double>(const DevProblem& P) { return P.A_val; }
+template <> __device__ __forceinline__ const float* aval<float>(const DevProblem& P) { return P.A_valf; }
+
+// ------------------------------------------------------------------------------------
+// teams and fragments
+// ------------------------------------------------------------------------------------
+struct Team {
+  int G;          // lanes per row
+  int lane;       // lane inside the team
+  int id;         // team index inside the scope
+  int count;      // teams in the scope
+  int nc;         // chunks per row (ld / 4)
+  unsigned mask;  // shuffle mask of the team's lanes
+};
+
+__host__ __device__ inline int team_size_for(int ld) {
+  int nc = ld / CHUNK;
+  int need = (nc + KMAX - 1) / KMAX;
+  int G = 1;
+  while (G < need) G <<= 1;
+  return G > 32 ? 32 : G;
+}
+
+__device__ inline Team make_team(int ld, int tid, int nthreads) {
+  Team t;
+  t.G = team_size_for(ld);
+  t.lane = tid & (t.G - 1);
+  t.id = tid / t.G;
+  t.count = nthreads / t.G;
+  t.nc = ld / CHUNK;
+  int wl = threadIdx.x & 31;
+  int base = wl & ~(t.G - 1);
+  t.mask = (t.G == 32) ? 0xffffffffu : (((1u << t.G) - 1u) << base);
+  return t;
+}
+
+template <typename T>
+struct Frag {
+  T v[KMAX][CHUNK];
+};
+
+template <typename T> __device__ __forceinline__ void load4(const T* p, T* o);
+template <> __device__ __forceinline__ void load4<float>(const float* p, float* o) {
+  float4 x = *reinterpret_cast<const float4*>(p);
+  o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+}
+template <> __device__ __forceinline__ void load4<double>(const double* p, double* o) {
+  double2 x = reinterpret_cast<const double2*>(p)[0];
+  double2 y = reinterpret_cast<const double2*>(p)[1];
+  o[0] = x.x; o[1] = x.y; o[2] = y.x; o[3] = y.y;
+}
+template <typename T> __device__ __forceinline__ void store4(T* p, const T* o);
+template <> __device__ __forceinline__ void store4<float>(float* p, const float* o) {
+  *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+template <> __device__ __forceinline__ void store4<double>(double* p, const double* o) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
+}
+
+template <typename T>
+__device__ __forceinline__ void frag_zero(Frag<T>& f) {
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+    for (int e = 0; e < CHUNK; ++e) f.v[k][e] = T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void frag_load(Frag<T>& f, const T* base, long long row, int ld,
+                                          const Team& t) {
+  const T* p = base + row * (long long)ld;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    int c = t.lane + k * t.G;
+    if (c < t.nc) {
+      load4<T>(p + c * CHUNK, f.v[k]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < CHUNK; ++e) f.v[k][e] = T(0);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void frag_store(const Frag<T>& f, T* base, long long row, int ld,
+                                           const Team& t) {
+  T* p = base + row * (long long)ld;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    int c = t.lane + k * t.G;
+    if (c < t.nc) store4<T>(p + c * CHUNK, f.v[k]);
+  }
+}
+
+// convert between element types (FP64 master <-> FP32 shadow)
+template <typename D, typename S>
+__device__ __forceinline__ void frag_convert(Frag<D>& d, const Frag<S>& s) {
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+    for (int e = 0; e < CHUNK; ++e) d.v[k][e] = D(s.v[k][e]);
+}
+
+// lane-local partial dot product, accumulated in T
+template <typename T>
+__device__ __forceinline__ T frag_dot_local(const Frag<T>& a, const Frag<T>& b) {
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+    for (int e = 0; e < CHUNK; ++e) s = fma(a.v[k][e], b.v[k][e], s);
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T team_sum(T x, const Team& t) {
+  for (int off = t.G >> 1; off > 0; off >>= 1) x += __shfl_xor_sync(t.mask, x, off);
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T frag_dot(const Frag<T>& a, const Frag<T>& b, const Team& t) {
+  return team_sum(frag_dot_local(a, b), t);
+}
+
+// y += alpha x
+template <typename T>
+__device__ __forceinline__ void frag_axpy(Frag<T>& y, T alpha, const Frag<T>& x) {
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+    for (int e = 0; e < CHUNK; ++e) y.v[k][e] = fma(alpha, x.v[k][e], y.v[k][e]);
+}
+
+// ------------------------------------------------------------------------------------
+// counter-based random numbers: SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) and the
+// Box-Muller transform (Box and Muller, 1958)
+// ------------------------------------------------------------------------------------
+__host__ __device__ inline uint64_t splitmix64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+// output i (0-based) of the SplitMix64 stream seeded with key
+__host__ __device__ inline uint64_t splitmix64_at(uint64_t key, uint64_t i) {
+  return splitmix64_mix(key + (i + 1ULL) * 0x9E3779B97F4A7C15ULL);
+}
+// key of sub-stream s: 0 draws U_0, g >= 1 draws the columns of the g-th rank growth
+__host__ __device__ inline uint64_t stream_key(uint64_t seed, uint64_t s) {
+  return splitmix64_at(seed, s);
+}
+__device__ inline double uniform_open01(uint64_t key, uint64_t i) {
+  return ((double)(splitmix64_at(key, i) >> 11) + 0.5) * 0x1.0p-53;
+}
+// standard normal number e of the stream: outputs 2e and 2e+1
+__device__ inline double normal_at(uint64_t key, uint64_t e) {
+  double u1 = uniform_open01(key, 2 * e);
+  double u2 = uniform_open01(key, 2 * e + 1);
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// ------------------------------------------------------------------------------------
+// scopes: one CTA, or the whole grid of a cooperative launch
+// ------------------------------------------------------------------------------------
+struct GridCtl {
+  unsigned int count;
+  unsigned int gen;
+  int error;
+  int pad;
+  double result[MAXRED];
+};
+
+// deterministic CTA-wide sum of k values; every thread receives the sums in v
+__device__ inline void block_reduce(double* v, int k, double* red /* smem [33*MAXRED] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int i = 0; i < k; ++i) {
+    double x = v[i];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[warp * MAXRED + i] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int i = 0; i < k; ++i) {
+      double x = lane < nw ? red[lane * MAXRED + i] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      if (lane == 0) red[32 * MAXRED + i] = x;
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < k; ++i) v[i] = red[32 * MAXRED + i];
+}
+
+struct BlockScope {
+  double* red;
+  __device__ int tid() const { return threadIdx.x; }
+  __device__ int nthreads() const { return blockDim.x; }
+  __device__ bool sync() {
+    __syncthreads();
+    return true;
+  }
+  __device__ bool reduce(double* v, int k) {
+    block_reduce(v, k, red);
+    return true;
+  }
+  __device__ bool is_leader() const { return threadIdx.x == 0; }
+};
+
+struct GridScope {
+  double* red;             // shared memory
+  GridCtl* ctl;            // zeroed before launch
+  double* partials;        // gridDim.x * MAXRED
+  long long spin_limit;    // polls before a barrier gives up
+
+  __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+  __device__ int nthreads() const { return gridDim.x * blockDim.x; }
+  __device__ bool is_leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+
+  // bounded barrier over all CTAs; with k > 0 it also sums v (already CTA-reduced and
+  // stored in red[32*MAXRED + i]) over CTAs in CTA order.
+  __device__ bool barrier(int k) {
+    volatile GridCtl* vc = ctl;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      unsigned my_gen = 0;
+      int last = 0;
+      if (lane == 0) {
+        for (int i = 0; i < k; ++i) partials[blockIdx.x * MAXRED + i] = red[32 * MAXRED + i];
+        my_gen = vc->gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(&ctl->count, 1u);
+        last = (arrived == gridDim.x - 1);
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last) {
+        __threadfence();
+        volatile double* vp = partials;
+        for (int i = 0; i < k; ++i) {
+          double x = 0.0;
+          for (int b = lane; b < (int)gridDim.x; b += 32) x += vp[b * MAXRED + i];
+          for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+          if (lane == 0) vc->result[i] = x;
+        }
+        if (lane == 0) {
+          vc->count = 0;
+          __threadfence();
+          atomicAdd(&ctl->gen, 1u);
+        }
+      } else if (lane == 0) {
+        long long it = 0;
+        while (vc->gen == my_gen) {
+          if (vc->error) break;
+          if (++it > spin_limit) {
+            atomicExch(&ctl->error, 1);
+            break;
+          }
+          __nanosleep(40);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence();
+        for (int i = 0; i < k; ++i) red[32 * MAXRED + i] = vc->result[i];
+      }
+    }
+    __syncthreads();
+    return vc->error == 0;
+  }
+
+  __device__ bool sync() {
+    __syncthreads();
+    return barrier(0);
+  }
+  __device__ bool reduce(double* v, int k) {
+    block_reduce(v, k, red);   // leaves CTA sums in red[32*MAXRED + i]
+    bool ok = barrier(k);
+    for (int i = 0; i < k; ++i) v[i] = red[32 * MAXRED + i];
+    return ok;
+  }
+};
+
+// ------------------------------------------------------------------------------------
+// per-row operators (shared by the solver and the operator entry points)
+// ------------------------------------------------------------------------------------
+
+// Hessian of eq. linU on row j with fixed factor W:
+//   (H P)_j = rho * sum_{entries (j,k) of A_i} a q_i W_k + gamma P_j,
+//   q_i = <A_i, P W^T> = a (P_j . W_k + P_k . W_j)   (off-diagonal)   or   a P_j . W_j.
+// Returns the row in out; Pj is loaded by the caller (it is also needed for p.Hp).
+template <typename T>
+__device__ __forceinline__ void hessian_row(const DevProblem& P, const T* Wm, const T* Pm,
+                                            int ld, int j, const Frag<T>& Pj, T rho, T gamma,
+                                            const Team& t, Frag<T>& out) {
+  Frag<T> Wj, acc;
+  frag_load(Wj, Wm, j, ld, t);
+  frag_zero(acc);
+  const T* av = aval<T>(P);
+  const int e0 = P.A_rp[j], e1 = P.A_rp[j + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int k = P.A_col[e];
+    const T a = av[e];
+    if (k == j) {
+      T q = a * frag_dot(Pj, Wj, t);
+      frag_axpy(acc, a * q, Wj);
+    } else {
+      Frag<T> Wk, Pk;
+      frag_load(Wk, Wm, k, ld, t);
+      frag_load(Pk, Pm, k, ld, t);
+      T q = a * team_sum(frag_dot_local(Pj, Wk) + frag_dot_local(Pk, Wj), t);
+      frag_axpy(acc, a * q, Wk);
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+    for (int ee = 0; ee < CHUNK; ++ee) out.v[kk][ee] = fma(rho, acc.v[kk][ee], gamma * Pj.v[kk][ee]);
+}
+
+// (A^T(w) - C) W on row j, w_i = wb * b_i + wl * lambda_i + we * e_i (e may be NULL),
+// plus gamma W_j.  All in T.
+template <typename T>
+__device__ __forceinline__ void spmm_row(const DevProblem& P, const T* Wm, int ld, int j,
+                                         const double* lam, const double* e, double wb, double wl,
+                                         double we, T gamma, const Team& t, Frag<T>& out) {
+  Frag<T> acc;
+  frag_zero(acc);
+  const T* cv = cval<T>(P);
+  for (int q = P.C_rp[j]; q < P.C_rp[j + 1]; ++q) {
+    Frag<T> Wk;
+    frag_load(Wk, Wm, P.C_col[q], ld, t);
+    frag_axpy(acc, -cv[q], Wk);
+  }
+  const T* av = aval<T>(P);
+  const bool a_part = (wb != 0.0) || (lam != nullptr) || (e != nullptr);
+  for (int q = a_part ? P.A_rp[j] : 0; q < (a_part ? P.A_rp[j + 1] : 0); ++q) {
+    const int i = P.A_con[q];
+    double w = wb * P.b[i];
+    if (lam) w += wl * lam[i];
+    if (e) w += we * e[i];
+    Frag<T> Wk;
+    frag_load(Wk, Wm, P.A_col[q], ld, t);
+    frag_axpy(acc, (T)(w * (double)av[q]), Wk);
+  }
+  if (gamma != T(0)) {
+    Frag<T> Wj;
+    frag_load(Wj, Wm, j, ld, t);
+    frag_axpy(acc, gamma, Wj);
+  }
+  out = acc;
+}
+
+// <A_i, U V^T> for single-entry constraint i (team-cooperative)
+template <typename T>
+__device__ __forceinline__ double sddmm_con(const DevProblem& P, const T* Um, const T* Vm, int ld,
+                                            int i, const Team& t) {
+  const int r = P.con_r[i], c = P.con_c[i];
+  const double a = P.con_a[i];
+  Frag<T> Ur, Vc;
+  frag_load(Ur, Um, r, ld, t);
+  frag_load(Vc, Vm, c, ld, t);
+  T loc = frag_dot_local(Ur, Vc);
+  if (r != c) {
+    Frag<T> Uc, Vr;
+    frag_load(Uc, Um, c, ld, t);
+    frag_load(Vr, Vm, r, ld, t);
+    loc += frag_dot_local(Uc, Vr);
+  }
+  return a * (double)team_sum(loc, t);
+}
+
+}  // namespace lorads

@@ -1,0 +1,145 @@
+// Kernel entry points of the solver and of the operator calls, instantiated per element
+// type by lorads_f64.cu / lorads_f32.cu.
+#pragma once
+#include "lorads_solver.cuh"
+
+namespace lorads {
+
+constexpr int SOLVER_THREADS = 256;
+
+// one CTA per problem; CTAs take problems from a queue (batches), or a single problem
+template <typename T>
+__global__ void __launch_bounds__(SOLVER_THREADS)
+solve_block_kernel(const SolverArgs<T>* args, int count, int* queue) {
+  __shared__ double red[33 * MAXRED];
+  __shared__ SolverArgs<T> sa;
+  __shared__ int inst;
+  for (;;) {
+    if (threadIdx.x == 0) inst = atomicAdd(queue, 1);
+    __syncthreads();
+    const int i = inst;
+    if (i >= count) return;
+    if (threadIdx.x == 0) sa = args[i];
+    __syncthreads();
+    BlockScope sc{red};
+    run_solver<T>(sa, sc);
+    __syncthreads();
+  }
+}
+
+// one problem over the whole grid (cooperative launch: all CTAs co-resident)
+template <typename T>
+__global__ void __launch_bounds__(SOLVER_THREADS)
+solve_grid_kernel(const SolverArgs<T>* args, GridCtl* ctl, double* partials, long long spin) {
+  __shared__ double red[33 * MAXRED];
+  __shared__ SolverArgs<T> sa;
+  if (threadIdx.x == 0) sa = *args;
+  __syncthreads();
+  GridScope sc{red, ctl, partials, spin};
+  run_solver<T>(sa, sc);
+}
+
+// ---- operators on caller-owned device arrays ----
+template <typename T>
+__global__ void op_sddmm_kernel(DevProblem P, int ld, const T* U, const T* V, double* q) {
+  const Team t = make_team(ld, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  for (int i = t.id; i < P.m; i += t.count) {
+    const double v = sddmm_con<T>(P, U, V, ld, i, t);
+    if (t.lane == 0) q[i] = v;
+  }
+}
+
+template <typename T>
+__global__ void op_spmm_kernel(DevProblem P, int ld, const double* w, double gamma, const T* V,
+                               T* out) {
+  const Team t = make_team(ld, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  for (int j = t.id; j < P.n; j += t.count) {
+    Frag<T> o;
+    spmm_row<T>(P, V, ld, j, w, nullptr, 0.0, 1.0, 0.0, (T)gamma, t, o);
+    frag_store(o, out, j, ld, t);
+  }
+}
+
+template <typename T>
+__global__ void op_hessian_kernel(DevProblem P, int ld, T rho, T gamma, const T* V, const T* Pm,
+                                  T* out) {
+  const Team t = make_team(ld, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  for (int j = t.id; j < P.n; j += t.count) {
+    Frag<T> Pj, H;
+    frag_load(Pj, Pm, j, ld, t);
+    hessian_row<T>(P, V, Pm, ld, j, Pj, rho, gamma, t, H);
+    frag_store(H, out, j, ld, t);
+  }
+}
+
+// host-side launchers (defined in the per-type translation units)
+template <typename T>
+struct Launch {
+  static cudaError_t solve_block(const SolverArgs<T>* args, int count, int* queue, int grid,
+                                 cudaStream_t s);
+  static cudaError_t solve_grid(const SolverArgs<T>* args, GridCtl* ctl, double* partials,
+                                long long spin, int grid, cudaStream_t s);
+  static cudaError_t grid_capacity(int* blocks_per_sm);
+  static cudaError_t op_sddmm(const DevProblem& P, int ld, const T* U, const T* V, double* q,
+                              int grid, cudaStream_t s);
+  static cudaError_t op_spmm(const DevProblem& P, int ld, const double* w, double gamma,
+                             const T* V, T* out, int grid, cudaStream_t s);
+  static cudaError_t op_hessian(const DevProblem& P, int ld, double rho, double gamma, const T* V,
+                                const T* Pm, T* out, int grid, cudaStream_t s);
+};
+
+#define LORADS_DECLARE_LAUNCH(T)                                                               \
+  template <> cudaError_t Launch<T>::solve_block(const SolverArgs<T>*, int, int*, int,          \
+                                                 cudaStream_t);                                 \
+  template <> cudaError_t Launch<T>::solve_grid(const SolverArgs<T>*, GridCtl*, double*,        \
+                                                long long, int, cudaStream_t);                  \
+  template <> cudaError_t Launch<T>::grid_capacity(int*);                                       \
+  template <> cudaError_t Launch<T>::op_sddmm(const DevProblem&, int, const T*, const T*,      \
+                                              double*, int, cudaStream_t);                      \
+  template <> cudaError_t Launch<T>::op_spmm(const DevProblem&, int, const double*, double,    \
+                                             const T*, T*, int, cudaStream_t);                  \
+  template <> cudaError_t Launch<T>::op_hessian(const DevProblem&, int, double, double,        \
+                                                const T*, const T*, T*, int, cudaStream_t);
+LORADS_DECLARE_LAUNCH(double)
+LORADS_DECLARE_LAUNCH(float)
+
+#define LORADS_DEFINE_LAUNCH(T)                                                                \
+  template <>                                                                                  \
+  cudaError_t Launch<T>::solve_block(const SolverArgs<T>* args, int count, int* queue, int grid,\
+                                     cudaStream_t s) {                                         \
+    solve_block_kernel<T><<<grid, SOLVER_THREADS, 0, s>>>(args, count, queue);                 \
+    return cudaGetLastError();                                                                 \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t Launch<T>::solve_grid(const SolverArgs<T>* args, GridCtl* ctl, double* partials, \
+                                    long long spin, int grid, cudaStream_t s) {                \
+    void* kargs[] = {(void*)&args, (void*)&ctl, (void*)&partials, (void*)&spin};               \
+    return cudaLaunchCooperativeKernel((const void*)solve_grid_kernel<T>, dim3(grid),          \
+                                       dim3(SOLVER_THREADS), kargs, 0, s);                     \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t Launch<T>::grid_capacity(int* blocks_per_sm) {                                   \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_grid_kernel<T>,  \
+                                                         SOLVER_THREADS, 0);                   \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t Launch<T>::op_sddmm(const DevProblem& P, int ld, const T* U, const T* V,         \
+                                  double* q, int grid, cudaStream_t s) {                       \
+    op_sddmm_kernel<T><<<grid, 256, 0, s>>>(P, ld, U, V, q);                                   \
+    return cudaGetLastError();                                                                 \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t Launch<T>::op_spmm(const DevProblem& P, int ld, const double* w, double gamma,   \
+                                 const T* V, T* out, int grid, cudaStream_t s) {               \
+    op_spmm_kernel<T><<<grid, 256, 0, s>>>(P, ld, w, gamma, V, out);                           \
+    return cudaGetLastError();                                                                 \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t Launch<T>::op_hessian(const DevProblem& P, int ld, double rho, double gamma,     \
+                                    const T* V, const T* Pm, T* out, int grid,                 \
+                                    cudaStream_t s) {                                          \
+    op_hessian_kernel<T><<<grid, 256, 0, s>>>(P, ld, (T)rho, (T)gamma, V, Pm, out);            \
+    return cudaGetLastError();                                                                 \
+  }
+
+}  // namespace lorads

@@ -1,0 +1,869 @@
+// Persistent device solver for LoRADS (Algorithm 2).
+//
+// The whole method runs inside one launch: Phase I (augmented Lagrangian on the BM
+// problem, L-BFGS with exact quartic line search, dynamic rank), the switch, Phase II
+// (Algorithm 1 with warm-started CG on eq. linU / eq. linV, dual step, penalty schedule)
+// and the output step U_hat = (U + V)/2 with its residuals.  It is written once against a
+// "scope": one CTA (BlockScope: small problems and batches, one CTA per problem) or the
+// whole grid of a cooperative launch (GridScope: one large problem).  Every scalar decision
+// is taken redundantly by all threads from reduced values, so control flow is uniform.
+//
+// Precision: T is the element type of the CG operators and vectors (double: plain FP64,
+// float: mixed form).  The masters U, V, lambda, the CG scalars alpha/beta, all residual
+// norms and the objective stay FP64; the CG of each subproblem solves for the correction
+// delta of H delta = R_0, R_0 = G - H X_0 formed in FP64 from the warm start X_0.
+#pragma once
+#include "lorads_device.cuh"
+
+namespace lorads {
+
+struct DevParams {
+  int r0, rank_cap;
+  double rank_factor;
+  double tol, switch_tol, h, rho_max, rho_growth;
+  int rho_every;
+  double gamma;
+  int max_admm_iter, cg_max_iter;
+  double cg_rel_tol, cg_abs_floor;
+  int lbfgs_mem, inner_max_iter;
+  double inner_tol_factor, inner_tol_max;
+  int max_outer;
+  double sigma_factor, sigma_decrease, new_col_std;
+  unsigned long long seed;
+  int phase1;
+  int r_start;
+  double rho0;
+  long long time_limit_ns;
+};
+
+struct SolveOut {
+  int status, rank, ld, admm_iters, cg_iters, hess_applies, alm_outer, lbfgs_iters, growths;
+  int pad;
+  double objective, dual_objective, r_P, r_P_split, r_stop, r_D, gap, rho, gamma, sigma;
+  long long t_phase1_ns, t_phase2_ns;
+};
+
+// status values written to SolveOut (mirror the public codes)
+enum { ST_OK = 0, ST_MAXITER = -5, ST_TIMEOUT = -6, ST_NAN = -7, ST_DEVICE = -9 };
+
+template <typename T>
+struct SolverArgs {
+  DevProblem P;
+  DevParams prm;
+  double* U;      // masters, capacity n * ld_cap
+  double* V;
+  T* Ut;          // shadows of U, V in T (alias U, V when T is double)
+  T* Vt;
+  T* Dl;          // CG correction delta
+  T* R;
+  T* Pd;
+  T* HP;
+  double* lam;    // m
+  double* e;      // m
+  double* grad;   // n * ld_cap (Phase I)
+  double* grad_old;
+  double* dir;
+  double* S;      // lbfgs_mem * n * ld_cap
+  double* Y;
+  double* tmp;    // n * ld_cap (rank growth, U_hat)
+  long long ld_cap;
+  SolveOut* out;
+};
+
+__device__ inline long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (long long)t;
+}
+
+__host__ __device__ inline int round4(int r) { return (r + 3) & ~3; }
+
+// real roots of c3 t^3 + c2 t^2 + c1 t + c0 (c3 != 0) by the trigonometric / Cardano
+// formulas, each polished by two Newton steps; returns the count
+__device__ inline int cubic_roots(double c3, double c2, double c1, double c0, double* x) {
+  const double B = c2 / c3, C = c1 / c3, D = c0 / c3;
+  const double p = C - B * B / 3.0;
+  const double q = 2.0 * B * B * B / 27.0 - B * C / 3.0 + D;
+  const double disc = 0.25 * q * q + p * p * p / 27.0;
+  int k = 0;
+  if (disc > 0.0) {
+    const double s = sqrt(disc);
+    x[k++] = cbrt(-0.5 * q + s) + cbrt(-0.5 * q - s) - B / 3.0;
+  } else if (p == 0.0) {
+    x[k++] = -B / 3.0;
+  } else {
+    const double m = 2.0 * sqrt(-p / 3.0);
+    double arg = 3.0 * q / (p * m);
+    arg = fmin(1.0, fmax(-1.0, arg));
+    const double th = acos(arg) / 3.0;
+    for (int j = 0; j < 3; ++j) x[k++] = m * cos(th - 2.0 * M_PI * j / 3.0) - B / 3.0;
+  }
+  for (int j = 0; j < k; ++j) {
+    for (int it = 0; it < 2; ++it) {
+      const double t = x[j];
+      const double f = ((t + B) * t + C) * t + D;
+      const double df = (3.0 * t + 2.0 * B) * t + C;
+      if (df != 0.0) x[j] = t - f / df;
+    }
+  }
+  return k;
+}
+
+// argmin over t > 0 of a1 t + a2 t^2 + a3 t^3 + a4 t^4; 0 when nothing decreases
+__device__ inline double quartic_step(double a1, double a2, double a3, double a4) {
+  double roots[3];
+  int k = 0;
+  if (a4 != 0.0) {
+    k = cubic_roots(4.0 * a4, 3.0 * a3, 2.0 * a2, a1, roots);
+  } else if (a3 != 0.0) {
+    const double A = 3.0 * a3, Bq = 2.0 * a2, Cq = a1;
+    const double d = Bq * Bq - 4.0 * A * Cq;
+    if (d >= 0.0) {
+      roots[k++] = (-Bq + sqrt(d)) / (2.0 * A);
+      roots[k++] = (-Bq - sqrt(d)) / (2.0 * A);
+    }
+  } else if (a2 != 0.0) {
+    roots[k++] = -a1 / (2.0 * a2);
+  }
+  double best = 0.0, fbest = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double t = roots[j];
+    if (!(t > 0.0)) continue;
+    const double f = (((a4 * t + a3) * t + a2) * t + a1) * t;
+    if (f < fbest) {
+      fbest = f;
+      best = t;
+    }
+  }
+  return best;
+}
+
+template <typename T, class Scope>
+struct Solver {
+  const SolverArgs<T>& A;
+  Scope& sc;
+  const DevProblem& P;
+  const DevParams& prm;
+  int n, m, r, ld;
+  Team tm;
+  Team tmc;  // team geometry for constraint loops (same as tm)
+  long long t_start;
+  int status;
+  // counters
+  int cg_iters, hess, admm_iters, alm_outer, lbfgs_iters, growths;
+  double last_rs;
+
+  __device__ Solver(const SolverArgs<T>& a, Scope& s)
+      : A(a), sc(s), P(a.P), prm(a.prm), n(a.P.n), m(a.P.m), r(0), ld(0), status(ST_OK),
+        cg_iters(0), hess(0), admm_iters(0), alm_outer(0), lbfgs_iters(0), growths(0),
+        last_rs(0.0) {}
+
+  __device__ void set_rank(int rr) {
+    r = rr;
+    ld = round4(rr);
+    tm = make_team(ld, sc.tid(), sc.nthreads());
+    tmc = tm;
+  }
+
+  // ----------------------------------------------------------------------------------
+  // Phase I pieces (FP64)
+  // ----------------------------------------------------------------------------------
+  __device__ void init_factor() {
+    const uint64_t key = stream_key(prm.seed, 0);
+    const double inv = 1.0 / sqrt((double)r);
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> f;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) {
+          const int c = (tm.lane + k * tm.G) * CHUNK + e;
+          f.v[k][e] = (c < r) ? normal_at(key, (uint64_t)j * r + c) * inv : 0.0;
+        }
+      if (P.row_norm != nullptr && P.row_norm[j] > 0.0) {
+        const double nr = sqrt(frag_dot(f, f, tm));
+        const double s = P.row_norm[j] / nr;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+          for (int e = 0; e < CHUNK; ++e) f.v[k][e] *= s;
+      }
+      frag_store(f, A.U, j, ld, tm);
+    }
+  }
+
+  // e = A(U U^T) - b (stored), returns ||e||^2 and <lambda, e> via red
+  __device__ bool eval_residual_UU(double& e2) {
+    double v[1] = {0.0};
+    for (int i = tmc.id; i < m; i += tmc.count) {
+      const double q = sddmm_con<double>(P, A.U, A.U, ld, i, tmc);
+      const double ei = q - P.b[i];
+      if (tmc.lane == 0) {
+        A.e[i] = ei;
+        v[0] += ei * ei;
+      }
+    }
+    if (!sc.reduce(v, 1)) return false;
+    e2 = v[0];
+    return true;
+  }
+
+  // grad = 2 (C + A^T(lambda + sigma e)) U, returns ||grad||_F^2
+  __device__ bool eval_grad(double sigma, double& g2) {
+    double v[1] = {0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> out;
+      spmm_row<double>(P, A.U, ld, j, A.lam, A.e, 0.0, -1.0, -sigma, 0.0, tm, out);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) out.v[k][e] *= -2.0;
+      frag_store(out, A.grad, j, ld, tm);
+      const double d = frag_dot(out, out, tm);
+      if (tm.lane == 0) v[0] += d;
+    }
+    if (!sc.reduce(v, 1)) return false;
+    g2 = v[0];
+    return true;
+  }
+
+  // L-BFGS two-loop recursion (Nocedal and Wright, Algorithm 7.4), passes fused with the
+  // dot products they feed.  dir <- -H grad; returns <dir, grad>.  The pairs live in a
+  // ring of lbfgs_mem + 1 slots: the cnt kept pairs end at head - 1 and slot head is free,
+  // so a rejected candidate pair never overwrites a kept one.
+  __device__ bool lbfgs_direction(int cnt, int head, const double* hrho, double H0,
+                                  double& dg) {
+    const int mem = prm.lbfgs_mem + 1;
+    const long long NS = (long long)n * A.ld_cap;
+    double alpha[MAXMEM + 1], beta_prev = 0.0;
+    if (cnt == 0) {
+      double v[1] = {0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> g;
+        frag_load(g, A.grad, j, ld, tm);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+          for (int e = 0; e < CHUNK; ++e) g.v[k][e] = -g.v[k][e];
+        frag_store(g, A.dir, j, ld, tm);
+        const double d = frag_dot(g, g, tm);
+        if (tm.lane == 0) v[0] -= d;
+      }
+      if (!sc.reduce(v, 1)) return false;
+      dg = v[0];
+      return true;
+    }
+    // loop 1: newest -> oldest
+    for (int i = 0; i < cnt; ++i) {
+      const int slot = (head - 1 - i + 2 * mem) % mem;
+      const int prev = (head - i + 2 * mem) % mem;   // slot of pair i-1
+      double v[1] = {0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> q, s;
+        if (i == 0) {
+          frag_load(q, A.grad, j, ld, tm);
+        } else {
+          Frag<double> y;
+          frag_load(q, A.dir, j, ld, tm);
+          frag_load(y, A.Y + prev * NS, j, ld, tm);
+          frag_axpy(q, -alpha[i - 1], y);
+        }
+        frag_store(q, A.dir, j, ld, tm);
+        frag_load(s, A.S + slot * NS, j, ld, tm);
+        const double d = frag_dot(s, q, tm);
+        if (tm.lane == 0) v[0] += d;
+      }
+      if (!sc.reduce(v, 1)) return false;
+      alpha[i] = hrho[slot] * v[0];
+    }
+    // loop 2: oldest -> newest, starting from H0 (q - alpha_last y_last)
+    for (int i = 0; i < cnt; ++i) {
+      const int slot = (head - cnt + i + 2 * mem) % mem;
+      const int ai = cnt - 1 - i;
+      double v[1] = {0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> q;
+        frag_load(q, A.dir, j, ld, tm);
+        if (i == 0) {
+          Frag<double> y;
+          frag_load(y, A.Y + slot * NS, j, ld, tm);
+          frag_axpy(q, -alpha[cnt - 1], y);
+#pragma unroll
+          for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+            for (int e = 0; e < CHUNK; ++e) q.v[k][e] *= H0;
+        } else {
+          const int ps = (slot - 1 + mem) % mem;
+          Frag<double> s;
+          frag_load(s, A.S + ps * NS, j, ld, tm);
+          frag_axpy(q, alpha[ai + 1] - beta_prev, s);
+        }
+        frag_store(q, A.dir, j, ld, tm);
+        Frag<double> y;
+        frag_load(y, A.Y + slot * NS, j, ld, tm);
+        const double d = frag_dot(y, q, tm);
+        if (tm.lane == 0) v[0] += d;
+      }
+      if (!sc.reduce(v, 1)) return false;
+      beta_prev = hrho[slot] * v[0];
+    }
+    {
+      const int last = (head - 1 + 2 * mem) % mem;
+      double v[1] = {0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> q, s, g;
+        frag_load(q, A.dir, j, ld, tm);
+        frag_load(s, A.S + last * NS, j, ld, tm);
+        frag_axpy(q, alpha[0] - beta_prev, s);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+          for (int e = 0; e < CHUNK; ++e) q.v[k][e] = -q.v[k][e];
+        frag_store(q, A.dir, j, ld, tm);
+        frag_load(g, A.grad, j, ld, tm);
+        const double d = frag_dot(q, g, tm);
+        if (tm.lane == 0) v[0] += d;
+      }
+      if (!sc.reduce(v, 1)) return false;
+      dg = v[0];
+    }
+    return true;
+  }
+
+  // dir <- -grad (restart)
+  __device__ bool steepest() {
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> g;
+      frag_load(g, A.grad, j, ld, tm);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) g.v[k][e] = -g.v[k][e];
+      frag_store(g, A.dir, j, ld, tm);
+    }
+    return sc.sync();
+  }
+
+  // quartic coefficients of phi(U + t D) - phi(U)
+  __device__ bool line_search_coeffs(double sigma, double* a) {
+    double v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = 0.0;
+    // <C, U D^T + D U^T> = 2 sum_j D_j . (C U)_j ;  <C, D D^T> = sum_j D_j . (C D)_j
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> mCU, mCD, Dj;
+      spmm_row<double>(P, A.U, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCU);
+      spmm_row<double>(P, A.dir, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCD);
+      frag_load(Dj, A.dir, j, ld, tm);
+      const double c1 = -2.0 * frag_dot(Dj, mCU, tm);
+      const double c2 = -frag_dot(Dj, mCD, tm);
+      if (tm.lane == 0) {
+        v[7] += c1;
+        v[8] += c2;
+      }
+    }
+    for (int i = tmc.id; i < m; i += tmc.count) {
+      const int rr = P.con_r[i], cc = P.con_c[i];
+      const double aa = P.con_a[i];
+      Frag<double> Ur, Dc, Dr, Uc;
+      frag_load(Ur, A.U, rr, ld, tmc);
+      frag_load(Dc, A.dir, cc, ld, tmc);
+      frag_load(Dr, A.dir, rr, ld, tmc);
+      frag_load(Uc, A.U, cc, ld, tmc);
+      double e1, e2;
+      if (rr != cc) {
+        e1 = 2.0 * aa * team_sum(frag_dot_local(Ur, Dc) + frag_dot_local(Uc, Dr), tmc);
+        e2 = 2.0 * aa * frag_dot(Dr, Dc, tmc);
+      } else {
+        e1 = 2.0 * aa * frag_dot(Ur, Dr, tmc);
+        e2 = aa * frag_dot(Dr, Dr, tmc);
+      }
+      if (tmc.lane == 0) {
+        const double l = A.lam[i], e0 = A.e[i];
+        v[0] += l * e1;
+        v[1] += l * e2;
+        v[2] += e0 * e1;
+        v[3] += e0 * e2;
+        v[4] += e1 * e1;
+        v[5] += e1 * e2;
+        v[6] += e2 * e2;
+      }
+    }
+    if (!sc.reduce(v, 9)) return false;
+    a[0] = v[7] + v[0] + sigma * v[2];
+    a[1] = v[8] + v[1] + 0.5 * sigma * (v[4] + 2.0 * v[3]);
+    a[2] = sigma * v[5];
+    a[3] = 0.5 * sigma * v[6];
+    return true;
+  }
+
+  // U <- U + t dir; S[head] = t dir; grad_old = grad
+  __device__ bool take_step(double t, int head) {
+    const long long NS = (long long)n * A.ld_cap;
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> u, d, g;
+      frag_load(u, A.U, j, ld, tm);
+      frag_load(d, A.dir, j, ld, tm);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) d.v[k][e] *= t;
+      frag_axpy(u, 1.0, d);
+      frag_store(u, A.U, j, ld, tm);
+      frag_store(d, A.S + head * NS, j, ld, tm);
+      frag_load(g, A.grad, j, ld, tm);
+      frag_store(g, A.grad_old, j, ld, tm);
+    }
+    return sc.sync();
+  }
+
+  // Y[head] = grad - grad_old; returns s.y and y.y
+  __device__ bool history_pair(int head, double& sy, double& yy) {
+    const long long NS = (long long)n * A.ld_cap;
+    double v[2] = {0.0, 0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> g, go, s;
+      frag_load(g, A.grad, j, ld, tm);
+      frag_load(go, A.grad_old, j, ld, tm);
+      frag_axpy(g, -1.0, go);
+      frag_store(g, A.Y + head * NS, j, ld, tm);
+      frag_load(s, A.S + head * NS, j, ld, tm);
+      const double a = frag_dot(s, g, tm), b = frag_dot(g, g, tm);
+      if (tm.lane == 0) {
+        v[0] += a;
+        v[1] += b;
+      }
+    }
+    if (!sc.reduce(v, 2)) return false;
+    sy = v[0];
+    yy = v[1];
+    return true;
+  }
+
+  // append columns r..r_new-1 drawn N(0, std^2) from sub-stream g (Section 4.3)
+  __device__ bool grow_rank(int r_new, int g) {
+    const int r_old = r, ld_old = ld;
+    const Team t_old = tm;
+    for (int j = t_old.id; j < n; j += t_old.count) {
+      Frag<double> u;
+      frag_load(u, A.U, j, ld_old, t_old);
+      frag_store(u, A.tmp, j, ld_old, t_old);
+    }
+    if (!sc.sync()) return false;
+    set_rank(r_new);
+    const uint64_t key = stream_key(prm.seed, (uint64_t)g);
+    const int extra = r_new - r_old;
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> u;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) {
+          const int c = (tm.lane + k * tm.G) * CHUNK + e;
+          double x = 0.0;
+          if (c < r_old)
+            x = A.tmp[(long long)j * ld_old + c];
+          else if (c < r_new)
+            x = prm.new_col_std * normal_at(key, (uint64_t)j * extra + (c - r_old));
+          u.v[k][e] = x;
+        }
+      frag_store(u, A.U, j, ld, tm);
+    }
+    return sc.sync();
+  }
+
+  // ----------------------------------------------------------------------------------
+  // Phase I: LRALM (Section 4.1) with dynamic rank (Section 4.3)
+  // ----------------------------------------------------------------------------------
+  __device__ bool phase1(double& sigma_out) {
+    for (int i = sc.tid(); i < m; i += sc.nthreads()) A.lam[i] = 0.0;
+    init_factor();
+    if (!sc.sync()) return false;
+    double sigma = 1.0 / (1.0 + P.b_inf);
+    double rp_prev = INFINITY, rp = 0.0;
+    double hrho[MAXMEM + 1], hsy[MAXMEM + 1], hyy[MAXMEM + 1];
+    const int ring = prm.lbfgs_mem + 1;
+    for (int outer = 1; outer <= prm.max_outer; ++outer) {
+      alm_outer = outer;
+      int cnt = 0, head = 0;
+      double e2, g2;
+      if (!eval_residual_UU(e2)) return false;
+      if (!eval_grad(sigma, g2)) return false;
+      int it = 0;
+      bool stalled = false;
+      for (;;) {
+        rp = sqrt(e2) / (1.0 + P.b_inf);
+        const double grel = sqrt(g2) / (1.0 + P.C_fro);
+        if (!(grel == grel)) { status = ST_NAN; return true; }
+        if (grel <= fmax(1e-12, fmin(prm.inner_tol_max, prm.inner_tol_factor * rp))) break;
+        if (it >= prm.inner_max_iter) { stalled = true; break; }
+        double dg;
+        const int newest = (head - 1 + ring) % ring;
+        const double H0 = cnt > 0 ? hsy[newest] / hyy[newest] : 1.0;
+        if (!lbfgs_direction(cnt, head, hrho, H0, dg)) return false;
+        if (dg >= 0.0) {
+          if (!steepest()) return false;
+          cnt = 0;
+          head = 0;
+        }
+        double a[4];
+        if (!line_search_coeffs(sigma, a)) return false;
+        const double t = quartic_step(a[0], a[1], a[2], a[3]);
+        if (!(t > 0.0)) {
+          if (cnt > 0) { cnt = 0; head = 0; continue; }
+          break;
+        }
+        if (!take_step(t, head)) return false;
+        if (!eval_residual_UU(e2)) return false;
+        if (!eval_grad(sigma, g2)) return false;
+        double sy, yy;
+        if (!history_pair(head, sy, yy)) return false;
+        if (sy > 0.0) {
+          hrho[head] = 1.0 / sy;
+          hsy[head] = sy;
+          hyy[head] = yy;
+          head = (head + 1) % ring;
+          cnt = cnt < prm.lbfgs_mem ? cnt + 1 : prm.lbfgs_mem;
+        }
+        ++it;
+      }
+      lbfgs_iters += it;
+      if (rp <= prm.switch_tol) {
+        for (int i = sc.tid(); i < m; i += sc.nthreads()) A.lam[i] += sigma * A.e[i];
+        if (!sc.sync()) return false;
+        break;
+      }
+      if (stalled && r < prm.rank_cap) {
+        ++growths;
+        int r_new = (int)ceil(prm.rank_factor * r - 1e-9);
+        if (r_new > prm.rank_cap) r_new = prm.rank_cap;
+        if (!grow_rank(r_new, growths)) return false;
+        continue;
+      }
+      for (int i = sc.tid(); i < m; i += sc.nthreads()) A.lam[i] += sigma * A.e[i];
+      if (!sc.sync()) return false;
+      if (rp > prm.sigma_decrease * rp_prev) sigma *= prm.sigma_factor;
+      rp_prev = rp;
+    }
+    sigma_out = sigma;
+    return true;
+  }
+
+  // ----------------------------------------------------------------------------------
+  // Phase II: one CG solve of eq. linU / eq. linV with fixed factor W, warm start X_0 = W
+  // ----------------------------------------------------------------------------------
+  // R_0 = G - H W with G = (A^T(rho b - lambda) - C) W + gamma W, computed in FP64:
+  //   R_0j = sum_{entries} a (rho b_i - lambda_i - rho q_i) W_k - (C W)_j,
+  //   q_i = <A_i, W W^T>  (the gamma terms cancel because X_0 = W).
+  __device__ bool cg_solve(const double* Wm, const T* Wt, double* Xm, T* Xt, double rho,
+                           double gamma, bool want_dv, double* dv) {
+    double v[2] = {0.0, 0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Wj, accR, mC;
+      frag_load(Wj, Wm, j, ld, tm);
+      spmm_row<double>(P, Wm, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mC);
+      accR = mC;
+      Frag<double> accG = mC;
+      for (int q = P.A_rp[j]; q < P.A_rp[j + 1]; ++q) {
+        const int k = P.A_col[q], i = P.A_con[q];
+        const double a = P.A_val[q];
+        double qi;
+        Frag<double> Wk;
+        if (k == j) {
+          Wk = Wj;
+          qi = a * frag_dot(Wj, Wj, tm);
+        } else {
+          frag_load(Wk, Wm, k, ld, tm);
+          qi = 2.0 * a * frag_dot(Wj, Wk, tm);
+        }
+        const double w = rho * P.b[i] - A.lam[i];
+        frag_axpy(accG, a * w, Wk);
+        frag_axpy(accR, a * (w - rho * qi), Wk);
+      }
+      frag_axpy(accG, gamma, Wj);
+      Frag<T> Rt, Zt;
+      frag_convert(Rt, accR);
+      frag_zero(Zt);
+      frag_store(Rt, A.R, j, ld, tm);
+      frag_store(Rt, A.Pd, j, ld, tm);
+      frag_store(Zt, A.Dl, j, ld, tm);
+      Frag<double> Rd;
+      frag_convert(Rd, Rt);
+      const double a1 = frag_dot(Rd, Rd, tm), a2 = frag_dot(accG, accG, tm);
+      if (tm.lane == 0) {
+        v[0] += a1;
+        v[1] += a2;
+      }
+    }
+    if (!sc.reduce(v, 2)) return false;
+    ++hess;
+    double rr = v[0];
+    const double target = fmax(prm.cg_rel_tol * sqrt(rr), prm.cg_abs_floor * sqrt(v[1]));
+    const T rho_t = (T)rho, gamma_t = (T)gamma;
+    int it = 0;
+    while (sqrt(rr) > target && it < prm.cg_max_iter) {
+      // HP = H P, p.Hp
+      double w[1] = {0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<T> Pj, Hj;
+        frag_load(Pj, A.Pd, j, ld, tm);
+        hessian_row<T>(P, Wt, A.Pd, ld, j, Pj, rho_t, gamma_t, tm, Hj);
+        frag_store(Hj, A.HP, j, ld, tm);
+        const double d = (double)team_sum(frag_dot_local(Pj, Hj), tm);
+        if (tm.lane == 0) w[0] += d;
+      }
+      if (!sc.reduce(w, 1)) return false;
+      ++hess;
+      const double pHp = w[0];
+      if (!(pHp > 0.0)) {
+        if (!(pHp == pHp)) status = ST_NAN;
+        break;
+      }
+      const double alpha = rr / pHp;
+      const T alpha_t = (T)alpha;
+      double z[1] = {0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<T> Dj, Pj, Rj, Hj;
+        frag_load(Dj, A.Dl, j, ld, tm);
+        frag_load(Pj, A.Pd, j, ld, tm);
+        frag_load(Rj, A.R, j, ld, tm);
+        frag_load(Hj, A.HP, j, ld, tm);
+        frag_axpy(Dj, alpha_t, Pj);
+        frag_axpy(Rj, -alpha_t, Hj);
+        frag_store(Dj, A.Dl, j, ld, tm);
+        frag_store(Rj, A.R, j, ld, tm);
+        Frag<double> Rd;
+        frag_convert(Rd, Rj);
+        const double d = frag_dot(Rd, Rd, tm);
+        if (tm.lane == 0) z[0] += d;
+      }
+      if (!sc.reduce(z, 1)) return false;
+      ++it;
+      const double rr_new = z[0];
+      if (sqrt(rr_new) <= target) { rr = rr_new; break; }
+      const T beta_t = (T)(rr_new / rr);
+      rr = rr_new;
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<T> Pj, Rj;
+        frag_load(Pj, A.Pd, j, ld, tm);
+        frag_load(Rj, A.R, j, ld, tm);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+          for (int e = 0; e < CHUNK; ++e) Pj.v[k][e] = fma(beta_t, Pj.v[k][e], Rj.v[k][e]);
+        frag_store(Pj, A.Pd, j, ld, tm);
+      }
+      if (!sc.sync()) return false;
+    }
+    cg_iters += it;
+    // X = W + delta (FP64 master and T shadow)
+    dv[0] = 0.0;
+    dv[1] = 0.0;
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Wj, Xj;
+      Frag<T> Dj;
+      frag_load(Wj, Wm, j, ld, tm);
+      frag_load(Dj, A.Dl, j, ld, tm);
+      frag_convert(Xj, Dj);
+      frag_axpy(Xj, 1.0, Wj);
+      if (want_dv) {
+        Frag<double> Xo;
+        frag_load(Xo, Xm, j, ld, tm);
+        const double o2 = frag_dot(Xo, Xo, tm);
+        frag_axpy(Xo, -1.0, Xj);
+        const double d2 = frag_dot(Xo, Xo, tm);
+        if (tm.lane == 0) {
+          dv[0] += d2;
+          dv[1] += o2;
+        }
+      }
+      frag_store(Xj, Xm, j, ld, tm);
+      if ((const void*)Xt != (const void*)Xm) {
+        Frag<T> Xs;
+        frag_convert(Xs, Xj);
+        frag_store(Xs, Xt, j, ld, tm);
+      }
+    }
+    return sc.sync();
+  }
+
+  // dual step lambda += rho (A(U V^T) - b); partial sums of ||e||^2 and of the output
+  // infeasibility ||A(U_hat U_hat^T) - b||^2, U_hat = (U + V)/2
+  __device__ void dual_step(double rho, double* v) {
+    for (int i = tmc.id; i < m; i += tmc.count) {
+      const int rr = P.con_r[i], cc = P.con_c[i];
+      const double a = P.con_a[i];
+      Frag<double> Ur, Vc, Uc, Vr;
+      frag_load(Ur, A.U, rr, ld, tmc);
+      frag_load(Vc, A.V, cc, ld, tmc);
+      frag_load(Uc, A.U, cc, ld, tmc);
+      frag_load(Vr, A.V, rr, ld, tmc);
+      Frag<double> Hr = Ur, Hc = Uc;
+      frag_axpy(Hr, 1.0, Vr);
+      frag_axpy(Hc, 1.0, Vc);
+      double q, qh;
+      if (rr != cc) {
+        q = a * team_sum(frag_dot_local(Ur, Vc) + frag_dot_local(Uc, Vr), tmc);
+        qh = 0.5 * a * frag_dot(Hr, Hc, tmc);      // 2 (Hr/2).(Hc/2)
+      } else {
+        q = a * frag_dot(Ur, Vr, tmc);
+        qh = 0.25 * a * frag_dot(Hr, Hr, tmc);
+      }
+      if (tmc.lane == 0) {
+        const double e = q - P.b[i], eh = qh - P.b[i];
+        A.lam[i] += rho * e;
+        v[0] += e * e;
+        v[1] += eh * eh;
+      }
+    }
+  }
+
+  __device__ bool phase2(double rho, double& rho_out) {
+    const double gamma = prm.gamma;
+    for (int k = 0; k < prm.max_admm_iter; ++k) {
+      double dv[2];
+      // U-step: eq. linU with W = V^k, CG warm-started from V^k
+      if (!cg_solve(A.V, A.Vt, A.U, A.Ut, rho, gamma, false, dv)) return false;
+      if (status != ST_OK) break;
+      // V-step: eq. linV with W = U^{k+1}, CG warm-started from U^{k+1}
+      if (!cg_solve(A.U, A.Ut, A.V, A.Vt, rho, gamma, true, dv)) return false;
+      if (status != ST_OK) break;
+      double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      dual_step(rho, v);
+      v[2] = dv[0];
+      v[3] = dv[1];
+      if (sc.is_leader()) v[4] = (double)(globaltimer_ns() - t_start);
+      if (!sc.reduce(v, 5)) return false;
+      admm_iters = k + 1;
+      const double rp = sqrt(v[0]) / (1.0 + P.b_inf);
+      const double rph = sqrt(v[1]) / (1.0 + P.b_inf);
+      const double rs = gamma * sqrt(v[2]) / (1.0 + sqrt(v[3]));
+      last_rs = rs;
+      if (!(rp == rp) || !(rs == rs)) { status = ST_NAN; break; }
+      if (fmax(rp, fmax(rs, rph)) <= prm.tol) {
+        rho_out = rho;
+        return true;
+      }
+      if ((long long)v[4] > prm.time_limit_ns) { status = ST_TIMEOUT; break; }
+      if ((k + 1) % prm.rho_every == 0) rho = fmin(rho * prm.rho_growth, prm.rho_max);
+    }
+    if (status == ST_OK) status = ST_MAXITER;
+    rho_out = rho;
+    return true;
+  }
+
+  // U_hat, objective, dual stationarity, output infeasibility, b^T lambda
+  __device__ bool output(double* res) {
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> u, w;
+      frag_load(u, A.U, j, ld, tm);
+      frag_load(w, A.V, j, ld, tm);
+      frag_axpy(u, 1.0, w);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) u.v[k][e] *= 0.5;
+      frag_store(u, A.tmp, j, ld, tm);
+    }
+    if (!sc.sync()) return false;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Uh, mCU, mSU;
+      frag_load(Uh, A.tmp, j, ld, tm);
+      spmm_row<double>(P, A.tmp, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCU);
+      spmm_row<double>(P, A.tmp, ld, j, A.lam, nullptr, 0.0, -1.0, 0.0, 0.0, tm, mSU);
+      const double o = -frag_dot(Uh, mCU, tm), d = frag_dot(mSU, mSU, tm);
+      if (tm.lane == 0) {
+        v[0] += o;
+        v[1] += d;
+      }
+    }
+    for (int i = tmc.id; i < m; i += tmc.count) {
+      const double q = sddmm_con<double>(P, A.tmp, A.tmp, ld, i, tmc);
+      const double qs = sddmm_con<double>(P, A.U, A.V, ld, i, tmc);
+      if (tmc.lane == 0) {
+        const double eh = q - P.b[i], es = qs - P.b[i];
+        v[2] += eh * eh;
+        v[3] += P.b[i] * A.lam[i];
+        v[4] += es * es;
+      }
+    }
+    if (!sc.reduce(v, 5)) return false;
+    for (int i = 0; i < 5; ++i) res[i] = v[i];
+    return true;
+  }
+
+  __device__ void run() {
+    t_start = globaltimer_ns();
+    double sigma = 0.0, rho = 0.0;
+    set_rank(prm.phase1 ? prm.r0 : prm.r_start);
+    if (prm.phase1) {
+      if (!phase1(sigma)) { finish_error(); return; }
+      if (status != ST_OK) { finish(sigma, rho, nullptr, 0, 0); return; }
+      rho = fmin(prm.h * sigma, prm.rho_max);
+    } else {
+      rho = prm.rho0;
+    }
+    // switch: V = U (Algorithm 2), shadows
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> u;
+      frag_load(u, A.U, j, ld, tm);
+      frag_store(u, A.V, j, ld, tm);
+      if ((const void*)A.Ut != (const void*)A.U) {
+        Frag<T> s;
+        frag_convert(s, u);
+        frag_store(s, A.Ut, j, ld, tm);
+        frag_store(s, A.Vt, j, ld, tm);
+      }
+    }
+    if (!sc.sync()) { finish_error(); return; }
+    const long long t1 = globaltimer_ns();
+    double rho_out = rho;
+    if (!phase2(rho, rho_out)) { finish_error(); return; }
+    double res[5];
+    if (!output(res)) { finish_error(); return; }
+    finish(sigma, rho_out, res, t1, 1);
+  }
+
+  __device__ void finish_error() {
+    if (sc.is_leader()) A.out->status = ST_DEVICE;
+  }
+
+  __device__ void finish(double sigma, double rho, const double* res, long long t1, int have) {
+    if (!sc.is_leader()) return;
+    SolveOut* o = A.out;
+    const long long t2 = globaltimer_ns();
+    o->status = status;
+    o->rank = r;
+    o->ld = ld;
+    o->admm_iters = admm_iters;
+    o->cg_iters = cg_iters;
+    o->hess_applies = hess;
+    o->alm_outer = alm_outer;
+    o->lbfgs_iters = lbfgs_iters;
+    o->growths = growths;
+    o->rho = rho;
+    o->gamma = prm.gamma;
+    o->sigma = sigma;
+    o->t_phase1_ns = have ? t1 - t_start : t2 - t_start;
+    o->t_phase2_ns = have ? t2 - t1 : 0;
+    if (have) {
+      const double obj = res[0], dobj = -res[3];
+      o->objective = obj;
+      o->dual_objective = dobj;
+      o->r_D = sqrt(res[1]) / (1.0 + P.C_fro);
+      o->r_P = sqrt(res[2]) / (1.0 + P.b_inf);
+      o->r_P_split = sqrt(res[4]) / (1.0 + P.b_inf);
+      o->gap = (obj - dobj) / (1.0 + fabs(obj) + fabs(dobj));
+      o->r_stop = last_rs;
+    }
+  }
+};
+
+template <typename T, class Scope>
+__device__ void run_solver(const SolverArgs<T>& a, Scope& sc) {
+  Solver<T, Scope> s(a, sc);
+  s.run();
+}
+
+}  // namespace lorads

@@ -1,0 +1,61 @@
+"""The C ABI library builds, loads and exports every entry point include/lorads.h declares
+(no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+from oracle import Params
+from paper_2403_09133_gb300 import lorads as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lorads.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lorads_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_binding_mirrors_structs(lib):
+    pb, rb = ctypes.c_int64(), ctypes.c_int64()
+    lib.lorads_struct_sizes(ctypes.byref(pb), ctypes.byref(rb))
+    assert pb.value == ctypes.sizeof(L.lorads_params)
+    assert rb.value == ctypes.sizeof(L.lorads_result)
+
+
+def test_binding_exposes_same_names(lib):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_default_params_match_oracle_readings(lib):
+    p = L.lorads_default_params()
+    o = Params()
+    assert p.tol == o.tol and p.rho_max == o.rho_max and p.rho_growth == o.rho_growth
+    assert p.rho_every == o.rho_every and p.rank_factor == o.rank_factor
+    assert p.cg_rel_tol == o.cg_rel_tol and p.cg_abs_floor == o.cg_abs_floor
+    assert p.lbfgs_mem == o.lbfgs_mem and p.inner_max_iter == o.inner_max_iter
+    assert p.inner_tol_factor == o.inner_tol_factor and p.inner_tol_max == o.inner_tol_max
+    assert p.sigma_factor == o.sigma_factor and p.sigma_decrease == o.sigma_decrease
+    assert p.gamma_scale == o.gamma_scale and p.new_col_std == o.new_col_std
+    assert p.max_admm_iter == o.max_admm_iter and p.max_outer == o.max_outer
+
+
+def test_status_strings(lib):
+    for code in range(0, -10, -1):
+        assert L.lorads_status_string(code) != "unknown status"
+    assert L.lorads_status_string(-99) == "unknown status"
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.lorads_set_b(None, None) == L.LORADS_ERR_ARG
+    assert lib.lorads_solve(None, None, None, None) == L.LORADS_ERR_ARG
+    assert lib.lorads_create(0, 5, None) == L.LORADS_ERR_ARG

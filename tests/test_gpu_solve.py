@@ -1,0 +1,131 @@
+"""GPU solves (Algorithm 2 in one persistent launch) against the oracle, closed forms and
+certificates.
+
+Pins: the MaxCut SDP value of K_n (n^2/4) and of unit tori (n lambda_max(L)/4); the
+oracle's own solve of the same seeded instance with the same seed; lambda_min(C - A^T y)
+and the duality gap computed by the oracle from the GPU's y; matrix completion's 2||M||_*.
+The iterates of two runs need not agree (the method is nonconvex and reductions differ in
+order), so objectives are compared to the accuracy the stopping rule implies."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import SDP, Params, solve
+from oracle.certify import min_eig_dual_slack
+from paper_2403_09133_gb300 import instances as I
+from paper_2403_09133_gb300 import lorads as L
+
+pytestmark = pytest.mark.gpu
+
+
+def lam_max_cycle(k):
+    return 4.0 if k % 2 == 0 else 2.0 + 2.0 * math.cos(math.pi / k)
+
+
+def gpu_solve(inst, **kw):
+    p = L.Problem(inst)
+    res = p.solve(**kw)
+    sol = p.solution() if res["status"] in (0, L.LORADS_ERR_MAXITER) else None
+    p.close()
+    return res, sol
+
+
+@pytest.mark.parametrize("prec", [L.LORADS_PREC_FP64, L.LORADS_PREC_MIXED])
+def test_complete_graph(cuda, prec):
+    n = 12
+    res, sol = gpu_solve(I.maxcut_complete(n), precision=prec, tol=1e-9, max_admm_iter=3000)
+    assert res["status"] in (0, L.LORADS_ERR_MAXITER)
+    assert abs(res["objective"] + n * n / 4) <= 1e-7 * n * n / 4
+    np.testing.assert_allclose(sol["y"], -n / 4, atol=1e-5 * n)
+
+
+@pytest.mark.parametrize("prec", [L.LORADS_PREC_FP64, L.LORADS_PREC_MIXED])
+def test_unit_torus(cuda, prec):
+    a, b = 6, 8
+    res, sol = gpu_solve(I.maxcut_torus(a, b, seed=None), precision=prec, tol=1e-9,
+                         max_admm_iter=3000)
+    want = a * b * (lam_max_cycle(a) + lam_max_cycle(b)) / 4
+    assert abs(-res["objective"] - want) <= 1e-7 * want
+
+
+@pytest.mark.parametrize("prec", [L.LORADS_PREC_FP64, L.LORADS_PREC_MIXED])
+def test_er500_against_oracle(cuda, prec):
+    inst = I.workload_er500()
+    sdp = SDP.from_instance(inst)
+    ref = solve(sdp, Params())
+    res, sol = gpu_solve(inst, precision=prec)
+    assert res["status"] == 0, L.lorads_status_string(res["status"])
+    assert res["r_P"] <= 1e-6 and res["r_P_split"] <= 1e-6 and res["r_stop"] <= 1e-6
+    assert abs(res["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+    # the library's own residual report agrees with the oracle's evaluation of its output
+    rep = OLkkt(sdp, sol)
+    assert abs(rep["objective"] - res["objective"]) <= 1e-10 * abs(res["objective"])
+    assert abs(rep["r_P"] - res["r_P"]) <= 1e-9
+    assert abs(rep["r_D"] - res["r_D"]) <= 1e-6 * max(rep["r_D"], 1e-12) + 1e-12
+    assert abs(rep["gap"] - res["gap"]) <= 1e-10
+    lmin = min_eig_dual_slack(sdp, sol["y"])
+    assert lmin >= -1e-3
+
+
+def OLkkt(sdp, sol):
+    from oracle.lorads import kkt_report
+    return kkt_report(sdp, sol["U_hat"], sol["y"])
+
+
+def test_grid_scope_matches_block_scope(cuda):
+    inst = I.workload_er500()
+    rb, _ = gpu_solve(inst, grid=1)
+    rg, _ = gpu_solve(inst, grid=16)
+    assert rb["status"] == 0 and rg["status"] == 0
+    assert abs(rb["objective"] - rg["objective"]) <= 1e-6 * abs(rb["objective"])
+
+
+def test_deterministic(cuda):
+    inst = I.maxcut_er(300, 6.0, seed=3)
+    r1, s1 = gpu_solve(inst, grid=8)
+    r2, s2 = gpu_solve(inst, grid=8)
+    assert r1["objective"] == r2["objective"]
+    assert np.array_equal(s1["U_hat"], s2["U_hat"])
+
+
+def test_matrix_completion_small(cuda):
+    inst = I.matrix_completion(30, 30, 2, 500, seed=3)
+    res, sol = gpu_solve(inst, switch_tol=1e-3, h=5.0, tol=1e-9, max_admm_iter=3000)
+    want = 2.0 * np.linalg.svd(inst.mc_P @ inst.mc_Q.T, compute_uv=False).sum()
+    assert abs(res["objective"] - want) <= 1e-7 * want
+
+
+def test_status_codes(cuda):
+    inst = I.maxcut_er(100, 5.0, seed=1)
+    res, _ = gpu_solve(inst, max_admm_iter=2)
+    assert res["status"] == L.LORADS_ERR_MAXITER
+    # a constraint with two entries is outside the single-entry device path
+    bad = I.maxcut_er(20, 3.0, seed=1)
+    bad.A_con = np.concatenate([bad.A_con, [0]]).astype(np.int32)
+    bad.A_row = np.concatenate([bad.A_row, [1]]).astype(np.int32)
+    bad.A_col = np.concatenate([bad.A_col, [2]]).astype(np.int32)
+    bad.A_val = np.concatenate([bad.A_val, [1.0]])
+    p = L.Problem(bad)
+    assert p.solve()["status"] == L.LORADS_ERR_UNSUPPORTED
+    p.close()
+
+
+def test_phase2_start_from_caller(cuda):
+    """phase1 = 0 starts Algorithm 1 from a caller-supplied (U_0, lambda_0, rho_0); here the
+    oracle's own Phase I output, so both sides then run the same Phase II."""
+    import oracle.lorads as OL
+    inst = I.maxcut_er(60, 6.0, seed=11)
+    sdp = SDP.from_instance(inst)
+    prm = Params()
+    U_init = OL.initial_factor(sdp, OL.initial_rank(sdp.m, sdp.n, prm), prm.seed)
+    ph1 = OL.lralm(sdp, U_init, prm)
+    rho0 = min(prm.h * ph1["sigma"], prm.rho_max)
+    p = L.Problem(inst)
+    assert L.lorads_set_start(p.handle, ph1["U"], ph1["lam"], rho0) == 0
+    res = p.solve(phase1=0)
+    p.close()
+    ref = solve(sdp, Params(phase1=False), U0=ph1["U"], lam0=ph1["lam"], rho0=rho0)
+    assert res["status"] == 0 and ref["converged"]
+    assert abs(res["admm_iters"] - ref["admm_iters"]) <= 2
+    assert abs(res["objective"] - ref["objective"]) <= 1e-7 * abs(ref["objective"])
