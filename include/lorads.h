@@ -44,7 +44,8 @@ enum {
   LORADS_ERR_TIMEOUT = -6,      /* time limit reached before the tolerance                */
   LORADS_ERR_NAN = -7,          /* a NaN or Inf appeared in the iterates or the input     */
   LORADS_ERR_UNSUPPORTED = -8,  /* constraint structure this build does not handle        */
-  LORADS_ERR_DEVICE = -9        /* a device-side wait gave up (bounded grid barrier)      */
+  LORADS_ERR_DEVICE = -9,       /* a device-side wait gave up (bounded grid barrier)      */
+  LORADS_ERR_TOO_LARGE = -10    /* lorads_solve_static: problem exceeds its fixed scratch */
 };
 
 /* ---------------------------------------------------------------- precision forms */
@@ -161,6 +162,35 @@ int lorads_solve(lorads_problem *p, const lorads_params *prm, void *stream, lora
  * row-major (r = result rank; any pointer may be NULL), y of length m. */
 int lorads_get_solution(const lorads_problem *p, double *U, double *V, double *U_hat,
                         double *y, int32_t *r);
+
+/* Allocation-free solve.  The paper has no counterpart: this is a deployment variant of
+ * lorads_solve for callers that must not allocate device memory while they solve -- code
+ * that runs between the set-up and the end of a latency-critical loop, processes that
+ * share a GPU under a fixed memory budget, or hosts whose allocator must not be entered
+ * from the solving thread.  Such a caller builds the problem once (lorads_create, the
+ * set calls, and one lorads_solve or lorads_op_* call, which assemble the device form and
+ * do allocate); afterwards this call allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.
+ *
+ * The solver's working memory (factors, CG vectors, L-BFGS history, reduction scratch) is a
+ * file-scope device array of LORADS_STATIC_SCRATCH_BYTES (32 MiB) that every GPU which loads
+ * the library holds until the process exits.  Problems whose working set does not fit are
+ * rejected with LORADS_ERR_TOO_LARGE (roughly n * 4 ceil(r_max/4) <= 150,000 for the default
+ * L-BFGS memory, r_max the rank cap).  The problem must already be assembled, else
+ * LORADS_ERR_STATE.
+ *
+ * Outputs go to caller DEVICE buffers: U_hat as n x ldu row-major doubles (ldu >= the final
+ * rank, which is at most the rank cap; columns beyond the final rank are left unchanged),
+ * y (length m, y = -lambda); either may be NULL.  res (host) receives the report.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call shares
+ * the one array and leaves the last call's contents in it; the call clears what must start
+ * at zero.  Calls that overlap on the GPU (several streams or host threads at once) race on
+ * the array: serialize them.  The call returns when the solve has finished on stream. */
+#define LORADS_STATIC_SCRATCH_BYTES (32ull << 20)
+int lorads_solve_static(lorads_problem *p, const lorads_params *prm, void *stream,
+                        double *U_hat, int64_t ldu, double *y, lorads_result *res);
 
 /* Releases the problem and its device memory.  NULL is ignored. */
 void lorads_destroy(lorads_problem *p);

@@ -6,6 +6,7 @@
 // launches the persistent solver.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -668,6 +669,7 @@ const char* lorads_status_string(int code) {
     case LORADS_ERR_NAN: return "NaN or Inf in the iterates";
     case LORADS_ERR_UNSUPPORTED: return "constraint structure not supported by the device path";
     case LORADS_ERR_DEVICE: return "device-side wait gave up";
+    case LORADS_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of lorads_solve_static";
     default: return "unknown status";
   }
 }
@@ -734,3 +736,252 @@ int lorads_op_hessian(lorads_problem* p, int32_t prec, int32_t r, int32_t ld, do
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// lorads_solve_static: the solver's working memory in a fixed file-scope device array
+// ---------------------------------------------------------------------------------------
+// The array is the only memory the call touches besides the problem's assembled device
+// form (built earlier) and the caller's output buffers.  Host code must not use the
+// symbol's name as an address: it is a host-side stand-in.  The device address is looked
+// up once per device with cudaGetSymbolAddress and passed to the kernels.
+static __device__ __align__(256) unsigned char g_static_scratch[LORADS_STATIC_SCRATCH_BYTES];
+
+__global__ void static_negate_kernel(const double* lam, double* y, int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    y[i] = -lam[i];
+}
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_addr[kMaxDevices] = {};
+
+// device address of g_static_scratch on `device`, which must be current
+int static_scratch_address(int device, unsigned char** out) {
+  if (device < 0 || device >= kMaxDevices) return LORADS_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (g_static_addr[device] == nullptr) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+      cudaGetLastError();
+      return LORADS_ERR_CUDA;
+    }
+    g_static_addr[device] = static_cast<unsigned char*>(ptr);
+  }
+  *out = g_static_addr[device];
+  return LORADS_OK;
+}
+
+// bump carving of the fixed array; never allocates
+struct StaticCarve {
+  unsigned char* base;
+  size_t cap;
+  size_t used;
+  template <typename X>
+  X* take(size_t count) {
+    const size_t bytes = ((count * sizeof(X) + 255) / 256) * 256;
+    if (used + bytes > cap) return nullptr;
+    X* q = reinterpret_cast<X*>(base + used);
+    used += bytes;
+    return q;
+  }
+};
+
+// switches to the problem's device for the call and restores the caller's device after
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    if (!ok) cudaGetLastError();
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+template <typename T>
+static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStream_t s,
+                            double* U_hat, int64_t ldu, double* y, lorads_result* res) {
+  const int64_t n = p->n, m = p->m;
+  DevParams dv{};
+  const int cap = resolve_rank_cap(p, prm);
+  dv.rank_cap = cap;
+  dv.r0 = resolve_r0(p, prm, cap);
+  dv.rank_factor = prm->rank_factor;
+  dv.tol = prm->tol;
+  dv.switch_tol = prm->switch_tol >= 0 ? prm->switch_tol : (p->diag_separable ? 1e-2 : 1e-3);
+  dv.h = prm->h >= 0 ? prm->h : (p->diag_separable ? 10.0 : 1.0);
+  dv.rho_max = prm->rho_max;
+  dv.rho_growth = prm->rho_growth;
+  dv.rho_every = std::max(1, prm->rho_every);
+  dv.gamma = prm->gamma_fixed > 0 ? prm->gamma_fixed
+                                  : prm->gamma_scale * (p->C_inf > 0 ? p->C_inf : 1.0);
+  dv.max_admm_iter = prm->max_admm_iter;
+  dv.cg_max_iter = prm->cg_max_iter;
+  dv.cg_rel_tol = prm->cg_rel_tol;
+  dv.cg_abs_floor = prm->cg_abs_floor;
+  dv.lbfgs_mem = std::min(std::max(prm->lbfgs_mem, 1), MAXMEM);
+  dv.inner_max_iter = prm->inner_max_iter;
+  dv.inner_tol_factor = prm->inner_tol_factor;
+  dv.inner_tol_max = prm->inner_tol_max;
+  dv.max_outer = prm->max_outer;
+  dv.sigma_factor = prm->sigma_factor;
+  dv.sigma_decrease = prm->sigma_decrease;
+  dv.new_col_std = prm->new_col_std;
+  dv.seed = prm->seed;
+  dv.phase1 = prm->phase1 ? 1 : 0;
+  dv.r_start = p->start_r;
+  dv.rho0 = p->start_rho > 0 ? p->start_rho : 100.0;
+  dv.time_limit_ns = (long long)(prm->time_limit_s * 1e9);
+  if (!dv.phase1 && (!p->has_start || p->start_r > 256)) return LORADS_ERR_STATE;
+  const int rmax = std::max(cap, dv.phase1 ? 0 : p->start_r);
+  const long long ld_cap = round4(rmax);
+  if (U_hat != nullptr && ldu < rmax) return LORADS_ERR_ARG;
+  const size_t NS = (size_t)n * ld_cap;
+  const int ring = dv.lbfgs_mem + 1;
+  const bool mixed = sizeof(T) == 4;
+  int dev_sms = 0;
+  CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
+  unsigned char* base = nullptr;
+  int st = static_scratch_address(p->device, &base);
+  if (st != LORADS_OK) return st;
+  StaticCarve a{base, (size_t)LORADS_STATIC_SCRATCH_BYTES, 0};
+  SolverArgs<T> h{};
+  h.P = p->dp;
+  h.prm = dv;
+  h.U = a.take<double>(NS);
+  h.V = a.take<double>(NS);
+  if (mixed) {
+    h.Ut = a.take<T>(NS);
+    h.Vt = a.take<T>(NS);
+  } else {
+    h.Ut = reinterpret_cast<T*>(h.U);
+    h.Vt = reinterpret_cast<T*>(h.V);
+  }
+  h.Dl = a.take<T>(NS);
+  h.R = a.take<T>(NS);
+  h.Pd = a.take<T>(NS);
+  h.HP = a.take<T>(NS);
+  h.lam = a.take<double>(m);
+  h.e = a.take<double>(m);
+  h.grad = a.take<double>(NS);
+  h.grad_old = a.take<double>(NS);
+  h.dir = a.take<double>(NS);
+  h.tmp = a.take<double>(NS);
+  h.S = a.take<double>(NS * ring);
+  h.Y = a.take<double>(NS * ring);
+  h.ld_cap = ld_cap;
+  SolverArgs<T>* dargs = a.take<SolverArgs<T>>(1);
+  SolveOut* dout = a.take<SolveOut>(1);
+  GridCtl* dctl = a.take<GridCtl>(1);
+  double* dpartials = a.take<double>((size_t)dev_sms * 8 * MAXRED);
+  int* dqueue = a.take<int>(4);
+  if (!h.U || !h.V || !h.Ut || !h.Vt || !h.Dl || !h.R || !h.Pd || !h.HP || !h.lam || !h.e ||
+      !h.grad || !h.grad_old || !h.dir || !h.tmp || !h.S || !h.Y || !dargs || !dout || !dctl ||
+      !dpartials || !dqueue)
+    return LORADS_ERR_TOO_LARGE;
+  h.out = dout;
+  if (!dv.phase1) {
+    const int r = p->start_r, ld = round4(r);
+    CU(cudaMemsetAsync(h.U, 0, NS * sizeof(double), s));
+    CU(cudaMemcpy2DAsync(h.U, (size_t)ld * 8, p->start_U.data(), (size_t)r * 8, (size_t)r * 8,
+                         (size_t)n, cudaMemcpyHostToDevice, s));
+    if (!p->start_lam.empty())
+      CU(cudaMemcpyAsync(h.lam, p->start_lam.data(), m * 8, cudaMemcpyHostToDevice, s));
+    else
+      CU(cudaMemsetAsync(h.lam, 0, m * 8, s));
+  }
+  // what must start at zero: the report, the grid barrier and the CTA queue
+  CU(cudaMemcpyAsync(dargs, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(dout, 0, sizeof(SolveOut), s));
+  CU(cudaMemsetAsync(dctl, 0, sizeof(GridCtl), s));
+  CU(cudaMemsetAsync(dqueue, 0, 16, s));
+  int grid = prm->grid;
+  if (grid <= 0) grid = (n < 4096) ? 1 : dev_sms;
+  cudaError_t le;
+  if (grid == 1) {
+    le = Launch<T>::solve_block(dargs, 1, dqueue, 1, s);
+  } else {
+    int per_sm = 0;
+    CU(Launch<T>::grid_capacity(&per_sm));
+    grid = std::min(std::min(grid, std::max(1, per_sm) * dev_sms), dev_sms * 8);
+    le = Launch<T>::solve_grid(dargs, dctl, dpartials, 50LL * 1000 * 1000, grid, s);
+  }
+  CU(le);
+  SolveOut out{};
+  CU(cudaMemcpyAsync(&out, dout, sizeof(out), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (out.ld > 0) {
+    if (U_hat != nullptr && out.rank > 0)
+      CU(cudaMemcpy2DAsync(U_hat, (size_t)ldu * 8, h.tmp, (size_t)out.ld * 8,
+                           (size_t)out.rank * 8, (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if (y != nullptr) {
+      static_negate_kernel<<<std::max(1, std::min(dev_sms * 4, (int)((m + 255) / 256))), 256, 0,
+                             s>>>(h.lam, y, (int)m);
+      CU(cudaGetLastError());
+    }
+    CU(cudaStreamSynchronize(s));
+  }
+  if (res) {
+    lorads_result r{};
+    r.status = out.status;
+    r.rank = out.rank;
+    r.objective = out.objective;
+    r.dual_objective = out.dual_objective;
+    r.r_P = out.r_P;
+    r.r_P_split = out.r_P_split;
+    r.r_stop = out.r_stop;
+    r.r_D = out.r_D;
+    r.gap = out.gap;
+    r.rho = out.rho;
+    r.gamma = out.gamma;
+    r.sigma = out.sigma;
+    r.admm_iters = out.admm_iters;
+    r.cg_iters = out.cg_iters;
+    r.hessian_applies = out.hess_applies;
+    r.alm_outer = out.alm_outer;
+    r.lbfgs_iters = out.lbfgs_iters;
+    r.rank_growths = out.growths;
+    r.time_phase1_s = out.t_phase1_ns * 1e-9;
+    r.time_phase2_s = out.t_phase2_ns * 1e-9;
+    *res = r;
+  }
+  return out.status;
+}
+
+extern "C" int lorads_solve_static(lorads_problem* p, const lorads_params* prm, void* stream,
+                                   double* U_hat, int64_t ldu, double* y, lorads_result* res) {
+  if (res) std::memset(res, 0, sizeof(*res));
+  int st = LORADS_OK;
+  if (!p || !prm) {
+    st = LORADS_ERR_ARG;
+  } else if (prm->precision != LORADS_PREC_FP64 && prm->precision != LORADS_PREC_MIXED) {
+    st = LORADS_ERR_ARG;
+  } else if (!(prm->tol > 0) || prm->max_admm_iter < 1 || prm->cg_max_iter < 1) {
+    st = LORADS_ERR_ARG;
+  } else if (!p->assembled || p->assemble_status != LORADS_OK) {
+    st = LORADS_ERR_STATE;       // assembling would allocate
+  } else {
+    DeviceGuard guard(p->device);
+    if (!guard.ok) {
+      st = LORADS_ERR_CUDA;
+    } else {
+      cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+      st = prm->precision == LORADS_PREC_MIXED
+               ? run_solve_static<float>(p, prm, s, U_hat, ldu, y, res)
+               : run_solve_static<double>(p, prm, s, U_hat, ldu, y, res);
+    }
+  }
+  if (res) res->status = st;
+  return st;
+}

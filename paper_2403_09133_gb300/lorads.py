@@ -25,6 +25,8 @@ LORADS_ERR_TIMEOUT = -6
 LORADS_ERR_NAN = -7
 LORADS_ERR_UNSUPPORTED = -8
 LORADS_ERR_DEVICE = -9
+LORADS_ERR_TOO_LARGE = -10
+LORADS_STATIC_SCRATCH_BYTES = 32 << 20
 LORADS_PREC_FP64 = 0
 LORADS_PREC_MIXED = 1
 
@@ -90,6 +92,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lorads_destroy": (None, [P]),
         "lorads_status_string": (ctypes.c_char_p, [_i32]),
         "lorads_struct_sizes": (None, [ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+        "lorads_solve_static": (_i32, [P, ctypes.POINTER(lorads_params), P, P, _i64, P,
+                                       ctypes.POINTER(lorads_result)]),
         "lorads_op_sddmm": (_i32, [P, _i32, _i32, _i32, P, P, P, P]),
         "lorads_op_spmm": (_i32, [P, _i32, _i32, _i32, P, _f64, P, P, P]),
         "lorads_op_hessian": (_i32, [P, _i32, _i32, _i32, _f64, _f64, P, P, P, P]),
@@ -266,3 +270,13 @@ def lorads_struct_sizes() -> tuple:
     pb, rb = _i64(), _i64()
     load_library().lorads_struct_sizes(ctypes.byref(pb), ctypes.byref(rb))
     return pb.value, rb.value
+
+
+def lorads_solve_static(p, prm: lorads_params, U_hat=None, ldu: int = 0, y=None,
+                        stream=None) -> lorads_result:
+    """Allocation-free solve into caller device buffers (torch CUDA tensors or addresses):
+    U_hat (n x ldu float64, row-major) and y (m float64); see include/lorads.h."""
+    res = lorads_result()
+    load_library().lorads_solve_static(p, ctypes.byref(prm), _stream_ptr(stream), _dev(U_hat),
+                                       ldu, _dev(y), ctypes.byref(res))
+    return res

@@ -50,7 +50,7 @@ def test_default_params_match_oracle_readings(lib):
 
 
 def test_status_strings(lib):
-    for code in range(0, -10, -1):
+    for code in range(0, -11, -1):
         assert L.lorads_status_string(code) != "unknown status"
     assert L.lorads_status_string(-99) == "unknown status"
 
