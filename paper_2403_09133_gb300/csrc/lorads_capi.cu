@@ -303,6 +303,9 @@ static int assemble(lorads_problem* p) {
   dp.b_inf = binf;
   dp.C_fro = p->C_fro;
   dp.C_inf = cinf;
+  bool diag_only = true;
+  for (int64_t i = 0; i < m; ++i) diag_only = diag_only && (con_r[i] == con_c[i]);
+  dp.a_diag_only = diag_only ? 1 : 0;
   p->dp = dp;
   p->assembled = true;
   p->assemble_status = LORADS_OK;

@@ -20,7 +20,7 @@ namespace lorads {
 
 constexpr int KMAX = 2;      // chunks per lane
 constexpr int CHUNK = 4;     // elements per chunk (16 B of float, 32 B of double)
-constexpr int MAXRED = 12;   // values per reduction
+constexpr int MAXRED = 12;   // values per reduction (the last slot carries the barrier status)
 constexpr int MAXMEM = 8;    // L-BFGS memory cap
 
 // ------------------------------------------------------------------------------------
@@ -48,6 +48,8 @@ struct DevProblem {
   // diagonal entry on its own row with b/a > 0): U_0 row j gets norm row_norm[j] (< 0: keep)
   const double* row_norm;
   double b_inf, C_fro, C_inf;
+  // every constraint is a diagonal entry: the Hessian of eq. linU is row-local
+  int a_diag_only;
 };
 
 template <typename T> __device__ __forceinline__ const T* cval(const DevProblem& P);
@@ -219,6 +221,25 @@ __device__ inline double normal_at(uint64_t key, uint64_t e) {
 // ------------------------------------------------------------------------------------
 // scopes: one CTA, or the whole grid of a cooperative launch
 // ------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 struct GridCtl {
   unsigned int count;
   unsigned int gen;
@@ -272,55 +293,49 @@ struct GridScope {
   __device__ int nthreads() const { return gridDim.x * blockDim.x; }
   __device__ bool is_leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
 
-  // bounded barrier over all CTAs; with k > 0 it also sums v (already CTA-reduced and
-  // stored in red[32*MAXRED + i]) over CTAs in CTA order.
+  // Bounded barrier over all CTAs.  With k > 0 it also sums, over CTAs in CTA order, the
+  // CTA sums left in red[32*MAXRED + i] by block_reduce.  Arrival is an acq_rel increment of
+  // ctl->count; the last CTA resets the count and releases the generation; the others poll
+  // the generation with acquire loads (bounded).  Every CTA then reads all partials with
+  // L2 loads issued together and adds them in the same fixed order.
   __device__ bool barrier(int k) {
-    volatile GridCtl* vc = ctl;
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
-      unsigned my_gen = 0;
-      int last = 0;
       if (lane == 0) {
         for (int i = 0; i < k; ++i) partials[blockIdx.x * MAXRED + i] = red[32 * MAXRED + i];
-        my_gen = vc->gen;
-        __threadfence();
-        unsigned arrived = atomicAdd(&ctl->count, 1u);
-        last = (arrived == gridDim.x - 1);
-      }
-      last = __shfl_sync(0xffffffffu, last, 0);
-      if (last) {
-        __threadfence();
-        volatile double* vp = partials;
-        for (int i = 0; i < k; ++i) {
-          double x = 0.0;
-          for (int b = lane; b < (int)gridDim.x; b += 32) x += vp[b * MAXRED + i];
-          for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-          if (lane == 0) vc->result[i] = x;
-        }
-        if (lane == 0) {
-          vc->count = 0;
-          __threadfence();
-          atomicAdd(&ctl->gen, 1u);
-        }
-      } else if (lane == 0) {
-        long long it = 0;
-        while (vc->gen == my_gen) {
-          if (vc->error) break;
-          if (++it > spin_limit) {
-            atomicExch(&ctl->error, 1);
-            break;
+        const unsigned my_gen = ld_acquire_u32(&ctl->gen);
+        const unsigned arrived = atom_add_acq_rel_u32(&ctl->count, 1u);
+        if (arrived == gridDim.x - 1) {
+          ctl->count = 0;
+          red_add_release_u32(&ctl->gen, 1u);
+        } else {
+          long long it = 0;
+          while (ld_acquire_u32(&ctl->gen) == my_gen) {
+            if (ld_acquire_s32(&ctl->error)) break;
+            if (++it > spin_limit) {
+              atomicExch(&ctl->error, 1);
+              break;
+            }
+            __nanosleep(32);
           }
-          __nanosleep(40);
         }
       }
       __syncwarp();
-      if (lane == 0) {
+      if (k > 0) {
+        // fence for the other lanes: their loads follow lane 0's acquire through __syncwarp
         __threadfence();
-        for (int i = 0; i < k; ++i) red[32 * MAXRED + i] = vc->result[i];
+        const int nb = gridDim.x;
+        for (int i = 0; i < k; ++i) {
+          double x = 0.0;
+          for (int b = lane; b < nb; b += 32) x += __ldcg(partials + b * MAXRED + i);
+          for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+          if (lane == 0) red[32 * MAXRED + i] = x;
+        }
       }
+      if (lane == 0) red[32 * MAXRED + MAXRED - 1] = (double)ld_acquire_s32(&ctl->error);
     }
     __syncthreads();
-    return vc->error == 0;
+    return red[32 * MAXRED + MAXRED - 1] == 0.0;
   }
 
   __device__ bool sync() {

@@ -600,6 +600,10 @@ struct Solver {
     double rr = v[0];
     const double target = fmax(prm.cg_rel_tol * sqrt(rr), prm.cg_abs_floor * sqrt(v[1]));
     const T rho_t = (T)rho, gamma_t = (T)gamma;
+    // row-local Hessian (diagonal constraints): the direction update P = R + beta P of the
+    // previous iteration is done inside the next apply, saving one grid-wide sync
+    const bool fuse = P.a_diag_only != 0;
+    T beta_pending = T(0);
     int it = 0;
     while (sqrt(rr) > target && it < prm.cg_max_iter) {
       // HP = H P, p.Hp
@@ -607,6 +611,15 @@ struct Solver {
       for (int j = tm.id; j < n; j += tm.count) {
         Frag<T> Pj, Hj;
         frag_load(Pj, A.Pd, j, ld, tm);
+        if (fuse && it > 0) {
+          Frag<T> Rj;
+          frag_load(Rj, A.R, j, ld, tm);
+#pragma unroll
+          for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+            for (int e = 0; e < CHUNK; ++e) Pj.v[k][e] = fma(beta_pending, Pj.v[k][e], Rj.v[k][e]);
+          frag_store(Pj, A.Pd, j, ld, tm);
+        }
         hessian_row<T>(P, Wt, A.Pd, ld, j, Pj, rho_t, gamma_t, tm, Hj);
         frag_store(Hj, A.HP, j, ld, tm);
         const double d = (double)team_sum(frag_dot_local(Pj, Hj), tm);
@@ -643,6 +656,10 @@ struct Solver {
       if (sqrt(rr_new) <= target) { rr = rr_new; break; }
       const T beta_t = (T)(rr_new / rr);
       rr = rr_new;
+      if (fuse) {
+        beta_pending = beta_t;
+        continue;
+      }
       for (int j = tm.id; j < n; j += tm.count) {
         Frag<T> Pj, Rj;
         frag_load(Pj, A.Pd, j, ld, tm);

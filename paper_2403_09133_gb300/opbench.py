@@ -51,7 +51,8 @@ def main():
     ap.add_argument("--samples", type=int, default=15_694_167)
     ap.add_argument("--rank", type=int, default=0)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--op", default="hessian", choices=["hessian", "spmm", "sddmm", "all"])
+    ap.add_argument("--op", default="hessian", choices=["hessian", "spmm", "sddmm", "all", "solve"])
+    ap.add_argument("--admm-cap", type=int, default=20, help="--op solve: Phase II iterations")
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--seed", type=int, default=2)
@@ -59,6 +60,21 @@ def main():
 
     inst = make(a.family, a.side, a.n1, a.samples, a.seed)
     n, m = inst.n, inst.m
+    if a.op == "solve":
+        # one capped solve (a short launch of the persistent solver kernel, e.g. for ncu)
+        prob = L.Problem(inst)
+        prec = L.LORADS_PREC_MIXED if a.prec == "mixed" else L.LORADS_PREC_FP64
+        out = []
+        for it in range(a.warmup + a.iters):
+            res = prob.solve(precision=prec, max_admm_iter=a.admm_cap)
+            out.append(res)
+        prob.close()
+        last = out[-1]
+        print(json.dumps({"op": "solve", "family": a.family, "n": n, "m": m, "prec": a.prec,
+                          "admm_iters": last["admm_iters"], "cg_iters": last["cg_iters"],
+                          "status": last["status"],
+                          "ms_phase2": last["time_phase2_s"] * 1e3}), flush=True)
+        return
     r = a.rank or int(np.ceil(np.log2(max(m, 2))))
     ld = (r + 3) // 4 * 4
     prec = L.LORADS_PREC_MIXED if a.prec == "mixed" else L.LORADS_PREC_FP64
