@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--oracle-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512)
     return ap.parse_args()
 
 
@@ -275,11 +277,60 @@ def run_gpu(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if not args.no_batch:
+        line["batch"] = batch_bench(args, stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(inst, args.oracle_seconds, rm["admm_iters"])
     if world > 1:
         dist.destroy_process_group()
     return line
+
+
+def batch_bench(args, stream):
+    """512 uneven ER MaxCuts (n ~ U[64, 2048], degree ~ U[3, 12], seeds 1000+i) in one
+    persistent launch (mixed form, autotuned CTA size and lanes per row), against plain FP64
+    one-problem solves on a sample of 16 of them, scaled to the batch."""
+    import torch
+    from paper_2403_09133_gb300 import instances as I
+    from paper_2403_09133_gb300 import lorads as L
+    insts = I.workload_batch(count=args.batch_count)
+    probs = [L.Problem(x) for x in insts]
+    handles = [p.handle for p in probs]
+    prm = probs[0].params(precision=L.LORADS_PREC_MIXED)
+    res, th, mu = L.lorads_solve_batch(handles, prm, stream)      # tunes + warms up
+    prm.threads, prm.team_mult = th, mu
+    times = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, _, _ = L.lorads_solve_batch(handles, prm, stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    t_batch = min(times)
+    sample = list(range(0, len(probs), max(1, len(probs) // 16)))[:16]
+    p64 = probs[0].params(precision=L.LORADS_PREC_FP64)
+    t_seq = 0.0
+    for i in sample:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.lorads_solve(handles[i], p64, stream)
+        e1.record(stream)
+        e1.synchronize()
+        t_seq += e0.elapsed_time(e1) * 1e-3
+    t_seq_scaled = t_seq * len(probs) / len(sample)
+    for p in probs:
+        p.close()
+    return {"count": len(insts), "seconds_one_launch": t_batch,
+            "solves_per_s": len(insts) / t_batch, "tuned_threads": th, "tuned_team_mult": mu,
+            "converged": int(sum(r["status"] == 0 for r in res)),
+            "admm_iters_total": int(sum(r["admm_iters"] for r in res)),
+            "plain_fp64_sequential_s_est": t_seq_scaled,
+            "speedup_vs_sequential_fp64": t_seq_scaled / t_batch,
+            "sample": f"{len(sample)} one-problem FP64 solves scaled x{len(probs) / len(sample):.0f}"}
 
 
 def run_reference(args):

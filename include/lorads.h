@@ -91,6 +91,8 @@ typedef struct lorads_params {
   double time_limit_s;     /* wall-clock cap of one solve on the device (60 s)               */
   int32_t threads;         /* CTA size of the solver kernels (0 = library choice)            */
   int32_t grid;            /* solver CTAs (0 = library choice; 1 forces one-CTA scope)       */
+  int32_t team_mult;       /* lanes per factor row = team_mult x the minimum for the rank    */
+                           /* (1, 2, 4, 8; 0 = 1, or autotuned by lorads_solve_batch)         */
 } lorads_params;
 
 /* ---------------------------------------------------------------- result */
@@ -157,6 +159,20 @@ int lorads_set_start(lorads_problem *p, int32_t r, const double *U0, const doubl
  * the call returns when the solve has finished.  res may be NULL.  The return value is
  * the solve status (also res->status). */
 int lorads_solve(lorads_problem *p, const lorads_params *prm, void *stream, lorads_result *res);
+
+/* Solves count independent problems (same device) in one persistent launch: one CTA per
+ * problem, CTAs take problems from a device-side queue, largest problems first, so uneven
+ * sizes balance across the SMs.  prm applies to every problem ("auto" fields resolved per
+ * problem).  When prm->threads or prm->team_mult is 0 the library autotunes them first: it
+ * times every (CTA size in {128, 256}) x (lanes-per-row multiplier in {1, 2, 4}) on a
+ * sample of up to 24 problems (Phase II capped at 200 iterations) and keeps the fastest;
+ * the choice is returned in *tuned_threads / *tuned_team_mult (either may be NULL).  res
+ * (may be NULL) receives count reports; each problem's solution is then available through
+ * lorads_get_solution.  Returns LORADS_OK when the batch ran (per-problem statuses are in
+ * res), or the first set-up error. */
+int lorads_solve_batch(lorads_problem *const *ps, int32_t count, const lorads_params *prm,
+                       void *stream, lorads_result *res, int32_t *tuned_threads,
+                       int32_t *tuned_team_mult);
 
 /* The last solve's factors and dual into caller host buffers: U, V, U_hat as n x r
  * row-major (r = result rank; any pointer may be NULL), y of length m. */

@@ -326,11 +326,9 @@ static int resolve_r0(const lorads_problem* p, const lorads_params* prm, int cap
   return (int)std::max<int64_t>(r, 1);
 }
 
-template <typename T>
-static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s,
-                     lorads_result* res) {
-  const int64_t n = p->n, m = p->m;
-  DevParams dv{};
+// resolves the caller's parameters for problem p (auto values, gamma, ranks, limits)
+static int fill_params(const lorads_problem* p, const lorads_params* prm, DevParams& dv) {
+  dv = DevParams{};
   const int cap = resolve_rank_cap(p, prm);
   dv.rank_cap = cap;
   dv.r0 = resolve_r0(p, prm, cap);
@@ -360,16 +358,27 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   dv.r_start = p->start_r;
   dv.rho0 = p->start_rho > 0 ? p->start_rho : 100.0;
   dv.time_limit_ns = (long long)(prm->time_limit_s * 1e9);
+  dv.team_mult = prm->team_mult > 0 ? prm->team_mult : 1;
+  if (dv.team_mult != 1 && dv.team_mult != 2 && dv.team_mult != 4 && dv.team_mult != 8)
+    return LORADS_ERR_ARG;
   if (!dv.phase1) {
     if (!p->has_start) return LORADS_ERR_STATE;
     if (p->start_r > 256) return LORADS_ERR_ARG;
   }
-  const int rmax = std::max(cap, dv.phase1 ? 0 : p->start_r);
+  return LORADS_OK;
+}
+
+// allocates (or reuses) p's state arena, lays out the solver arrays, uploads the Phase II
+// start if any and the argument block, and clears what must start at zero
+template <typename T>
+static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
+                         SolverArgs<T>& h, SolverArgs<T>** dargs_out) {
+  const int64_t n = p->n, m = p->m;
+  const int rmax = std::max(dv.rank_cap, dv.phase1 ? 0 : p->start_r);
   const long long ld_cap = round4(rmax);
   const size_t NS = (size_t)n * ld_cap;
   const int ring = dv.lbfgs_mem + 1;
   const bool mixed = sizeof(T) == 4;
-  // state arena
   int dev_sms = 0;
   CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
   size_t bytes = Arena::need(NS, 8) * 7 + Arena::need(NS, sizeof(T)) * (mixed ? 6 : 4) +
@@ -380,7 +389,7 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   int st = p->state_mem.reserve(bytes);
   if (st != LORADS_OK) return st;
   Arena& a = p->state_mem;
-  SolverArgs<T> h{};
+  h = SolverArgs<T>{};
   h.P = p->dp;
   h.prm = dv;
   h.U = a.take<double>(NS);
@@ -423,6 +432,8 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
     for (int64_t j = 0; j < n; ++j)
       for (int c = 0; c < r; ++c) Upad[(size_t)j * ld + c] = p->start_U[(size_t)j * r + c];
     CU(cudaMemcpyAsync(h.U, Upad.data(), Upad.size() * 8, cudaMemcpyHostToDevice, s));
+    // the pageable source must stay alive until the copy is done
+    CU(cudaStreamSynchronize(s));
     if (!p->start_lam.empty())
       CU(cudaMemcpyAsync(h.lam, p->start_lam.data(), m * 8, cudaMemcpyHostToDevice, s));
     else
@@ -432,25 +443,12 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   CU(cudaMemsetAsync(p->dout, 0, sizeof(SolveOut), s));
   CU(cudaMemsetAsync(p->dctl, 0, sizeof(GridCtl), s));
   CU(cudaMemsetAsync(p->dqueue, 0, 16, s));
-  // scope: one CTA for small problems, the whole GPU for large ones
-  int grid = prm->grid;
-  if (grid <= 0) grid = (n < 4096) ? 1 : dev_sms;
-  cudaError_t le;
-  if (grid == 1) {
-    le = Launch<T>::solve_block(dargs, 1, p->dqueue, 1, s);
-  } else {
-    int per_sm = 0;
-    CU(Launch<T>::grid_capacity(&per_sm));
-    const int maxg = std::max(1, per_sm) * dev_sms;
-    grid = std::min(std::min(grid, maxg), dev_sms * 8);
-    const long long spin = 50LL * 1000 * 1000;   // ~ a few seconds of polling
-    le = Launch<T>::solve_grid(dargs, p->dctl, p->dpartials, spin, grid, s);
-  }
-  CU(le);
-  SolveOut out{};
-  CU(cudaMemcpyAsync(&out, p->dout, sizeof(out), cudaMemcpyDeviceToHost, s));
-  CU(cudaStreamSynchronize(s));
-  lorads_result r{};
+  *dargs_out = dargs;
+  return LORADS_OK;
+}
+
+static void to_result(const SolveOut& out, lorads_result& r) {
+  r = lorads_result{};
   r.status = out.status;
   r.rank = out.rank;
   r.objective = out.objective;
@@ -471,12 +469,151 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   r.rank_growths = out.growths;
   r.time_phase1_s = out.t_phase1_ns * 1e-9;
   r.time_phase2_s = out.t_phase2_ns * 1e-9;
+}
+
+static void record_solution(lorads_problem* p, const SolveOut& out, const lorads_result& r) {
   p->last = r;
   p->sol_r = out.rank;
   p->sol_ld = out.ld;
   p->has_solution = out.ld > 0;
+}
+
+template <typename T>
+static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s,
+                     lorads_result* res) {
+  DevParams dv;
+  int st = fill_params(p, prm, dv);
+  if (st != LORADS_OK) return st;
+  SolverArgs<T> h;
+  SolverArgs<T>* dargs = nullptr;
+  st = prepare_state<T>(p, dv, s, h, &dargs);
+  if (st != LORADS_OK) return st;
+  int dev_sms = 0;
+  CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
+  // scope: one CTA for small problems, the whole GPU for large ones
+  int grid = prm->grid;
+  if (grid <= 0) grid = (p->n < 4096) ? 1 : dev_sms;
+  const int threads = prm->threads > 0 ? prm->threads : SOLVER_THREADS;
+  if (threads % 32 != 0 || threads > SOLVER_THREADS) return LORADS_ERR_ARG;
+  cudaError_t le;
+  if (grid == 1) {
+    le = Launch<T>::solve_block(dargs, 1, p->dqueue, 1, threads, s);
+  } else {
+    int per_sm = 0;
+    CU(Launch<T>::grid_capacity(&per_sm));
+    const int maxg = std::max(1, per_sm) * dev_sms;
+    grid = std::min(std::min(grid, maxg), dev_sms * 8);
+    const long long spin = 50LL * 1000 * 1000;   // ~ a few seconds of polling
+    le = Launch<T>::solve_grid(dargs, p->dctl, p->dpartials, spin, grid, s);
+  }
+  CU(le);
+  SolveOut out{};
+  CU(cudaMemcpyAsync(&out, p->dout, sizeof(out), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  lorads_result r;
+  to_result(out, r);
+  record_solution(p, out, r);
   if (res) *res = r;
   return r.status;
+}
+
+// ---------------------------------------------------------------------------------------
+// batches: one CTA per problem, CTAs take problems from a device queue, largest first
+// ---------------------------------------------------------------------------------------
+template <typename T>
+static int run_batch_once(lorads_problem* const* ps, int count, const lorads_params* prm,
+                          cudaStream_t s, int threads, int team_mult, lorads_result* res,
+                          double* seconds) {
+  const int device = ps[0]->device;
+  std::vector<SolverArgs<T>> hs(count);
+  std::vector<std::pair<double, int>> order(count);
+  lorads_params q = *prm;
+  q.team_mult = team_mult;
+  for (int i = 0; i < count; ++i) {
+    lorads_problem* p = ps[i];
+    if (p->device != device) return LORADS_ERR_ARG;
+    int st = assemble(p);
+    if (st != LORADS_OK) return st;
+    DevParams dv;
+    st = fill_params(p, &q, dv);
+    if (st != LORADS_OK) return st;
+    SolverArgs<T>* unused = nullptr;
+    st = prepare_state<T>(p, dv, s, hs[i], &unused);
+    if (st != LORADS_OK) return st;
+    // work estimate: rows times (A + C entries per row), for largest-first scheduling
+    order[i] = {-(double)p->n * (double)(p->C_row.size() + p->A_con.size() + p->n) / p->n, i};
+  }
+  std::stable_sort(order.begin(), order.end());
+  std::vector<SolverArgs<T>> sorted(count);
+  for (int k = 0; k < count; ++k) sorted[k] = hs[order[k].second];
+  SolverArgs<T>* dargs = nullptr;
+  int* dqueue = nullptr;
+  CU(cudaMalloc((void**)&dargs, sizeof(SolverArgs<T>) * count + 256));
+  dqueue = reinterpret_cast<int*>(reinterpret_cast<char*>(dargs) + sizeof(SolverArgs<T>) * count);
+  int st = LORADS_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  do {
+    if ((st = check_cuda(cudaMemcpyAsync(dargs, sorted.data(), sizeof(SolverArgs<T>) * count,
+                                         cudaMemcpyHostToDevice, s))) != LORADS_OK) break;
+    if ((st = check_cuda(cudaMemsetAsync(dqueue, 0, 16, s))) != LORADS_OK) break;
+    int dev_sms = 0, per_sm = 0;
+    if ((st = check_cuda(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount,
+                                                device))) != LORADS_OK) break;
+    if ((st = check_cuda(Launch<T>::block_capacity(threads, &per_sm))) != LORADS_OK) break;
+    const int grid = std::max(1, std::min(count, std::max(1, per_sm) * dev_sms));
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    if ((st = check_cuda(Launch<T>::solve_block(dargs, count, dqueue, grid, threads, s))) !=
+        LORADS_OK) break;
+    cudaEventRecord(e1, s);
+    if ((st = check_cuda(cudaStreamSynchronize(s))) != LORADS_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (seconds) *seconds = ms * 1e-3;
+    for (int i = 0; i < count; ++i) {
+      SolveOut out{};
+      if ((st = check_cuda(cudaMemcpy(&out, ps[i]->dout, sizeof(out), cudaMemcpyDeviceToHost))) !=
+          LORADS_OK) break;
+      lorads_result r;
+      to_result(out, r);
+      record_solution(ps[i], out, r);
+      if (res) res[i] = r;
+    }
+  } while (false);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(dargs);
+  return st;
+}
+
+// Autotuner: times a sample of the batch (every k-th problem, largest included) under each
+// (CTA size, lanes-per-row multiplier) candidate and returns the fastest.
+template <typename T>
+static int autotune_batch(lorads_problem* const* ps, int count, const lorads_params* prm,
+                          cudaStream_t s, int* threads_out, int* mult_out) {
+  const int cand_threads[] = {128, 256};
+  const int cand_mult[] = {1, 2, 4};
+  std::vector<lorads_problem*> sample;
+  const int want = std::min(count, 24);
+  for (int k = 0; k < want; ++k) sample.push_back(ps[(int64_t)k * count / want]);
+  lorads_params q = *prm;
+  q.max_admm_iter = std::min(prm->max_admm_iter, 200);
+  double best = 1e300;
+  *threads_out = SOLVER_THREADS;
+  *mult_out = 1;
+  for (int th : cand_threads)
+    for (int mu : cand_mult) {
+      double sec = 0.0;
+      int st = run_batch_once<T>(sample.data(), (int)sample.size(), &q, s, th, mu, nullptr, &sec);
+      if (st != LORADS_OK) return st;
+      if (sec < best) {
+        best = sec;
+        *threads_out = th;
+        *mult_out = mu;
+      }
+    }
+  return LORADS_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -582,6 +719,7 @@ void lorads_default_params(lorads_params* prm) {
   prm->time_limit_s = 60.0;
   prm->threads = 0;
   prm->grid = 0;
+  prm->team_mult = 0;
 }
 
 int lorads_set_start(lorads_problem* p, int32_t r, const double* U0, const double* lambda0,
@@ -622,6 +760,41 @@ int lorads_solve(lorads_problem* p, const lorads_params* prm, void* stream, lora
   if (res) std::memset(res, 0, sizeof(*res));
   const int st = solve_impl(p, prm, stream, res);
   if (res) res->status = st;
+  return st;
+}
+
+int lorads_solve_batch(lorads_problem* const* ps, int32_t count, const lorads_params* prm,
+                       void* stream, lorads_result* res, int32_t* tuned_threads,
+                       int32_t* tuned_team_mult) {
+  if (!ps || count <= 0) return LORADS_ERR_ARG;
+  for (int32_t i = 0; i < count; ++i)
+    if (!ps[i]) return LORADS_ERR_ARG;
+  lorads_params defaults;
+  if (!prm) {
+    lorads_default_params(&defaults);
+    prm = &defaults;
+  }
+  if (prm->precision != LORADS_PREC_FP64 && prm->precision != LORADS_PREC_MIXED)
+    return LORADS_ERR_ARG;
+  if (!(prm->tol > 0) || prm->max_admm_iter < 1 || prm->cg_max_iter < 1) return LORADS_ERR_ARG;
+  if (res) std::memset(res, 0, sizeof(lorads_result) * count);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool mixed = prm->precision == LORADS_PREC_MIXED;
+  int threads = prm->threads, mult = prm->team_mult;
+  int st = LORADS_OK;
+  if (threads <= 0 || mult <= 0) {
+    int th = SOLVER_THREADS, mu = 1;
+    st = mixed ? autotune_batch<float>(ps, count, prm, s, &th, &mu)
+               : autotune_batch<double>(ps, count, prm, s, &th, &mu);
+    if (st != LORADS_OK) return st;
+    if (threads <= 0) threads = th;
+    if (mult <= 0) mult = mu;
+  }
+  if (threads % 32 != 0 || threads > SOLVER_THREADS) return LORADS_ERR_ARG;
+  if (tuned_threads) *tuned_threads = threads;
+  if (tuned_team_mult) *tuned_team_mult = mult;
+  st = mixed ? run_batch_once<float>(ps, count, prm, s, threads, mult, res, nullptr)
+             : run_batch_once<double>(ps, count, prm, s, threads, mult, res, nullptr);
   return st;
 }
 
@@ -846,6 +1019,7 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   dv.r_start = p->start_r;
   dv.rho0 = p->start_rho > 0 ? p->start_rho : 100.0;
   dv.time_limit_ns = (long long)(prm->time_limit_s * 1e9);
+  dv.team_mult = 1;
   if (!dv.phase1 && (!p->has_start || p->start_r > 256)) return LORADS_ERR_STATE;
   const int rmax = std::max(cap, dv.phase1 ? 0 : p->start_r);
   const long long ld_cap = round4(rmax);
@@ -913,7 +1087,7 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   if (grid <= 0) grid = (n < 4096) ? 1 : dev_sms;
   cudaError_t le;
   if (grid == 1) {
-    le = Launch<T>::solve_block(dargs, 1, dqueue, 1, s);
+    le = Launch<T>::solve_block(dargs, 1, dqueue, 1, SOLVER_THREADS, s);
   } else {
     int per_sm = 0;
     CU(Launch<T>::grid_capacity(&per_sm));

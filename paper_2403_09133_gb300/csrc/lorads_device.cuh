@@ -79,9 +79,10 @@ __host__ __device__ inline int team_size_for(int ld) {
   return G > 32 ? 32 : G;
 }
 
-__device__ inline Team make_team(int ld, int tid, int nthreads) {
+__device__ inline Team make_team(int ld, int tid, int nthreads, int mult = 1) {
   Team t;
-  t.G = team_size_for(ld);
+  t.G = team_size_for(ld) * (mult > 0 ? mult : 1);
+  if (t.G > 32) t.G = 32;
   t.lane = tid & (t.G - 1);
   t.id = tid / t.G;
   t.count = nthreads / t.G;

@@ -76,7 +76,8 @@ __global__ void op_hessian_kernel(DevProblem P, int ld, T rho, T gamma, const T*
 template <typename T>
 struct Launch {
   static cudaError_t solve_block(const SolverArgs<T>* args, int count, int* queue, int grid,
-                                 cudaStream_t s);
+                                 int threads, cudaStream_t s);
+  static cudaError_t block_capacity(int threads, int* blocks_per_sm);
   static cudaError_t solve_grid(const SolverArgs<T>* args, GridCtl* ctl, double* partials,
                                 long long spin, int grid, cudaStream_t s);
   static cudaError_t grid_capacity(int* blocks_per_sm);
@@ -89,8 +90,9 @@ struct Launch {
 };
 
 #define LORADS_DECLARE_LAUNCH(T)                                                               \
-  template <> cudaError_t Launch<T>::solve_block(const SolverArgs<T>*, int, int*, int,          \
+  template <> cudaError_t Launch<T>::solve_block(const SolverArgs<T>*, int, int*, int, int,     \
                                                  cudaStream_t);                                 \
+  template <> cudaError_t Launch<T>::block_capacity(int, int*);                                 \
   template <> cudaError_t Launch<T>::solve_grid(const SolverArgs<T>*, GridCtl*, double*,        \
                                                 long long, int, cudaStream_t);                  \
   template <> cudaError_t Launch<T>::grid_capacity(int*);                                       \
@@ -106,9 +108,14 @@ LORADS_DECLARE_LAUNCH(float)
 #define LORADS_DEFINE_LAUNCH(T)                                                                \
   template <>                                                                                  \
   cudaError_t Launch<T>::solve_block(const SolverArgs<T>* args, int count, int* queue, int grid,\
-                                     cudaStream_t s) {                                         \
-    solve_block_kernel<T><<<grid, SOLVER_THREADS, 0, s>>>(args, count, queue);                 \
+                                     int threads, cudaStream_t s) {                            \
+    solve_block_kernel<T><<<grid, threads, 0, s>>>(args, count, queue);                        \
     return cudaGetLastError();                                                                 \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t Launch<T>::block_capacity(int threads, int* blocks_per_sm) {                     \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_block_kernel<T>, \
+                                                         threads, 0);                          \
   }                                                                                            \
   template <>                                                                                  \
   cudaError_t Launch<T>::solve_grid(const SolverArgs<T>* args, GridCtl* ctl, double* partials, \

@@ -34,6 +34,7 @@ struct DevParams {
   int r_start;
   double rho0;
   long long time_limit_ns;
+  int team_mult;   // lanes per row = team_mult * the minimum for ld (autotuned for batches)
 };
 
 struct SolveOut {
@@ -161,7 +162,7 @@ struct Solver {
   __device__ void set_rank(int rr) {
     r = rr;
     ld = round4(rr);
-    tm = make_team(ld, sc.tid(), sc.nthreads());
+    tm = make_team(ld, sc.tid(), sc.nthreads(), prm.team_mult);
     tmc = tm;
   }
 

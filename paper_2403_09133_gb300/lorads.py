@@ -43,7 +43,7 @@ class lorads_params(ctypes.Structure):
         ("inner_tol_factor", _f64), ("inner_tol_max", _f64), ("max_outer", _i32),
         ("sigma_factor", _f64), ("sigma_decrease", _f64), ("new_col_std", _f64),
         ("seed", _u64), ("precision", _i32), ("phase1", _i32), ("time_limit_s", _f64),
-        ("threads", _i32), ("grid", _i32),
+        ("threads", _i32), ("grid", _i32), ("team_mult", _i32),
     ]
 
 
@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lorads_set_start": (_i32, [P, _i32, P, P, _f64]),
         "lorads_solve": (_i32, [P, ctypes.POINTER(lorads_params), P, ctypes.POINTER(lorads_result)]),
         "lorads_get_solution": (_i32, [P, P, P, P, P, ctypes.POINTER(_i32)]),
+        "lorads_solve_batch": (_i32, [P, _i32, ctypes.POINTER(lorads_params), P,
+                                      P, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
         "lorads_destroy": (None, [P]),
         "lorads_status_string": (ctypes.c_char_p, [_i32]),
         "lorads_struct_sizes": (None, [ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -280,3 +282,18 @@ def lorads_solve_static(p, prm: lorads_params, U_hat=None, ldu: int = 0, y=None,
     load_library().lorads_solve_static(p, ctypes.byref(prm), _stream_ptr(stream), _dev(U_hat),
                                        ldu, _dev(y), ctypes.byref(res))
     return res
+
+
+def lorads_solve_batch(handles, prm: lorads_params, stream=None):
+    """Solves the problems behind `handles` in one launch; returns (results, threads, mult)."""
+    count = len(handles)
+    arr = (ctypes.c_void_p * count)(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                      for h in handles])
+    res = (lorads_result * count)()
+    th, mu = _i32(), _i32()
+    code = load_library().lorads_solve_batch(ctypes.cast(arr, ctypes.c_void_p), count,
+                                             ctypes.byref(prm), _stream_ptr(stream),
+                                             ctypes.cast(res, ctypes.c_void_p),
+                                             ctypes.byref(th), ctypes.byref(mu))
+    _check(code, "lorads_solve_batch")
+    return [r.as_dict() for r in res], th.value, mu.value
