@@ -261,9 +261,11 @@ def run_gpu(args):
                    "l2": "256 MB buffer written between timed solves"},
         "solve": {k: rm[k] for k in ("status", "objective", "r_P", "r_P_split", "r_stop", "r_D",
                                     "gap", "admm_iters", "cg_iters", "hessian_applies",
-                                    "alm_outer", "lbfgs_iters", "rank")},
+                                    "alm_outer", "lbfgs_iters", "rank", "time_phase1_s",
+                                    "time_phase2_s")},
         "kkt_reached": rm["status"] == 0,
         "plain_fp64": {"ms_per_solve": t_fp64 * 1e3, "status": rf["status"],
+                       "time_phase1_s": rf["time_phase1_s"], "time_phase2_s": rf["time_phase2_s"],
                        "objective": rf["objective"], "admm_iters": rf["admm_iters"],
                        "cg_iters": rf["cg_iters"],
                        "cg_operator_gbs": bytes_fp64 / t_fp64 / 1e9},

@@ -248,7 +248,7 @@ static int assemble(lorads_problem* p) {
                  Arena::need(A_col.size(), 4) * 2 + Arena::need(A_val.size(), 8) +
                  Arena::need(A_val.size(), 4) + Arena::need(C_col.size(), 4) +
                  Arena::need(C_val.size(), 8) + Arena::need(C_val.size(), 4) +
-                 Arena::need(n, 8) + 4096;
+                 Arena::need(n, 8) + Arena::need(n, 4) * 2 + Arena::need(n, 8) + 4096;
   int st = p->prob_mem.reserve(bytes);
   if (st != LORADS_OK) return st;
   Arena& a = p->prob_mem;
@@ -305,7 +305,27 @@ static int assemble(lorads_problem* p) {
   dp.C_inf = cinf;
   bool diag_only = true;
   for (int64_t i = 0; i < m; ++i) diag_only = diag_only && (con_r[i] == con_c[i]);
+  // row-local form needs at most one constraint per row
+  std::vector<int32_t> row_con(n, -1);
+  std::vector<double> row_a(n, 0.0);
+  for (int64_t i = 0; i < m && diag_only; ++i) {
+    if (row_con[con_r[i]] >= 0) diag_only = false;
+    row_con[con_r[i]] = (int32_t)i;
+    row_a[con_r[i]] = con_a[i];
+  }
   dp.a_diag_only = diag_only ? 1 : 0;
+  if (diag_only) {
+    std::vector<float> row_af(row_a.begin(), row_a.end());
+    int* d_row_con = a.take<int>(n);
+    double* d_row_a = a.take<double>(n);
+    float* d_row_af = a.take<float>(n);
+    CU(up(d_row_con, row_con.data(), n * 4));
+    CU(up(d_row_a, row_a.data(), n * 8));
+    CU(up(d_row_af, row_af.data(), n * 4));
+    dp.row_con = d_row_con;
+    dp.row_a = d_row_a;
+    dp.row_af = d_row_af;
+  }
   p->dp = dp;
   p->assembled = true;
   p->assemble_status = LORADS_OK;
@@ -381,11 +401,11 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   const bool mixed = sizeof(T) == 4;
   int dev_sms = 0;
   CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
-  size_t bytes = Arena::need(NS, 8) * 7 + Arena::need(NS, sizeof(T)) * (mixed ? 6 : 4) +
+  size_t bytes = Arena::need(NS, 8) * 7 + Arena::need(NS, sizeof(T)) * (mixed ? 7 : 5) +
                  Arena::need(m, 8) * 2 + Arena::need(NS * ring, 8) * 2 +
                  Arena::need(1, sizeof(SolverArgs<T>)) + Arena::need(1, sizeof(SolveOut)) +
-                 Arena::need(1, sizeof(GridCtl)) + Arena::need((size_t)dev_sms * 8 * MAXRED, 8) +
-                 Arena::need(4, 4) + 4096;
+                 Arena::need(1, sizeof(GridCtl)) +
+                 Arena::need((size_t)dev_sms * 8 * MAXRED * 3, 8) + Arena::need(4, 4) + 4096;
   int st = p->state_mem.reserve(bytes);
   if (st != LORADS_OK) return st;
   Arena& a = p->state_mem;
@@ -405,6 +425,7 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   h.R = a.take<T>(NS);
   h.Pd = a.take<T>(NS);
   h.HP = a.take<T>(NS);
+  h.Sv = a.take<T>(NS);
   h.lam = a.take<double>(m);
   h.e = a.take<double>(m);
   h.grad = a.take<double>(NS);
@@ -418,7 +439,7 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   p->dout = a.take<SolveOut>(1);
   h.out = p->dout;
   p->dctl = a.take<GridCtl>(1);
-  p->dpartials = a.take<double>((size_t)dev_sms * 8 * MAXRED);
+  p->dpartials = a.take<double>((size_t)dev_sms * 8 * MAXRED * 3);
   p->dqueue = a.take<int>(4);
   p->dU = h.U;
   p->dV = h.V;
@@ -442,6 +463,7 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   CU(cudaMemcpyAsync(dargs, &h, sizeof(h), cudaMemcpyHostToDevice, s));
   CU(cudaMemsetAsync(p->dout, 0, sizeof(SolveOut), s));
   CU(cudaMemsetAsync(p->dctl, 0, sizeof(GridCtl), s));
+  CU(cudaMemsetAsync(p->dpartials, 0xFF, sizeof(double) * (size_t)dev_sms * 8 * MAXRED * 3, s));
   CU(cudaMemsetAsync(p->dqueue, 0, 16, s));
   *dargs_out = dargs;
   return LORADS_OK;
@@ -493,18 +515,27 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   // scope: one CTA for small problems, the whole GPU for large ones
   int grid = prm->grid;
   if (grid <= 0) grid = (p->n < 4096) ? 1 : dev_sms;
-  const int threads = prm->threads > 0 ? prm->threads : SOLVER_THREADS;
+  const int threads = (grid == 1 && prm->threads > 0) ? prm->threads : SOLVER_THREADS;
   if (threads % 32 != 0 || threads > SOLVER_THREADS) return LORADS_ERR_ARG;
   cudaError_t le;
   if (grid == 1) {
     le = Launch<T>::solve_block(dargs, 1, p->dqueue, 1, threads, s);
   } else {
+    // CTA size: enough teams for one row each at the initial rank, within [128, 320]
+    int gthreads = prm->threads > 0 ? prm->threads : 0;
+    if (gthreads == 0) {
+      const int G = team_size_for(round4(dv.phase1 ? dv.r0 : p->start_r)) * dv.team_mult;
+      const long long lanes = (long long)p->n * std::min(G, 32);
+      const int per = (int)((lanes + grid - 1) / grid);
+      gthreads = std::min(GRID_THREADS_MAX, std::max(128, ((per + 31) / 32) * 32));
+    }
+    if (gthreads % 32 != 0 || gthreads > GRID_THREADS_MAX) return LORADS_ERR_ARG;
     int per_sm = 0;
-    CU(Launch<T>::grid_capacity(&per_sm));
+    CU(Launch<T>::grid_capacity(gthreads, &per_sm));
     const int maxg = std::max(1, per_sm) * dev_sms;
     grid = std::min(std::min(grid, maxg), dev_sms * 8);
     const long long spin = 50LL * 1000 * 1000;   // ~ a few seconds of polling
-    le = Launch<T>::solve_grid(dargs, p->dctl, p->dpartials, spin, grid, s);
+    le = Launch<T>::solve_grid(dargs, p->dctl, p->dpartials, spin, grid, gthreads, s);
   }
   CU(le);
   SolveOut out{};
@@ -1049,6 +1080,7 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   h.R = a.take<T>(NS);
   h.Pd = a.take<T>(NS);
   h.HP = a.take<T>(NS);
+  h.Sv = a.take<T>(NS);
   h.lam = a.take<double>(m);
   h.e = a.take<double>(m);
   h.grad = a.take<double>(NS);
@@ -1061,9 +1093,9 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   SolverArgs<T>* dargs = a.take<SolverArgs<T>>(1);
   SolveOut* dout = a.take<SolveOut>(1);
   GridCtl* dctl = a.take<GridCtl>(1);
-  double* dpartials = a.take<double>((size_t)dev_sms * 8 * MAXRED);
+  double* dpartials = a.take<double>((size_t)dev_sms * 8 * MAXRED * 3);
   int* dqueue = a.take<int>(4);
-  if (!h.U || !h.V || !h.Ut || !h.Vt || !h.Dl || !h.R || !h.Pd || !h.HP || !h.lam || !h.e ||
+  if (!h.U || !h.V || !h.Ut || !h.Vt || !h.Dl || !h.R || !h.Pd || !h.HP || !h.Sv || !h.lam || !h.e ||
       !h.grad || !h.grad_old || !h.dir || !h.tmp || !h.S || !h.Y || !dargs || !dout || !dctl ||
       !dpartials || !dqueue)
     return LORADS_ERR_TOO_LARGE;
@@ -1082,6 +1114,7 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   CU(cudaMemcpyAsync(dargs, &h, sizeof(h), cudaMemcpyHostToDevice, s));
   CU(cudaMemsetAsync(dout, 0, sizeof(SolveOut), s));
   CU(cudaMemsetAsync(dctl, 0, sizeof(GridCtl), s));
+  CU(cudaMemsetAsync(dpartials, 0xFF, sizeof(double) * (size_t)dev_sms * 8 * MAXRED * 3, s));
   CU(cudaMemsetAsync(dqueue, 0, 16, s));
   int grid = prm->grid;
   if (grid <= 0) grid = (n < 4096) ? 1 : dev_sms;
@@ -1090,9 +1123,10 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
     le = Launch<T>::solve_block(dargs, 1, dqueue, 1, SOLVER_THREADS, s);
   } else {
     int per_sm = 0;
-    CU(Launch<T>::grid_capacity(&per_sm));
+    CU(Launch<T>::grid_capacity(SOLVER_THREADS, &per_sm));
     grid = std::min(std::min(grid, std::max(1, per_sm) * dev_sms), dev_sms * 8);
-    le = Launch<T>::solve_grid(dargs, dctl, dpartials, 50LL * 1000 * 1000, grid, s);
+    le = Launch<T>::solve_grid(dargs, dctl, dpartials, 50LL * 1000 * 1000, grid, SOLVER_THREADS,
+                               s);
   }
   CU(le);
   SolveOut out{};

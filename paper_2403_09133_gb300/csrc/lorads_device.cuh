@@ -48,13 +48,20 @@ struct DevProblem {
   // diagonal entry on its own row with b/a > 0): U_0 row j gets norm row_norm[j] (< 0: keep)
   const double* row_norm;
   double b_inf, C_fro, C_inf;
-  // every constraint is a diagonal entry: the Hessian of eq. linU is row-local
+  // every constraint is a diagonal entry: the Hessian of eq. linU is row-local; then
+  // row_con[j] is the constraint on row j (-1: none) and row_a[j] its value (0: none)
   int a_diag_only;
+  const int* row_con;
+  const double* row_a;
+  const float* row_af;
 };
 
 template <typename T> __device__ __forceinline__ const T* cval(const DevProblem& P);
 template <> __device__ __forceinline__ const double* cval<double>(const DevProblem& P) { return P.C_val; }
 template <> __device__ __forceinline__ const float* cval<float>(const DevProblem& P) { return P.C_valf; }
+template <typename T> __device__ __forceinline__ const T* rowa(const DevProblem& P);
+template <> __device__ __forceinline__ const double* rowa<double>(const DevProblem& P) { return P.row_a; }
+template <> __device__ __forceinline__ const float* rowa<float>(const DevProblem& P) { return P.row_af; }
 template <typename T> __device__ __forceinline__ const T* aval(const DevProblem& P);
 template <> __device__ __forceinline__ const double* aval<double>(const DevProblem& P) { return P.A_val; }
 template <> __device__ __forceinline__ const float* aval<float>(const DevProblem& P) { return P.A_valf; }
@@ -297,11 +304,13 @@ struct GridScope {
   // Bounded barrier over all CTAs.  With k > 0 it also sums, over CTAs in CTA order, the
   // CTA sums left in red[32*MAXRED + i] by block_reduce.  Arrival is an acq_rel increment of
   // ctl->count; the last CTA resets the count and releases the generation; the others poll
-  // the generation with acquire loads (bounded).  Every CTA then reads all partials with
-  // L2 loads issued together and adds them in the same fixed order.
+  // the generation with acquire loads (bounded).  Every CTA then loads all partials -- the
+  // loads of one lane are issued together, eight CTAs at a time, so their L2 round trips
+  // overlap -- and adds them in the same fixed order.
   __device__ bool barrier(int k) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
+      int ok = 1;
       if (lane == 0) {
         for (int i = 0; i < k; ++i) partials[blockIdx.x * MAXRED + i] = red[32 * MAXRED + i];
         const unsigned my_gen = ld_acquire_u32(&ctl->gen);
@@ -312,28 +321,48 @@ struct GridScope {
         } else {
           long long it = 0;
           while (ld_acquire_u32(&ctl->gen) == my_gen) {
-            if (ld_acquire_s32(&ctl->error)) break;
-            if (++it > spin_limit) {
+            if ((++it & 63) == 0 && ld_acquire_s32(&ctl->error)) {
+              ok = 0;
+              break;
+            }
+            if (it > spin_limit) {
               atomicExch(&ctl->error, 1);
+              ok = 0;
               break;
             }
             __nanosleep(32);
           }
         }
+        red[32 * MAXRED + MAXRED - 1] = ok ? 0.0 : 1.0;
       }
+      // lane 0's acquire orders the other lanes' loads through __syncwarp
       __syncwarp();
       if (k > 0) {
-        // fence for the other lanes: their loads follow lane 0's acquire through __syncwarp
-        __threadfence();
         const int nb = gridDim.x;
-        for (int i = 0; i < k; ++i) {
-          double x = 0.0;
-          for (int b = lane; b < nb; b += 32) x += __ldcg(partials + b * MAXRED + i);
-          for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-          if (lane == 0) red[32 * MAXRED + i] = x;
+        for (int i0 = 0; i0 < k; i0 += 4) {
+          double x[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int b0 = 0; b0 < nb; b0 += 256) {
+            double buf[8][4];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int b = b0 + lane + 32 * t;
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii)
+                buf[t][ii] = (b < nb && i0 + ii < k) ? __ldcg(partials + b * MAXRED + i0 + ii) : 0.0;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii) x[ii] += buf[t][ii];
+          }
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            double y = x[ii];
+            for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
+            if (lane == 0 && i0 + ii < k) red[32 * MAXRED + i0 + ii] = y;
+          }
         }
       }
-      if (lane == 0) red[32 * MAXRED + MAXRED - 1] = (double)ld_acquire_s32(&ctl->error);
     }
     __syncthreads();
     return red[32 * MAXRED + MAXRED - 1] == 0.0;
@@ -397,10 +426,28 @@ __device__ __forceinline__ void spmm_row(const DevProblem& P, const T* Wm, int l
   Frag<T> acc;
   frag_zero(acc);
   const T* cv = cval<T>(P);
-  for (int q = P.C_rp[j]; q < P.C_rp[j + 1]; ++q) {
-    Frag<T> Wk;
-    frag_load(Wk, Wm, P.C_col[q], ld, t);
-    frag_axpy(acc, -cv[q], Wk);
+  {
+    // four rows in flight: the column indices, then the rows, then the sums
+    int q = P.C_rp[j];
+    const int qe = P.C_rp[j + 1];
+    for (; q + 4 <= qe; q += 4) {
+      const int k0 = P.C_col[q], k1 = P.C_col[q + 1], k2 = P.C_col[q + 2], k3 = P.C_col[q + 3];
+      const T c0 = cv[q], c1 = cv[q + 1], c2 = cv[q + 2], c3 = cv[q + 3];
+      Frag<T> W0, W1, W2, W3;
+      frag_load(W0, Wm, k0, ld, t);
+      frag_load(W1, Wm, k1, ld, t);
+      frag_load(W2, Wm, k2, ld, t);
+      frag_load(W3, Wm, k3, ld, t);
+      frag_axpy(acc, -c0, W0);
+      frag_axpy(acc, -c1, W1);
+      frag_axpy(acc, -c2, W2);
+      frag_axpy(acc, -c3, W3);
+    }
+    for (; q < qe; ++q) {
+      Frag<T> Wk;
+      frag_load(Wk, Wm, P.C_col[q], ld, t);
+      frag_axpy(acc, -cv[q], Wk);
+    }
   }
   const T* av = aval<T>(P);
   const bool a_part = (wb != 0.0) || (lam != nullptr) || (e != nullptr);

@@ -5,7 +5,8 @@
 
 namespace lorads {
 
-constexpr int SOLVER_THREADS = 256;
+constexpr int SOLVER_THREADS = 256;       // one-CTA solver (small problems, batches)
+constexpr int GRID_THREADS_MAX = 320;     // grid solver: CTA size chosen per problem
 
 // one CTA per problem; CTAs take problems from a queue (batches), or a single problem
 template <typename T>
@@ -29,7 +30,7 @@ solve_block_kernel(const SolverArgs<T>* args, int count, int* queue) {
 
 // one problem over the whole grid (cooperative launch: all CTAs co-resident)
 template <typename T>
-__global__ void __launch_bounds__(SOLVER_THREADS)
+__global__ void __launch_bounds__(GRID_THREADS_MAX)
 solve_grid_kernel(const SolverArgs<T>* args, GridCtl* ctl, double* partials, long long spin) {
   __shared__ double red[33 * MAXRED];
   __shared__ SolverArgs<T> sa;
@@ -79,8 +80,8 @@ struct Launch {
                                  int threads, cudaStream_t s);
   static cudaError_t block_capacity(int threads, int* blocks_per_sm);
   static cudaError_t solve_grid(const SolverArgs<T>* args, GridCtl* ctl, double* partials,
-                                long long spin, int grid, cudaStream_t s);
-  static cudaError_t grid_capacity(int* blocks_per_sm);
+                                long long spin, int grid, int threads, cudaStream_t s);
+  static cudaError_t grid_capacity(int threads, int* blocks_per_sm);
   static cudaError_t op_sddmm(const DevProblem& P, int ld, const T* U, const T* V, double* q,
                               int grid, cudaStream_t s);
   static cudaError_t op_spmm(const DevProblem& P, int ld, const double* w, double gamma,
@@ -94,8 +95,8 @@ struct Launch {
                                                  cudaStream_t);                                 \
   template <> cudaError_t Launch<T>::block_capacity(int, int*);                                 \
   template <> cudaError_t Launch<T>::solve_grid(const SolverArgs<T>*, GridCtl*, double*,        \
-                                                long long, int, cudaStream_t);                  \
-  template <> cudaError_t Launch<T>::grid_capacity(int*);                                       \
+                                                long long, int, int, cudaStream_t);             \
+  template <> cudaError_t Launch<T>::grid_capacity(int, int*);                                  \
   template <> cudaError_t Launch<T>::op_sddmm(const DevProblem&, int, const T*, const T*,      \
                                               double*, int, cudaStream_t);                      \
   template <> cudaError_t Launch<T>::op_spmm(const DevProblem&, int, const double*, double,    \
@@ -119,15 +120,15 @@ LORADS_DECLARE_LAUNCH(float)
   }                                                                                            \
   template <>                                                                                  \
   cudaError_t Launch<T>::solve_grid(const SolverArgs<T>* args, GridCtl* ctl, double* partials, \
-                                    long long spin, int grid, cudaStream_t s) {                \
+                                    long long spin, int grid, int threads, cudaStream_t s) {   \
     void* kargs[] = {(void*)&args, (void*)&ctl, (void*)&partials, (void*)&spin};               \
     return cudaLaunchCooperativeKernel((const void*)solve_grid_kernel<T>, dim3(grid),          \
-                                       dim3(SOLVER_THREADS), kargs, 0, s);                     \
+                                       dim3(threads), kargs, 0, s);                            \
   }                                                                                            \
   template <>                                                                                  \
-  cudaError_t Launch<T>::grid_capacity(int* blocks_per_sm) {                                   \
+  cudaError_t Launch<T>::grid_capacity(int threads, int* blocks_per_sm) {                      \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_grid_kernel<T>,  \
-                                                         SOLVER_THREADS, 0);                   \
+                                                         threads, 0);                          \
   }                                                                                            \
   template <>                                                                                  \
   cudaError_t Launch<T>::op_sddmm(const DevProblem& P, int ld, const T* U, const T* V,         \

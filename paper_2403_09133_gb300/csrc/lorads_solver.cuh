@@ -59,6 +59,7 @@ struct SolverArgs {
   T* R;
   T* Pd;
   T* HP;
+  T* Sv;          // s = H p of the single-reduction CG (row-local form)
   double* lam;    // m
   double* e;      // m
   double* grad;   // n * ld_cap (Phase I)
@@ -705,6 +706,161 @@ struct Solver {
     return sc.sync();
   }
 
+  // ----------------------------------------------------------------------------------
+  // Row-local form (every constraint a diagonal entry, e.g. MaxCut): eq. linU's matrix is
+  // block diagonal, (H x)_j = rho a_j^2 (x_j . W_j) W_j + gamma x_j.  CG runs as the
+  // Chronopoulos-Gear recurrence (one grid reduction of r.r and r.Hr per iteration; the
+  // same iterates as textbook CG in exact arithmetic), each iteration one pass whose loads
+  // are independent.  The V-step's final pass also performs the dual step.
+  // ----------------------------------------------------------------------------------
+  __device__ __forceinline__ void local_h(const Frag<T>& x, const Frag<T>& Wj, T a, T rho,
+                                          T gamma, Frag<T>& out) const {
+    const T q = rho * a * a * frag_dot(x, Wj, tm);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+      for (int e = 0; e < CHUNK; ++e) out.v[k][e] = fma(q, Wj.v[k][e], gamma * x.v[k][e]);
+  }
+
+  __device__ bool cg_solve_local(const double* Wm, const T* Wt, double* Xm, T* Xt, double rho,
+                                 double gamma, bool fuse_dual, double* v) {
+    const T rho_t = (T)rho, gamma_t = (T)gamma;
+    const T* ra = rowa<T>(P);
+    // warm-start residual R_0 = G - H W (FP64), w_0 = H r_0
+    double g3[3] = {0.0, 0.0, 0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Wj, mC;
+      frag_load(Wj, Wm, j, ld, tm);
+      spmm_row<double>(P, Wm, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mC);
+      Frag<double> accR = mC, accG = mC;
+      const int i = P.row_con[j];
+      if (i >= 0) {
+        const double a = P.row_a[j];
+        const double qi = a * frag_dot(Wj, Wj, tm);
+        const double w = rho * P.b[i] - A.lam[i];
+        frag_axpy(accG, a * w, Wj);
+        frag_axpy(accR, a * (w - rho * qi), Wj);
+      }
+      frag_axpy(accG, gamma, Wj);
+      Frag<T> r, Wjt, w;
+      frag_convert(r, accR);
+      frag_convert(Wjt, Wj);
+      local_h(r, Wjt, ra[j], rho_t, gamma_t, w);
+      frag_store(r, A.R, j, ld, tm);
+      frag_store(w, A.HP, j, ld, tm);
+      const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(w, r, tm);
+      const double d3 = frag_dot(accG, accG, tm);
+      if (tm.lane == 0) {
+        g3[0] += d1;
+        g3[1] += d2;
+        g3[2] += d3;
+      }
+    }
+    if (!sc.reduce(g3, 3)) return false;
+    ++hess;
+    double gam = g3[0], del = g3[1];
+    const double target = fmax(prm.cg_rel_tol * sqrt(gam), prm.cg_abs_floor * sqrt(g3[2]));
+    double alpha = del > 0.0 ? gam / del : 0.0, beta = 0.0;
+    int it = 0;
+    while (sqrt(gam) > target && it < prm.cg_max_iter && del > 0.0) {
+      const T a_t = (T)alpha, b_t = (T)beta;
+      double z[2] = {0.0, 0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<T> r, w, pp, ss, x, Wjt;
+        frag_load(r, A.R, j, ld, tm);
+        frag_load(w, A.HP, j, ld, tm);
+        frag_load(Wjt, Wt, j, ld, tm);
+        if (it > 0) {
+          frag_load(pp, A.Pd, j, ld, tm);
+          frag_load(ss, A.Sv, j, ld, tm);
+          frag_load(x, A.Dl, j, ld, tm);
+        } else {
+          frag_zero(pp);
+          frag_zero(ss);
+          frag_zero(x);
+        }
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+          for (int e = 0; e < CHUNK; ++e) {
+            pp.v[k][e] = fma(b_t, pp.v[k][e], r.v[k][e]);
+            ss.v[k][e] = fma(b_t, ss.v[k][e], w.v[k][e]);
+            x.v[k][e] = fma(a_t, pp.v[k][e], x.v[k][e]);
+            r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
+          }
+        local_h(r, Wjt, ra[j], rho_t, gamma_t, w);
+        frag_store(pp, A.Pd, j, ld, tm);
+        frag_store(ss, A.Sv, j, ld, tm);
+        frag_store(x, A.Dl, j, ld, tm);
+        frag_store(r, A.R, j, ld, tm);
+        frag_store(w, A.HP, j, ld, tm);
+        const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(w, r, tm);
+        if (tm.lane == 0) {
+          z[0] += d1;
+          z[1] += d2;
+        }
+      }
+      if (!sc.reduce(z, 2)) return false;
+      ++hess;
+      ++it;
+      const double gam_new = z[0], del_new = z[1];
+      if (!(gam_new == gam_new) || !(del_new == del_new)) {
+        status = ST_NAN;
+        break;
+      }
+      if (sqrt(gam_new) <= target) break;
+      beta = gam_new / gam;
+      const double denom = del_new - beta * gam_new / alpha;
+      gam = gam_new;
+      del = denom;                 // loop ends if rounding made it non-positive
+      alpha = denom > 0.0 ? gam_new / denom : 0.0;
+    }
+    cg_iters += it;
+    // X = W + x; in the V-step also the dual step lambda += rho (A(U V^T) - b)
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Wj, Xj;
+      frag_load(Wj, Wm, j, ld, tm);
+      if (it > 0) {
+        Frag<T> x;
+        frag_load(x, A.Dl, j, ld, tm);
+        frag_convert(Xj, x);
+        frag_axpy(Xj, 1.0, Wj);
+      } else {
+        Xj = Wj;
+      }
+      if (fuse_dual) {
+        Frag<double> Xo;
+        frag_load(Xo, Xm, j, ld, tm);
+        const double o2 = frag_dot(Xo, Xo, tm);
+        frag_axpy(Xo, -1.0, Xj);
+        const double d2 = frag_dot(Xo, Xo, tm);
+        const int i = P.row_con[j];
+        double e = 0.0, eh = 0.0;
+        if (i >= 0) {
+          const double a = P.row_a[j];
+          Frag<double> H = Wj;
+          frag_axpy(H, 1.0, Xj);
+          e = a * frag_dot(Wj, Xj, tm) - P.b[i];
+          eh = 0.25 * a * frag_dot(H, H, tm) - P.b[i];
+        }
+        if (tm.lane == 0) {
+          if (i >= 0) A.lam[i] += rho * e;
+          v[0] += e * e;
+          v[1] += eh * eh;
+          v[2] += d2;
+          v[3] += o2;
+        }
+      }
+      frag_store(Xj, Xm, j, ld, tm);
+      if ((const void*)Xt != (const void*)Xm) {
+        Frag<T> Xs;
+        frag_convert(Xs, Xj);
+        frag_store(Xs, Xt, j, ld, tm);
+      }
+    }
+    return fuse_dual ? true : sc.sync();
+  }
+
   // dual step lambda += rho (A(U V^T) - b); partial sums of ||e||^2 and of the output
   // infeasibility ||A(U_hat U_hat^T) - b||^2, U_hat = (U + V)/2
   __device__ void dual_step(double rho, double* v) {
@@ -738,18 +894,27 @@ struct Solver {
 
   __device__ bool phase2(double rho, double& rho_out) {
     const double gamma = prm.gamma;
+    const bool local = P.a_diag_only != 0;
     for (int k = 0; k < prm.max_admm_iter; ++k) {
-      double dv[2];
-      // U-step: eq. linU with W = V^k, CG warm-started from V^k
-      if (!cg_solve(A.V, A.Vt, A.U, A.Ut, rho, gamma, false, dv)) return false;
-      if (status != ST_OK) break;
-      // V-step: eq. linV with W = U^{k+1}, CG warm-started from U^{k+1}
-      if (!cg_solve(A.U, A.Ut, A.V, A.Vt, rho, gamma, true, dv)) return false;
-      if (status != ST_OK) break;
       double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      dual_step(rho, v);
-      v[2] = dv[0];
-      v[3] = dv[1];
+      if (local) {
+        // U-step (eq. linU, W = V^k) and V-step (eq. linV, W = U^{k+1}) with the dual step
+        if (!cg_solve_local(A.V, A.Vt, A.U, A.Ut, rho, gamma, false, v)) return false;
+        if (status != ST_OK) break;
+        if (!cg_solve_local(A.U, A.Ut, A.V, A.Vt, rho, gamma, true, v)) return false;
+        if (status != ST_OK) break;
+      } else {
+        double dv[2];
+        // U-step: eq. linU with W = V^k, CG warm-started from V^k
+        if (!cg_solve(A.V, A.Vt, A.U, A.Ut, rho, gamma, false, dv)) return false;
+        if (status != ST_OK) break;
+        // V-step: eq. linV with W = U^{k+1}, CG warm-started from U^{k+1}
+        if (!cg_solve(A.U, A.Ut, A.V, A.Vt, rho, gamma, true, dv)) return false;
+        if (status != ST_OK) break;
+        dual_step(rho, v);
+        v[2] = dv[0];
+        v[3] = dv[1];
+      }
       if (sc.is_leader()) v[4] = (double)(globaltimer_ns() - t_start);
       if (!sc.reduce(v, 5)) return false;
       admm_iters = k + 1;

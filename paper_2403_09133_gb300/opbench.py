@@ -72,8 +72,10 @@ def main():
         last = out[-1]
         print(json.dumps({"op": "solve", "family": a.family, "n": n, "m": m, "prec": a.prec,
                           "admm_iters": last["admm_iters"], "cg_iters": last["cg_iters"],
-                          "status": last["status"],
-                          "ms_phase2": last["time_phase2_s"] * 1e3}), flush=True)
+                          "status": last["status"], "ms_phase1": last["time_phase1_s"] * 1e3,
+                          "ms_phase2": last["time_phase2_s"] * 1e3,
+                          "us_per_admm_iter": last["time_phase2_s"] * 1e6 / max(1, last["admm_iters"])}),
+              flush=True)
         return
     r = a.rank or int(np.ceil(np.log2(max(m, 2))))
     ld = (r + 3) // 4 * 4
