@@ -487,4 +487,147 @@ __device__ __forceinline__ double sddmm_con(const DevProblem& P, const T* Um, co
   return a * (double)team_sum(loc, t);
 }
 
+// ------------------------------------------------------------------------------------
+// warp-split rows: one warp per row, S = 32/G sub-teams of G lanes; sub-team s takes the
+// row's entries s, s+S, s+2S, ... two at a time (four rows in flight per sub-team), and the
+// partial sums are combined over sub-teams with shuffles.  Used where rows carry many
+// entries (matrix completion: ~785 per row at n = 40,000), which a single team would walk
+// as a chain of dependent loads.
+// ------------------------------------------------------------------------------------
+struct WarpRow {
+  Team st;     // the lane's sub-team
+  int sub;     // sub-team index inside the warp
+  int S;       // sub-teams per warp
+  int warp;    // warp index inside the scope
+  int nwarps;  // warps in the scope
+};
+
+__device__ inline WarpRow make_warp_row(int ld, int tid, int nthreads, int mult = 1) {
+  WarpRow w;
+  w.st = make_team(ld, threadIdx.x & 31, 32, mult);   // team ids 0..S-1 inside the warp
+  w.sub = w.st.id;
+  w.S = 32 / w.st.G;
+  w.warp = tid >> 5;
+  w.nwarps = nthreads >> 5;
+  return w;
+}
+
+template <typename T>
+__device__ __forceinline__ void frag_warp_combine(Frag<T>& f, int G) {
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+    for (int e = 0; e < CHUNK; ++e) {
+      T x = f.v[k][e];
+      for (int off = G; off < 32; off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      f.v[k][e] = x;
+    }
+}
+
+// contribution of one A entry (j,k,a) to (H P)_j: a q W_k, q = a (P_j.W_k + P_k.W_j)
+template <typename T>
+__device__ __forceinline__ void hess_entry(const T* Wm, const T* Pm, int ld, int j, int k, T a,
+                                           const Frag<T>& Pj, const Frag<T>& Wj, const Team& t,
+                                           Frag<T>& acc) {
+  if (k == j) {
+    const T q = a * frag_dot(Pj, Wj, t);
+    frag_axpy(acc, a * q, Wj);
+  } else {
+    Frag<T> Wk, Pk;
+    frag_load(Wk, Wm, k, ld, t);
+    frag_load(Pk, Pm, k, ld, t);
+    const T q = a * team_sum(frag_dot_local(Pj, Wk) + frag_dot_local(Pk, Wj), t);
+    frag_axpy(acc, a * q, Wk);
+  }
+}
+
+// (H P)_j = rho sum a q W_k + gamma P_j with the whole warp; out valid in every lane
+template <typename T>
+__device__ void hessian_row_warp(const DevProblem& P, const T* Wm, const T* Pm, int ld, int j,
+                                 const Frag<T>& Pj, T rho, T gamma, const WarpRow& w,
+                                 Frag<T>& out) {
+  const Team& t = w.st;
+  Frag<T> Wj, acc;
+  frag_load(Wj, Wm, j, ld, t);
+  frag_zero(acc);
+  const T* av = aval<T>(P);
+  const int e0 = P.A_rp[j], e1 = P.A_rp[j + 1];
+  int e = e0 + w.sub;
+  for (; e + w.S < e1; e += 2 * w.S) {
+    const int k0 = P.A_col[e], k1 = P.A_col[e + w.S];
+    const T a0 = av[e], a1 = av[e + w.S];
+    if (k0 != j && k1 != j) {
+      Frag<T> W0, P0, W1, P1;
+      frag_load(W0, Wm, k0, ld, t);
+      frag_load(P0, Pm, k0, ld, t);
+      frag_load(W1, Wm, k1, ld, t);
+      frag_load(P1, Pm, k1, ld, t);
+      const T q0 = a0 * team_sum(frag_dot_local(Pj, W0) + frag_dot_local(P0, Wj), t);
+      const T q1 = a1 * team_sum(frag_dot_local(Pj, W1) + frag_dot_local(P1, Wj), t);
+      frag_axpy(acc, a0 * q0, W0);
+      frag_axpy(acc, a1 * q1, W1);
+    } else {
+      hess_entry(Wm, Pm, ld, j, k0, a0, Pj, Wj, t, acc);
+      hess_entry(Wm, Pm, ld, j, k1, a1, Pj, Wj, t, acc);
+    }
+  }
+  if (e < e1) hess_entry(Wm, Pm, ld, j, P.A_col[e], av[e], Pj, Wj, t, acc);
+  frag_warp_combine(acc, t.G);
+#pragma unroll
+  for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+    for (int ee = 0; ee < CHUNK; ++ee) out.v[kk][ee] = fma(rho, acc.v[kk][ee], gamma * Pj.v[kk][ee]);
+}
+
+// (A^T(w) - C) W on row j with the whole warp (same weights as spmm_row); out in every lane
+template <typename T>
+__device__ void spmm_row_warp(const DevProblem& P, const T* Wm, int ld, int j, const double* lam,
+                              const double* e, double wb, double wl, double we, T gamma,
+                              const WarpRow& w, Frag<T>& out) {
+  const Team& t = w.st;
+  Frag<T> acc;
+  frag_zero(acc);
+  const T* cv = cval<T>(P);
+  for (int q = P.C_rp[j] + w.sub; q < P.C_rp[j + 1]; q += w.S) {
+    Frag<T> Wk;
+    frag_load(Wk, Wm, P.C_col[q], ld, t);
+    frag_axpy(acc, -cv[q], Wk);
+  }
+  const T* av = aval<T>(P);
+  const bool a_part = (wb != 0.0) || (lam != nullptr) || (e != nullptr);
+  if (a_part) {
+    const int q1 = P.A_rp[j + 1];
+    int q = P.A_rp[j] + w.sub;
+    for (; q + w.S < q1; q += 2 * w.S) {
+      const int i0 = P.A_con[q], i1 = P.A_con[q + w.S];
+      const int k0 = P.A_col[q], k1 = P.A_col[q + w.S];
+      double c0 = wb * P.b[i0], c1 = wb * P.b[i1];
+      if (lam) { c0 += wl * lam[i0]; c1 += wl * lam[i1]; }
+      if (e) { c0 += we * e[i0]; c1 += we * e[i1]; }
+      Frag<T> W0, W1;
+      frag_load(W0, Wm, k0, ld, t);
+      frag_load(W1, Wm, k1, ld, t);
+      frag_axpy(acc, (T)(c0 * (double)av[q]), W0);
+      frag_axpy(acc, (T)(c1 * (double)av[q + w.S]), W1);
+    }
+    if (q < q1) {
+      const int i = P.A_con[q];
+      double c = wb * P.b[i];
+      if (lam) c += wl * lam[i];
+      if (e) c += we * e[i];
+      Frag<T> Wk;
+      frag_load(Wk, Wm, P.A_col[q], ld, t);
+      frag_axpy(acc, (T)(c * (double)av[q]), Wk);
+    }
+  }
+  frag_warp_combine(acc, t.G);
+  if (gamma != T(0)) {
+    Frag<T> Wj;
+    frag_load(Wj, Wm, j, ld, t);
+    frag_axpy(acc, gamma, Wj);
+  }
+  out = acc;
+}
+
 }  // namespace lorads

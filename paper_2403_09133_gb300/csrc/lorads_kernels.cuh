@@ -53,23 +53,44 @@ __global__ void op_sddmm_kernel(DevProblem P, int ld, const T* U, const T* V, do
 template <typename T>
 __global__ void op_spmm_kernel(DevProblem P, int ld, const double* w, double gamma, const T* V,
                                T* out) {
-  const Team t = make_team(ld, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-  for (int j = t.id; j < P.n; j += t.count) {
-    Frag<T> o;
-    spmm_row<T>(P, V, ld, j, w, nullptr, 0.0, 1.0, 0.0, (T)gamma, t, o);
-    frag_store(o, out, j, ld, t);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  if (P.a_diag_only) {
+    const Team t = make_team(ld, tid, nt);
+    for (int j = t.id; j < P.n; j += t.count) {
+      Frag<T> o;
+      spmm_row<T>(P, V, ld, j, w, nullptr, 0.0, 1.0, 0.0, (T)gamma, t, o);
+      frag_store(o, out, j, ld, t);
+    }
+  } else {
+    const WarpRow wr = make_warp_row(ld, tid, nt);
+    for (int j = wr.warp; j < P.n; j += wr.nwarps) {
+      Frag<T> o;
+      spmm_row_warp<T>(P, V, ld, j, w, nullptr, 0.0, 1.0, 0.0, (T)gamma, wr, o);
+      if (wr.sub == 0) frag_store(o, out, j, ld, wr.st);
+    }
   }
 }
 
 template <typename T>
 __global__ void op_hessian_kernel(DevProblem P, int ld, T rho, T gamma, const T* V, const T* Pm,
                                   T* out) {
-  const Team t = make_team(ld, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-  for (int j = t.id; j < P.n; j += t.count) {
-    Frag<T> Pj, H;
-    frag_load(Pj, Pm, j, ld, t);
-    hessian_row<T>(P, V, Pm, ld, j, Pj, rho, gamma, t, H);
-    frag_store(H, out, j, ld, t);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  if (P.a_diag_only) {
+    const Team t = make_team(ld, tid, nt);
+    for (int j = t.id; j < P.n; j += t.count) {
+      Frag<T> Pj, H;
+      frag_load(Pj, Pm, j, ld, t);
+      hessian_row<T>(P, V, Pm, ld, j, Pj, rho, gamma, t, H);
+      frag_store(H, out, j, ld, t);
+    }
+  } else {
+    const WarpRow wr = make_warp_row(ld, tid, nt);
+    for (int j = wr.warp; j < P.n; j += wr.nwarps) {
+      Frag<T> Pj, H;
+      frag_load(Pj, Pm, j, ld, wr.st);
+      hessian_row_warp<T>(P, V, Pm, ld, j, Pj, rho, gamma, wr, H);
+      if (wr.sub == 0) frag_store(H, out, j, ld, wr.st);
+    }
   }
 }
 

@@ -560,41 +560,53 @@ struct Solver {
   __device__ bool cg_solve(const double* Wm, const T* Wt, double* Xm, T* Xt, double rho,
                            double gamma, bool want_dv, double* dv) {
     double v[2] = {0.0, 0.0};
-    for (int j = tm.id; j < n; j += tm.count) {
-      Frag<double> Wj, accR, mC;
-      frag_load(Wj, Wm, j, ld, tm);
-      spmm_row<double>(P, Wm, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mC);
-      accR = mC;
-      Frag<double> accG = mC;
-      for (int q = P.A_rp[j]; q < P.A_rp[j + 1]; ++q) {
+    // one warp per row (entries split across sub-teams): rows with many entries
+    const WarpRow wr = make_warp_row(ld, sc.tid(), sc.nthreads(), prm.team_mult);
+    const Team& st = wr.st;
+    for (int j = wr.warp; j < n; j += wr.nwarps) {
+      Frag<double> Wj, accR, accG;
+      frag_load(Wj, Wm, j, ld, st);
+      frag_zero(accR);
+      frag_zero(accG);
+      for (int q = P.A_rp[j] + wr.sub; q < P.A_rp[j + 1]; q += wr.S) {
         const int k = P.A_col[q], i = P.A_con[q];
         const double a = P.A_val[q];
         double qi;
         Frag<double> Wk;
         if (k == j) {
           Wk = Wj;
-          qi = a * frag_dot(Wj, Wj, tm);
+          qi = a * frag_dot(Wj, Wj, st);
         } else {
-          frag_load(Wk, Wm, k, ld, tm);
-          qi = 2.0 * a * frag_dot(Wj, Wk, tm);
+          frag_load(Wk, Wm, k, ld, st);
+          qi = 2.0 * a * frag_dot(Wj, Wk, st);
         }
         const double w = rho * P.b[i] - A.lam[i];
         frag_axpy(accG, a * w, Wk);
         frag_axpy(accR, a * (w - rho * qi), Wk);
       }
+      for (int q = P.C_rp[j] + wr.sub; q < P.C_rp[j + 1]; q += wr.S) {
+        Frag<double> Wk;
+        frag_load(Wk, Wm, P.C_col[q], ld, st);
+        frag_axpy(accR, -P.C_val[q], Wk);
+        frag_axpy(accG, -P.C_val[q], Wk);
+      }
+      frag_warp_combine(accR, st.G);
+      frag_warp_combine(accG, st.G);
       frag_axpy(accG, gamma, Wj);
-      Frag<T> Rt, Zt;
-      frag_convert(Rt, accR);
-      frag_zero(Zt);
-      frag_store(Rt, A.R, j, ld, tm);
-      frag_store(Rt, A.Pd, j, ld, tm);
-      frag_store(Zt, A.Dl, j, ld, tm);
-      Frag<double> Rd;
-      frag_convert(Rd, Rt);
-      const double a1 = frag_dot(Rd, Rd, tm), a2 = frag_dot(accG, accG, tm);
-      if (tm.lane == 0) {
-        v[0] += a1;
-        v[1] += a2;
+      if (wr.sub == 0) {
+        Frag<T> Rt, Zt;
+        frag_convert(Rt, accR);
+        frag_zero(Zt);
+        frag_store(Rt, A.R, j, ld, st);
+        frag_store(Rt, A.Pd, j, ld, st);
+        frag_store(Zt, A.Dl, j, ld, st);
+        Frag<double> Rd;
+        frag_convert(Rd, Rt);
+        const double a1 = frag_dot(Rd, Rd, st), a2 = frag_dot(accG, accG, st);
+        if (st.lane == 0) {
+          v[0] += a1;
+          v[1] += a2;
+        }
       }
     }
     if (!sc.reduce(v, 2)) return false;
@@ -602,30 +614,19 @@ struct Solver {
     double rr = v[0];
     const double target = fmax(prm.cg_rel_tol * sqrt(rr), prm.cg_abs_floor * sqrt(v[1]));
     const T rho_t = (T)rho, gamma_t = (T)gamma;
-    // row-local Hessian (diagonal constraints): the direction update P = R + beta P of the
-    // previous iteration is done inside the next apply, saving one grid-wide sync
-    const bool fuse = P.a_diag_only != 0;
-    T beta_pending = T(0);
     int it = 0;
     while (sqrt(rr) > target && it < prm.cg_max_iter) {
       // HP = H P, p.Hp
       double w[1] = {0.0};
-      for (int j = tm.id; j < n; j += tm.count) {
+      for (int j = wr.warp; j < n; j += wr.nwarps) {
         Frag<T> Pj, Hj;
-        frag_load(Pj, A.Pd, j, ld, tm);
-        if (fuse && it > 0) {
-          Frag<T> Rj;
-          frag_load(Rj, A.R, j, ld, tm);
-#pragma unroll
-          for (int k = 0; k < KMAX; ++k)
-#pragma unroll
-            for (int e = 0; e < CHUNK; ++e) Pj.v[k][e] = fma(beta_pending, Pj.v[k][e], Rj.v[k][e]);
-          frag_store(Pj, A.Pd, j, ld, tm);
+        frag_load(Pj, A.Pd, j, ld, st);
+        hessian_row_warp<T>(P, Wt, A.Pd, ld, j, Pj, rho_t, gamma_t, wr, Hj);
+        if (wr.sub == 0) {
+          frag_store(Hj, A.HP, j, ld, st);
+          const double d = (double)team_sum(frag_dot_local(Pj, Hj), st);
+          if (st.lane == 0) w[0] += d;
         }
-        hessian_row<T>(P, Wt, A.Pd, ld, j, Pj, rho_t, gamma_t, tm, Hj);
-        frag_store(Hj, A.HP, j, ld, tm);
-        const double d = (double)team_sum(frag_dot_local(Pj, Hj), tm);
-        if (tm.lane == 0) w[0] += d;
       }
       if (!sc.reduce(w, 1)) return false;
       ++hess;
@@ -658,10 +659,6 @@ struct Solver {
       if (sqrt(rr_new) <= target) { rr = rr_new; break; }
       const T beta_t = (T)(rr_new / rr);
       rr = rr_new;
-      if (fuse) {
-        beta_pending = beta_t;
-        continue;
-      }
       for (int j = tm.id; j < n; j += tm.count) {
         Frag<T> Pj, Rj;
         frag_load(Pj, A.Pd, j, ld, tm);
