@@ -217,6 +217,51 @@ const char *lorads_status_string(int code);
  * binding can check its mirror of the two structs.  Either pointer may be NULL. */
 void lorads_struct_sizes(int64_t *params_bytes, int64_t *result_bytes);
 
+/* ---------------------------------------------------------------- learned warm start
+ * A 3-layer message-passing network over the cost graph proposes the Phase II start
+ * (U_0, y_0) in place of Phase I (the paper's Phase I is the Burer-Monteiro method,
+ * Section 4.1; better warm starts are its stated future work, Section 6).  Use:
+ * lorads_gnn_forward(..., U0, y0), then lorads_set_start(p, r, U0, lambda0 = -y0, rho0) and
+ * lorads_solve with phase1 = 0.  Weights are BF16 on the tensor cores (FP32 accumulation,
+ * FP32 master copy for Adam).  Widths: hidden 64, layers 3, r at most 16.
+ *   graph    edges (ei, ej) with weights w (for MaxCut the off-diagonal entries of C)
+ *   features 8 SplitMix64 normals of feature_seed, 1, log(1+deg), d/10, sum w / d
+ *            (d = 1 + sum |w|), zero padding to 64
+ *   layer    H = relu([H, A_hat H] Theta + b), A_hat_ij = w_ij / sqrt(d_i d_j)
+ *   heads    U_0 = rows of H Theta_u (first r columns) normalised to unit length,
+ *            y_0 = H theta_y + b_y
+ *   loss     mean over edges (U_i.U_j - Xs_e)^2 + 0.1 mean over nodes (y_i - ys_i)^2
+ * Parameter vector (FP32, lorads_gnn_param_count() entries): for l = 0..2 Theta_l
+ * (128 x 64 row-major, input feature major) then b_l (64); Theta_u (64 x 16 row-major);
+ * theta_y (64); b_y (1). */
+typedef struct lorads_gnn lorads_gnn;
+
+int lorads_gnn_param_count(void);
+
+/* New network on the current device; weights ~ N(0, 1/fan_in) from the SplitMix64 seed. */
+int lorads_gnn_create(uint64_t seed, lorads_gnn **out);
+
+/* Copies the FP32 parameters to / from a host vector of lorads_gnn_param_count() floats;
+ * set also resets the Adam moments. */
+int lorads_gnn_get_params(const lorads_gnn *g, float *params);
+int lorads_gnn_set_params(lorads_gnn *g, const float *params);
+
+/* Loads a graph (nedges undirected edges i != j, host arrays copied) and its features. */
+int lorads_gnn_load_graph(lorads_gnn *g, int64_t n, int64_t nedges, const int32_t *ei,
+                          const int32_t *ej, const double *w, uint64_t feature_seed);
+
+/* Forward pass; U0 (n x r row-major) and y0 (n) into host buffers (either may be NULL). */
+int lorads_gnn_forward(lorads_gnn *g, int32_t r, double *U0, double *y0, void *stream);
+
+/* One training step on the loaded graph with targets Xs (per edge, U_hat_i.U_hat_j of a
+ * solved instance) and ys (per node, the solved dual): forward, backward, and an Adam step
+ * with learning rate lr (lr = 0: gradients only).  *loss receives the loss before the step;
+ * grads (may be NULL) the FP32 gradient vector. */
+int lorads_gnn_train_step(lorads_gnn *g, int32_t r, const double *Xs, const double *ys,
+                          double lr, double *loss, float *grads, void *stream);
+
+void lorads_gnn_destroy(lorads_gnn *g);
+
 /* ---------------------------------------------------------------- operators
  * The linear maps of the method on caller-owned DEVICE arrays (row-major n x ld, ld a
  * multiple of 4, ld >= r), enqueued on stream; they return after enqueueing.  prec selects

@@ -1,6 +1,7 @@
 """Builds liblorads.so (the C ABI of include/lorads.h) in-tree with nvcc for sm_103a.
 
-Three translation units compile in parallel (FP64 kernels, FP32 kernels, host runtime) and
+Four translation units compile in parallel (FP64 kernels, FP32 kernels, host runtime, the
+learned warm start) and
 link into one shared library next to this file.  Usage: python -m paper_2403_09133_gb300.build
 """
 from __future__ import annotations
@@ -14,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblorads.so")
-SOURCES = ["lorads_f64.cu", "lorads_f32.cu", "lorads_capi.cu"]
+SOURCES = ["lorads_f64.cu", "lorads_f32.cu", "lorads_capi.cu", "lorads_gnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

@@ -512,9 +512,9 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   if (st != LORADS_OK) return st;
   int dev_sms = 0;
   CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
-  // scope: one CTA for small problems, the whole GPU for large ones
+  // scope: one CTA for small problems, the whole GPU from a few hundred rows up
   int grid = prm->grid;
-  if (grid <= 0) grid = (p->n < 4096) ? 1 : dev_sms;
+  if (grid <= 0) grid = (p->n < 512) ? 1 : dev_sms;
   const int threads = (grid == 1 && prm->threads > 0) ? prm->threads : SOLVER_THREADS;
   if (threads % 32 != 0 || threads > SOLVER_THREADS) return LORADS_ERR_ARG;
   cudaError_t le;
@@ -1117,7 +1117,7 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   CU(cudaMemsetAsync(dpartials, 0xFF, sizeof(double) * (size_t)dev_sms * 8 * MAXRED * 3, s));
   CU(cudaMemsetAsync(dqueue, 0, 16, s));
   int grid = prm->grid;
-  if (grid <= 0) grid = (n < 4096) ? 1 : dev_sms;
+  if (grid <= 0) grid = (n < 512) ? 1 : dev_sms;
   cudaError_t le;
   if (grid == 1) {
     le = Launch<T>::solve_block(dargs, 1, dqueue, 1, SOLVER_THREADS, s);

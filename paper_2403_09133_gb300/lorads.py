@@ -97,6 +97,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lorads_solve_static": (_i32, [P, ctypes.POINTER(lorads_params), P, P, _i64, P,
                                        ctypes.POINTER(lorads_result)]),
         "lorads_op_sddmm": (_i32, [P, _i32, _i32, _i32, P, P, P, P]),
+        "lorads_gnn_param_count": (_i32, []),
+        "lorads_gnn_create": (_i32, [_u64, ctypes.POINTER(P)]),
+        "lorads_gnn_get_params": (_i32, [P, P]),
+        "lorads_gnn_set_params": (_i32, [P, P]),
+        "lorads_gnn_load_graph": (_i32, [P, _i64, _i64, P, P, P, _u64]),
+        "lorads_gnn_forward": (_i32, [P, _i32, P, P, P]),
+        "lorads_gnn_train_step": (_i32, [P, _i32, P, P, _f64, ctypes.POINTER(_f64), P, P]),
+        "lorads_gnn_destroy": (None, [P]),
         "lorads_op_spmm": (_i32, [P, _i32, _i32, _i32, P, _f64, P, P, P]),
         "lorads_op_hessian": (_i32, [P, _i32, _i32, _i32, _f64, _f64, P, P, P, P]),
     }
@@ -297,3 +305,56 @@ def lorads_solve_batch(handles, prm: lorads_params, stream=None):
                                              ctypes.byref(th), ctypes.byref(mu))
     _check(code, "lorads_solve_batch")
     return [r.as_dict() for r in res], th.value, mu.value
+
+
+# ---- learned warm start ------------------------------------------------------------------
+def lorads_gnn_param_count() -> int:
+    return load_library().lorads_gnn_param_count()
+
+
+def lorads_gnn_create(seed: int = 1) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().lorads_gnn_create(seed, ctypes.byref(h)), "lorads_gnn_create")
+    return h
+
+
+def lorads_gnn_get_params(g) -> np.ndarray:
+    out = np.empty(lorads_gnn_param_count(), dtype=np.float32)
+    _check(load_library().lorads_gnn_get_params(g, out.ctypes.data_as(ctypes.c_void_p)),
+           "lorads_gnn_get_params")
+    return out
+
+
+def lorads_gnn_set_params(g, params) -> int:
+    a, ap = _host(params, np.float32)
+    if a.size != lorads_gnn_param_count():
+        raise ValueError("parameter vector has the wrong length")
+    return load_library().lorads_gnn_set_params(g, ap)
+
+
+def lorads_gnn_load_graph(g, n: int, ei, ej, w, feature_seed: int) -> int:
+    i, ip = _host(ei, np.int32); j, jp = _host(ej, np.int32); v, vp = _host(w, np.float64)
+    return load_library().lorads_gnn_load_graph(g, n, len(i), ip, jp, vp, feature_seed)
+
+
+def lorads_gnn_forward(g, n: int, r: int, stream=None):
+    U = np.empty((n, r)); y = np.empty(n)
+    _check(load_library().lorads_gnn_forward(g, r, U.ctypes.data_as(ctypes.c_void_p),
+                                             y.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)),
+           "lorads_gnn_forward")
+    return U, y
+
+
+def lorads_gnn_train_step(g, r: int, Xs, ys, lr: float, want_grads: bool = False, stream=None):
+    x, xp = _host(Xs, np.float64); t, tp = _host(ys, np.float64)
+    loss = _f64()
+    grads = np.empty(lorads_gnn_param_count(), dtype=np.float32) if want_grads else None
+    _check(load_library().lorads_gnn_train_step(
+        g, r, xp, tp, lr, ctypes.byref(loss),
+        grads.ctypes.data_as(ctypes.c_void_p) if want_grads else None, _stream_ptr(stream)),
+        "lorads_gnn_train_step")
+    return loss.value, grads
+
+
+def lorads_gnn_destroy(g) -> None:
+    load_library().lorads_gnn_destroy(g)
