@@ -31,6 +31,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-KKT<=1e-6 & CG-operator HBM GB/s: chosen form vs plain FP64, 1 GB300"
+# DRAM read+write bytes of one mixed-form solver launch on this workload, from one ncu capture
+# (profiles/solver_traffic_torus141.md); reported only while the solver sources are unchanged.
+SOLVER_SOURCES = ["lorads_solver.cuh", "lorads_device.cuh", "lorads_kernels.cuh", "lorads_f32.cu",
+                  "lorads_capi.cu"]
+SOLVER_TRAFFIC = {"sources_sha256_16": "ca48d9cab1606881", "bytes_per_launch": 67.25e6}
+
+
+def solver_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in SOLVER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2403_09133_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] == SOLVER_TRAFFIC["sources_sha256_16"]:
+        return SOLVER_TRAFFIC["bytes_per_launch"]
+    return None
 WORKLOAD = "maxcut_torus_141x141_pm1"
 
 
@@ -44,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-mc", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     return ap.parse_args()
 
@@ -273,7 +291,7 @@ def run_gpu(args):
         "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                     "frac": ach / peak, "traffic": None,
+                     "frac": ach / peak, "traffic": solver_traffic(),
                      "kernel": "lorads::solve_grid_kernel<float>",
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
         "gpu_launches": args.steps,
@@ -281,6 +299,10 @@ def run_gpu(args):
     }
     if not args.no_batch:
         line["batch"] = batch_bench(args, stream)
+    if not args.no_mc:
+        line["matrix_completion"] = mc_bench(args, stream)
+    if not args.no_learned:
+        line["learned_warm_start"] = learned_bench(args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(inst, args.oracle_seconds, rm["admm_iters"])
     if world > 1:
@@ -333,6 +355,78 @@ def batch_bench(args, stream):
             "plain_fp64_sequential_s_est": t_seq_scaled,
             "speedup_vs_sequential_fp64": t_seq_scaled / t_batch,
             "sample": f"{len(sample)} one-problem FP64 solves scaled x{len(probs) / len(sample):.0f}"}
+
+
+def mc_bench(args, stream):
+    """Matrix completion at n = 40,000 (n1 = n2 = 20,000), rank-5 M, 15,694,167 observed
+    entries (the size of the paper's MC_40000), r0 = 24, library defaults (switch 1e-3,
+    h = 1): one solve per form after a warm-up, plus the FP32 Hessian operator at this size."""
+    import torch
+    from paper_2403_09133_gb300 import instances as I
+    from paper_2403_09133_gb300 import lorads as L
+    inst = I.workload_mc()
+    ev = np.linalg.eigvals((inst.mc_P.T @ inst.mc_P) @ (inst.mc_Q.T @ inst.mc_Q)).real
+    nuclear2 = 2.0 * float(np.sqrt(np.clip(ev, 0, None)).sum())
+    prob = L.Problem(inst)
+    out = {"n": inst.n, "m": inst.m, "two_nuclear_norm": nuclear2}
+    for form, prec in (("mixed", L.LORADS_PREC_MIXED), ("fp64", L.LORADS_PREC_FP64)):
+        prm = prob.params(precision=prec)    # switch_tol 1e-3, h 1 ("auto" for non-diagonal A)
+        L.lorads_solve(prob.handle, prm, stream)          # warm-up (assembly, first touch)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = L.lorads_solve(prob.handle, prm, stream).as_dict()
+        e1.record(stream)
+        e1.synchronize()
+        out[form] = {"seconds": e0.elapsed_time(e1) * 1e-3, "status": r["status"],
+                     "objective_rel_err_vs_2nuclear": abs(r["objective"] - nuclear2) / nuclear2,
+                     "r_P": r["r_P"], "admm_iters": r["admm_iters"], "cg_iters": r["cg_iters"],
+                     "time_phase1_s": r["time_phase1_s"], "time_phase2_s": r["time_phase2_s"]}
+    # the CG operator at this size (FP32), CUDA events, L2 flushed
+    r_, ld = 24, 24
+    g = torch.Generator(device="cuda").manual_seed(1)
+    V = torch.randn((inst.n, ld), generator=g, device="cuda")
+    P = torch.randn((inst.n, ld), generator=g, device="cuda")
+    H = torch.empty_like(V)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    times = []
+    for it in range(8):
+        flush.fill_(float(it))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.lorads_op_hessian(prob.handle, L.LORADS_PREC_MIXED, r_, ld, 50.0, 1.0, V, P, H, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= 3:
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    t = statistics.median(times)
+    nnz = 2 * inst.m
+    compulsory = 3 * inst.n * ld * 4 + 4 * (inst.n + 1) + nnz * 8
+    gathered = nnz * 2 * ld * 4
+    out["hessian_fp32"] = {"us_per_apply": t * 1e6, "compulsory_gbs": compulsory / t / 1e9,
+                           "gathered_row_gbs": gathered / t / 1e9,
+                           "note": "gathered rows (2 per symmetric entry) come from L2"}
+    prob.close()
+    return out
+
+
+def learned_bench(args):
+    """Learned warm start (small): 32 solver-labelled training graphs (n in [100, 300]),
+    15 epochs on the GPU, then 8 held-out graphs solved from the Burer-Monteiro start and from
+    the trained network, to eq. stop <= 1e-4."""
+    from paper_2403_09133_gb300 import learned as LN
+    from paper_2403_09133_gb300 import lorads as L
+    t0 = time.perf_counter()
+    samples = LN.solve_targets(LN.make_graphs(32, 300_000, 100, 300))
+    g = L.lorads_gnn_create(5)
+    hist = LN.train(g, samples, epochs=15, lr=2e-3)
+    t1 = time.perf_counter()
+    rows = LN.evaluate(g, LN.make_graphs(8, 400_000, 100, 300), tol=1e-4)
+    L.lorads_gnn_destroy(g)
+    return {"train_graphs": 32, "epochs": 15, "loss_first": hist[0], "loss_last": hist[-1],
+            "seconds_data_and_training": t1 - t0, "eval_tol": 1e-4,
+            "eval": LN.summarize(rows)}
 
 
 def run_reference(args):

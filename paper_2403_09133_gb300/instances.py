@@ -67,6 +67,17 @@ class SDPInstance:
 # --------------------------------------------------------------------------------------
 # graphs
 # --------------------------------------------------------------------------------------
+def _sorted_unique(x: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (the same set np.unique returns; sort + adjacent difference)."""
+    s = np.sort(x, kind="stable")
+    if s.size == 0:
+        return s
+    keep = np.empty(s.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(s[1:], s[:-1], out=keep[1:])
+    return s[keep]
+
+
 def erdos_renyi_edges(n: int, num_edges: int, rng: np.random.Generator) -> np.ndarray:
     """G(n, M): ``num_edges`` distinct unordered pairs drawn uniformly (i < j)."""
     total = n * (n - 1) // 2
@@ -80,7 +91,7 @@ def erdos_renyi_edges(n: int, num_edges: int, rng: np.random.Generator) -> np.nd
         keep = i != j
         lo = np.minimum(i[keep], j[keep])
         hi = np.maximum(i[keep], j[keep])
-        chosen = np.unique(np.concatenate([chosen, lo * n + hi]))
+        chosen = _sorted_unique(np.concatenate([chosen, lo * n + hi]))
     # a uniformly random M-subset of the distinct pairs found
     pick = rng.permutation(chosen.size)[:num_edges]
     codes = np.sort(chosen[pick])
@@ -182,7 +193,7 @@ def matrix_completion(n1: int, n2: int, rank: int, num_samples: int, seed: int,
     while codes.size < num_samples:
         need = num_samples - codes.size
         draw = rng.integers(0, total, size=need + need // 8 + 16, dtype=np.int64)
-        codes = np.unique(np.concatenate([codes, draw]))
+        codes = _sorted_unique(np.concatenate([codes, draw]))
     codes = np.sort(codes[rng.permutation(codes.size)[:num_samples]])
     p = codes // n2
     q = codes % n2

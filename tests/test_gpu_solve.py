@@ -129,3 +129,19 @@ def test_phase2_start_from_caller(cuda):
     assert res["status"] == 0 and ref["converged"]
     assert abs(res["admm_iters"] - ref["admm_iters"]) <= 2
     assert abs(res["objective"] - ref["objective"]) <= 1e-7 * abs(ref["objective"])
+
+
+@pytest.mark.parametrize("prec", [L.LORADS_PREC_FP64, L.LORADS_PREC_MIXED])
+def test_rank_growth_matches_oracle(cuda, prec):
+    """Section 4.3's dynamic rank: with an inner cap of 3 L-BFGS iterations every ALM
+    subproblem stalls, so the rank grows by 1.5x (rounded up) until the cap floor(sqrt(2m)):
+    n = m = 100, r0 = ceil(log2 100) = 7 -> 11 -> 14 (cap), two growths on both sides."""
+    inst = I.maxcut_er(100, 6.0, seed=3)
+    sdp = SDP.from_instance(inst)
+    ref = solve(sdp, Params(inner_max_iter=3))
+    res, sol = gpu_solve(inst, precision=prec, inner_max_iter=3)
+    assert ref["rank"] == 14 and ref["growths"] == 2
+    assert res["rank"] == ref["rank"] and res["rank_growths"] == ref["growths"]
+    assert sol["U_hat"].shape == (100, 14)
+    assert res["status"] == 0 and ref["converged"]
+    assert abs(res["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
