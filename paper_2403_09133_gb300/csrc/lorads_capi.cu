@@ -1020,37 +1020,12 @@ template <typename T>
 static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStream_t s,
                             double* U_hat, int64_t ldu, double* y, lorads_result* res) {
   const int64_t n = p->n, m = p->m;
-  DevParams dv{};
-  const int cap = resolve_rank_cap(p, prm);
-  dv.rank_cap = cap;
-  dv.r0 = resolve_r0(p, prm, cap);
-  dv.rank_factor = prm->rank_factor;
-  dv.tol = prm->tol;
-  dv.switch_tol = prm->switch_tol >= 0 ? prm->switch_tol : (p->diag_separable ? 1e-2 : 1e-3);
-  dv.h = prm->h >= 0 ? prm->h : (p->diag_separable ? 10.0 : 1.0);
-  dv.rho_max = prm->rho_max;
-  dv.rho_growth = prm->rho_growth;
-  dv.rho_every = std::max(1, prm->rho_every);
-  dv.gamma = prm->gamma_fixed > 0 ? prm->gamma_fixed
-                                  : prm->gamma_scale * (p->C_inf > 0 ? p->C_inf : 1.0);
-  dv.max_admm_iter = prm->max_admm_iter;
-  dv.cg_max_iter = prm->cg_max_iter;
-  dv.cg_rel_tol = prm->cg_rel_tol;
-  dv.cg_abs_floor = prm->cg_abs_floor;
-  dv.lbfgs_mem = std::min(std::max(prm->lbfgs_mem, 1), MAXMEM);
-  dv.inner_max_iter = prm->inner_max_iter;
-  dv.inner_tol_factor = prm->inner_tol_factor;
-  dv.inner_tol_max = prm->inner_tol_max;
-  dv.max_outer = prm->max_outer;
-  dv.sigma_factor = prm->sigma_factor;
-  dv.sigma_decrease = prm->sigma_decrease;
-  dv.new_col_std = prm->new_col_std;
-  dv.seed = prm->seed;
-  dv.phase1 = prm->phase1 ? 1 : 0;
-  dv.r_start = p->start_r;
-  dv.rho0 = p->start_rho > 0 ? p->start_rho : 100.0;
-  dv.time_limit_ns = (long long)(prm->time_limit_s * 1e9);
-  dv.team_mult = 1;
+  DevParams dv;
+  lorads_params q = *prm;
+  q.team_mult = 1;
+  const int pst = fill_params(p, &q, dv);
+  if (pst != LORADS_OK) return pst;
+  const int cap = dv.rank_cap;
   if (!dv.phase1 && (!p->has_start || p->start_r > 256)) return LORADS_ERR_STATE;
   const int rmax = std::max(cap, dv.phase1 ? 0 : p->start_r);
   const long long ld_cap = round4(rmax);

@@ -168,8 +168,21 @@ struct Solver {
   }
 
   // ----------------------------------------------------------------------------------
-  // Phase I pieces (FP64)
+  // Phase I pieces.  Masters (U, the direction, gradients, L-BFGS pairs) and every scalar
+  // are FP64; the bulk products (residual SDDMM, gradient SpMM, line-search products) read
+  // T shadows of U (A.Ut) and of the direction (A.Dl, free until Phase II), so the mixed
+  // form runs them in FP32.  For T = double the shadows alias the masters.
   // ----------------------------------------------------------------------------------
+  __device__ T* dir_shadow() const {
+    return ((const void*)A.Ut == (const void*)A.U) ? reinterpret_cast<T*>(A.dir) : A.Dl;
+  }
+  __device__ __forceinline__ void store_shadow(const Frag<double>& f, T* dst, int j) const {
+    if ((const void*)dst == (const void*)A.U || (const void*)dst == (const void*)A.dir) return;
+    Frag<T> t;
+    frag_convert(t, f);
+    frag_store(t, dst, j, ld, tm);
+  }
+
   __device__ void init_factor() {
     const uint64_t key = stream_key(prm.seed, 0);
     const double inv = 1.0 / sqrt((double)r);
@@ -191,14 +204,15 @@ struct Solver {
           for (int e = 0; e < CHUNK; ++e) f.v[k][e] *= s;
       }
       frag_store(f, A.U, j, ld, tm);
+      store_shadow(f, A.Ut, j);
     }
   }
 
-  // e = A(U U^T) - b (stored), returns ||e||^2 and <lambda, e> via red
+  // e = A(U U^T) - b (stored), returns ||e||^2
   __device__ bool eval_residual_UU(double& e2) {
     double v[1] = {0.0};
     for (int i = tmc.id; i < m; i += tmc.count) {
-      const double q = sddmm_con<double>(P, A.U, A.U, ld, i, tmc);
+      const double q = sddmm_con<T>(P, A.Ut, A.Ut, ld, i, tmc);
       const double ei = q - P.b[i];
       if (tmc.lane == 0) {
         A.e[i] = ei;
@@ -213,16 +227,38 @@ struct Solver {
   // grad = 2 (C + A^T(lambda + sigma e)) U, returns ||grad||_F^2
   __device__ bool eval_grad(double sigma, double& g2) {
     double v[1] = {0.0};
-    for (int j = tm.id; j < n; j += tm.count) {
-      Frag<double> out;
-      spmm_row<double>(P, A.U, ld, j, A.lam, A.e, 0.0, -1.0, -sigma, 0.0, tm, out);
+    if (P.a_diag_only) {
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<T> ot;
+        Frag<double> out;
+        spmm_row<T>(P, A.Ut, ld, j, A.lam, A.e, 0.0, -1.0, -sigma, T(0), tm, ot);
+        frag_convert(out, ot);
 #pragma unroll
-      for (int k = 0; k < KMAX; ++k)
+        for (int k = 0; k < KMAX; ++k)
 #pragma unroll
-        for (int e = 0; e < CHUNK; ++e) out.v[k][e] *= -2.0;
-      frag_store(out, A.grad, j, ld, tm);
-      const double d = frag_dot(out, out, tm);
-      if (tm.lane == 0) v[0] += d;
+          for (int e = 0; e < CHUNK; ++e) out.v[k][e] *= -2.0;
+        frag_store(out, A.grad, j, ld, tm);
+        const double d = frag_dot(out, out, tm);
+        if (tm.lane == 0) v[0] += d;
+      }
+    } else {
+      // rows with many entries: one warp per row
+      const WarpRow wr = make_warp_row(ld, sc.tid(), sc.nthreads(), prm.team_mult);
+      for (int j = wr.warp; j < n; j += wr.nwarps) {
+        Frag<T> ot;
+        Frag<double> out;
+        spmm_row_warp<T>(P, A.Ut, ld, j, A.lam, A.e, 0.0, -1.0, -sigma, T(0), wr, ot);
+        frag_convert(out, ot);
+        if (wr.sub == 0) {
+#pragma unroll
+          for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+            for (int e = 0; e < CHUNK; ++e) out.v[k][e] *= -2.0;
+          frag_store(out, A.grad, j, ld, wr.st);
+          const double d = frag_dot(out, out, wr.st);
+          if (wr.st.lane == 0) v[0] += d;
+        }
+      }
     }
     if (!sc.reduce(v, 1)) return false;
     g2 = v[0];
@@ -248,6 +284,7 @@ struct Solver {
 #pragma unroll
           for (int e = 0; e < CHUNK; ++e) g.v[k][e] = -g.v[k][e];
         frag_store(g, A.dir, j, ld, tm);
+        store_shadow(g, dir_shadow(), j);
         const double d = frag_dot(g, g, tm);
         if (tm.lane == 0) v[0] -= d;
       }
@@ -322,6 +359,7 @@ struct Solver {
 #pragma unroll
           for (int e = 0; e < CHUNK; ++e) q.v[k][e] = -q.v[k][e];
         frag_store(q, A.dir, j, ld, tm);
+        store_shadow(q, dir_shadow(), j);
         frag_load(g, A.grad, j, ld, tm);
         const double d = frag_dot(q, g, tm);
         if (tm.lane == 0) v[0] += d;
@@ -342,6 +380,7 @@ struct Solver {
 #pragma unroll
         for (int e = 0; e < CHUNK; ++e) g.v[k][e] = -g.v[k][e];
       frag_store(g, A.dir, j, ld, tm);
+      store_shadow(g, dir_shadow(), j);
     }
     return sc.sync();
   }
@@ -352,13 +391,14 @@ struct Solver {
 #pragma unroll
     for (int i = 0; i < 9; ++i) v[i] = 0.0;
     // <C, U D^T + D U^T> = 2 sum_j D_j . (C U)_j ;  <C, D D^T> = sum_j D_j . (C D)_j
+    const T* Dt = dir_shadow();
     for (int j = tm.id; j < n; j += tm.count) {
-      Frag<double> mCU, mCD, Dj;
-      spmm_row<double>(P, A.U, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCU);
-      spmm_row<double>(P, A.dir, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCD);
-      frag_load(Dj, A.dir, j, ld, tm);
-      const double c1 = -2.0 * frag_dot(Dj, mCU, tm);
-      const double c2 = -frag_dot(Dj, mCD, tm);
+      Frag<T> mCU, mCD, Dj;
+      spmm_row<T>(P, A.Ut, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, T(0), tm, mCU);
+      spmm_row<T>(P, Dt, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, T(0), tm, mCD);
+      frag_load(Dj, Dt, j, ld, tm);
+      const double c1 = -2.0 * (double)frag_dot(Dj, mCU, tm);
+      const double c2 = -(double)frag_dot(Dj, mCD, tm);
       if (tm.lane == 0) {
         v[7] += c1;
         v[8] += c2;
@@ -367,18 +407,18 @@ struct Solver {
     for (int i = tmc.id; i < m; i += tmc.count) {
       const int rr = P.con_r[i], cc = P.con_c[i];
       const double aa = P.con_a[i];
-      Frag<double> Ur, Dc, Dr, Uc;
-      frag_load(Ur, A.U, rr, ld, tmc);
-      frag_load(Dc, A.dir, cc, ld, tmc);
-      frag_load(Dr, A.dir, rr, ld, tmc);
-      frag_load(Uc, A.U, cc, ld, tmc);
+      Frag<T> Ur, Dc, Dr, Uc;
+      frag_load(Ur, A.Ut, rr, ld, tmc);
+      frag_load(Dc, Dt, cc, ld, tmc);
+      frag_load(Dr, Dt, rr, ld, tmc);
+      frag_load(Uc, A.Ut, cc, ld, tmc);
       double e1, e2;
       if (rr != cc) {
-        e1 = 2.0 * aa * team_sum(frag_dot_local(Ur, Dc) + frag_dot_local(Uc, Dr), tmc);
-        e2 = 2.0 * aa * frag_dot(Dr, Dc, tmc);
+        e1 = 2.0 * aa * (double)team_sum(frag_dot_local(Ur, Dc) + frag_dot_local(Uc, Dr), tmc);
+        e2 = 2.0 * aa * (double)frag_dot(Dr, Dc, tmc);
       } else {
-        e1 = 2.0 * aa * frag_dot(Ur, Dr, tmc);
-        e2 = aa * frag_dot(Dr, Dr, tmc);
+        e1 = 2.0 * aa * (double)frag_dot(Ur, Dr, tmc);
+        e2 = aa * (double)frag_dot(Dr, Dr, tmc);
       }
       if (tmc.lane == 0) {
         const double l = A.lam[i], e0 = A.e[i];
@@ -412,6 +452,7 @@ struct Solver {
         for (int e = 0; e < CHUNK; ++e) d.v[k][e] *= t;
       frag_axpy(u, 1.0, d);
       frag_store(u, A.U, j, ld, tm);
+      store_shadow(u, A.Ut, j);
       frag_store(d, A.S + head * NS, j, ld, tm);
       frag_load(g, A.grad, j, ld, tm);
       frag_store(g, A.grad_old, j, ld, tm);
@@ -470,6 +511,7 @@ struct Solver {
           u.v[k][e] = x;
         }
       frag_store(u, A.U, j, ld, tm);
+      store_shadow(u, A.Ut, j);
     }
     return sc.sync();
   }
@@ -947,15 +989,32 @@ struct Solver {
     }
     if (!sc.sync()) return false;
     double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int j = tm.id; j < n; j += tm.count) {
-      Frag<double> Uh, mCU, mSU;
-      frag_load(Uh, A.tmp, j, ld, tm);
-      spmm_row<double>(P, A.tmp, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCU);
-      spmm_row<double>(P, A.tmp, ld, j, A.lam, nullptr, 0.0, -1.0, 0.0, 0.0, tm, mSU);
-      const double o = -frag_dot(Uh, mCU, tm), d = frag_dot(mSU, mSU, tm);
-      if (tm.lane == 0) {
-        v[0] += o;
-        v[1] += d;
+    if (P.a_diag_only) {
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> Uh, mCU, mSU;
+        frag_load(Uh, A.tmp, j, ld, tm);
+        spmm_row<double>(P, A.tmp, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCU);
+        spmm_row<double>(P, A.tmp, ld, j, A.lam, nullptr, 0.0, -1.0, 0.0, 0.0, tm, mSU);
+        const double o = -frag_dot(Uh, mCU, tm), d = frag_dot(mSU, mSU, tm);
+        if (tm.lane == 0) {
+          v[0] += o;
+          v[1] += d;
+        }
+      }
+    } else {
+      const WarpRow wr = make_warp_row(ld, sc.tid(), sc.nthreads(), prm.team_mult);
+      for (int j = wr.warp; j < n; j += wr.nwarps) {
+        Frag<double> Uh, mCU, mSU;
+        frag_load(Uh, A.tmp, j, ld, wr.st);
+        spmm_row_warp<double>(P, A.tmp, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, wr, mCU);
+        spmm_row_warp<double>(P, A.tmp, ld, j, A.lam, nullptr, 0.0, -1.0, 0.0, 0.0, wr, mSU);
+        if (wr.sub == 0) {
+          const double o = -frag_dot(Uh, mCU, wr.st), d = frag_dot(mSU, mSU, wr.st);
+          if (wr.st.lane == 0) {
+            v[0] += o;
+            v[1] += d;
+          }
+        }
       }
     }
     for (int i = tmc.id; i < m; i += tmc.count) {

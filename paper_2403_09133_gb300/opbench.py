@@ -72,7 +72,11 @@ def main():
         last = out[-1]
         print(json.dumps({"op": "solve", "family": a.family, "n": n, "m": m, "prec": a.prec,
                           "admm_iters": last["admm_iters"], "cg_iters": last["cg_iters"],
-                          "status": last["status"], "ms_phase1": last["time_phase1_s"] * 1e3,
+                          "status": last["status"], "rank": last["rank"],
+                          "alm_outer": last["alm_outer"], "lbfgs_iters": last["lbfgs_iters"],
+                          "rank_growths": last["rank_growths"], "sigma": last["sigma"],
+                          "rho": last["rho"], "r_P": last["r_P"], "r_stop": last["r_stop"],
+                          "ms_phase1": last["time_phase1_s"] * 1e3,
                           "ms_phase2": last["time_phase2_s"] * 1e3,
                           "us_per_admm_iter": last["time_phase2_s"] * 1e6 / max(1, last["admm_iters"])}),
               flush=True)
