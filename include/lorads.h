@@ -71,7 +71,8 @@ typedef struct lorads_params {
   double rho_max;          /* 5000 (Section 5.1)                                             */
   double rho_growth;       /* 1.2 (Section 5.1)                                              */
   int32_t rho_every;       /* 5 (Section 5.1)                                                */
-  double gamma_scale;      /* gamma = gamma_scale * max_j sum_k |C_jk| (paper silent): 1     */
+  double gamma_scale;      /* gamma = gamma_scale * max_j sum_k |C_jk| (paper silent); < 0:  */
+                           /*    1 when every constraint is one diagonal entry, else 2 (-1)  */
   double gamma_fixed;      /* > 0 overrides gamma                                            */
   int32_t max_admm_iter;   /* 5000 (Section 5.2)                                             */
   int32_t cg_max_iter;     /* 1000                                                           */
@@ -93,6 +94,17 @@ typedef struct lorads_params {
   int32_t grid;            /* solver CTAs (0 = library choice; 1 forces one-CTA scope)       */
   int32_t team_mult;       /* lanes per factor row = team_mult x the minimum for the rank    */
                            /* (1, 2, 4, 8; 0 = 1, or autotuned by lorads_solve_batch)         */
+  int32_t kkt_dinf;        /* 1: the final test includes the Appendix B dual infeasibility   */
+                           /*    (needs lanczos_steps > 0); 0: primal test and gap only (1)   */
+  int32_t lanczos_steps;   /* Lanczos steps of each lambda_min(C - A^T y) estimate, <= 512;  */
+                           /*    0 = no estimate (kkt_dinf must be 0) (128)                   */
+  int32_t dinf_every;      /* after a failed dual-infeasibility test at iteration k, the next */
+                           /*    waits max(dinf_every, k / 10) iterations (10)                */
+  double escape_scale;     /* when a dual-infeasibility test fails less than 10% below the   */
+                           /*    previous failed one, Phase II raises the rank by rank_factor */
+                           /*    (up to rank_max) with the eigenvector z of lambda_min as new */
+                           /*    column of U and V, scaled to escape_scale ||U_hat||_F/sqrt(r)*/
+                           /*    (0.3; 0 = never)                                             */
 } lorads_params;
 
 /* ---------------------------------------------------------------- result */
@@ -114,9 +126,12 @@ typedef struct lorads_result {
   int32_t hessian_applies; /* Hessian-vector products (CG iterations + warm-start residuals) */
   int32_t alm_outer;       /* Phase I outer iterations                                       */
   int32_t lbfgs_iters;     /* Phase I L-BFGS iterations                                      */
-  int32_t rank_growths;    /* rank increases                                                 */
+  int32_t rank_growths;    /* rank increases (Phase I and Phase II)                          */
   double time_phase1_s;    /* device time of Phase I                                         */
   double time_phase2_s;    /* device time of Phase II and the output step                    */
+  double p_infeas;         /* ||A(X) - b||_2 / (1 + ||b||_1)                    (Appendix B)  */
+  double d_infeas;         /* max(0, -lambda_min) / (1 + ||vec(C)||_1)          (Appendix B)  */
+  double lambda_min;       /* Lanczos estimate of lambda_min(C - A^T y) (NaN: not computed)  */
 } lorads_result;
 
 typedef struct lorads_problem lorads_problem;
@@ -157,7 +172,12 @@ int lorads_set_start(lorads_problem *p, int32_t r, const double *U0, const doubl
 
 /* Algorithm 2 on the device.  stream is a cudaStream_t (NULL = the legacy default stream);
  * the call returns when the solve has finished.  res may be NULL.  The return value is
- * the solve status (also res->status). */
+ * the solve status (also res->status).  Phase II ends (LORADS_OK) when the output
+ * X = U_hat U_hat^T, y = -lambda passes, in this order: the paper's termination
+ * ||A(X) - b||_2 / (1 + ||b||_inf) <= tol (Section 5.2), the Appendix B gap |gap| <= tol, and,
+ * with kkt_dinf, the Appendix B dual infeasibility <= tol (lambda_min by Lanczos, tested at
+ * most once per max(dinf_every, k/10) iterations after a failure); otherwise after
+ * max_admm_iter iterations with LORADS_ERR_MAXITER. */
 int lorads_solve(lorads_problem *p, const lorads_params *prm, void *stream, lorads_result *res);
 
 /* Solves count independent problems (same device) in one persistent launch: one CTA per

@@ -29,6 +29,17 @@ def min_eig_dual_slack(sdp: SDP, y, dense_limit: int = 2500) -> float:
     return float(vals[0])
 
 
+def min_eig_pair_dual_slack(sdp: SDP, y, dense_limit: int = 2500):
+    """(lambda_min, unit eigenvector) of S = C - A^T y."""
+    S = sdp.dual_slack(y)
+    if sdp.n <= dense_limit:
+        Sd = S.toarray() if sp.issparse(S) else np.asarray(S)
+        w, Z = np.linalg.eigh(0.5 * (Sd + Sd.T))
+        return float(w[0]), Z[:, 0]
+    w, Z = spla.eigsh(S, k=1, which="SA", tol=1e-10, maxiter=20000)
+    return float(w[0]), Z[:, 0] / np.linalg.norm(Z[:, 0])
+
+
 def exhaustive_maxcut(n: int, edges, w) -> float:
     """max over x in {-1,1}^n of sum_{(i,j)} w_ij (1 - x_i x_j)/2, with x_0 fixed."""
     if n > 22:

@@ -26,9 +26,19 @@ are the readings the CUDA library uses as well):
   * CG stops at ||R|| <= max(1e-3 ||R_0||, 1e-13 ||G||), R_0 the residual of the warm
     start, at most cg_max_iter steps;
   * the CG for the V-step starts from U^{k+1};
-  * Phase II stops on eq. stop (primal infeasibility of U V^T and gamma ||dV||) with the
-    output U_hat U_hat^T also primal feasible to tol; dual stationarity, the duality gap
-    and lambda_min(C - A^T y) are reported, not tested;
+  * Phase II stops when the output X = U_hat U_hat^T, y = -lambda meets the paper's own
+    termination (primal infeasibility ||A(X) - b||_2 / (1 + ||b||_inf) <= tol, the
+    SDPLR-aligned rule of Section 5.2) and, in addition, the two other error measures of
+    Appendix B: the primal-dual gap and the dual infeasibility
+    max(0, -lambda_min(C - A^T y)) / (1 + ||c||_1), each <= tol.  The tests are taken in
+    that order (each only when the previous ones hold); after a failed dual-infeasibility
+    test the next one waits max(10, k // 10) iterations.  Eq. stop's second term
+    gamma ||dV|| / (1 + ||V||) is reported, not tested;
+  * a dual infeasibility that fell by less than 10% since the previous (failed) test means
+    the rank is too small for the instance (lambda_min(C - A^T y) < 0 persists at a primal-dual
+    pair that is otherwise converged): Phase II then raises the rank as Section 4.3 does
+    (factor 1.5, same cap), the new columns of U and V being tau z, 0, ..., 0 with z the unit
+    eigenvector of lambda_min and tau = escape_scale ||U_hat||_F / sqrt(r);
   * Phase I: sigma_0 = 1/(1+||b||_inf), sigma *= 2 when r_P fails to fall 4x in an outer
     step, L-BFGS memory 4, inner stop at ||grad||_F/(1+||C||_F) <= min(0.1, 10 r_P), rank growth
     when an inner solve needs more than 300 iterations (switch test first).
@@ -47,6 +57,7 @@ from typing import Callable, List, Optional
 
 import numpy as np
 
+from .certify import min_eig_dual_slack, min_eig_pair_dual_slack
 from .sdp import SDP
 
 
@@ -82,6 +93,9 @@ class Params:
     new_col_std: float = 1e-2
     seed: int = 1
     phase1: bool = True           # False: caller supplies U0 / lambda0 / rho0
+    kkt_dinf: bool = True         # the Appendix B dual infeasibility is part of the stop
+    dinf_every: int = 10          # after a failed dual test: wait max(dinf_every, k // 10)
+    escape_scale: float = 0.3     # Phase II rank growth along the lambda_min eigenvector
 
 
 # ======================================================================================
@@ -171,6 +185,18 @@ def primal_infeasibility(sdp: SDP, U, V) -> float:
     return float(np.linalg.norm(sdp.A_of(U, V) - sdp.b) / (1.0 + sdp.b_inf))
 
 
+def pd_gap(sdp: SDP, Uh, y) -> float:
+    """Appendix B primal-dual gap (<C, X> - b^T y) / (1 + |<C, X>| + |b^T y|), X = Uh Uh^T."""
+    pobj = sdp.C_inner(Uh, Uh)
+    dobj = float(sdp.b @ y)
+    return (pobj - dobj) / (1.0 + abs(pobj) + abs(dobj))
+
+
+def dual_infeasibility(sdp: SDP, y) -> float:
+    """Appendix B dual infeasibility max(0, -lambda_min(C - A^T y)) / (1 + ||c||_1)."""
+    return max(0.0, -min_eig_dual_slack(sdp, y)) / (1.0 + sdp.c_one)
+
+
 def dual_stationarity(sdp: SDP, Uh, lam) -> float:
     """||(C + A^T(lambda)) U_hat||_F / (1 + ||C||_F): first line of eq. def:eKKT with
     f = <C, .> and multiplier 2 lambda (Theorem 1), i.e. y = -lambda."""
@@ -248,6 +274,7 @@ class AdmmState:
     k: int = 0
     cg_iters: int = 0
     rp: float = math.inf
+    growths: int = 0
 
 
 def admm_iteration(sdp: SDP, st: AdmmState, p: Params) -> dict:
@@ -282,17 +309,49 @@ def admm_iteration(sdp: SDP, st: AdmmState, p: Params) -> dict:
 
 
 def lradmm(sdp: SDP, U0, V0, lam0, rho0: float, p: Params, trace: Optional[list] = None):
-    """Algorithm 1 until eq. stop holds and the output U_hat U_hat^T is feasible too:
-    max(r_P(U V^T), gamma ||V^{k+1}-V^k||_F/(1+||V^k||_F), r_P(U_hat U_hat^T)) <= tol."""
+    """Algorithm 1 until the output X = U_hat U_hat^T, y = -lambda satisfies, in this order,
+    r_P(X) = ||A(X) - b||_2 / (1 + ||b||_inf) <= tol (the paper's termination, Section 5.2),
+    |Appendix B gap| <= tol and Appendix B dual infeasibility <= tol (the last tested at
+    most once per max(dinf_every, k // 10) iterations after a failure)."""
     st = AdmmState(U=U0.copy(), V=V0.copy(), lam=lam0.copy(), rho=rho0,
                    rp=primal_infeasibility(sdp, U0, V0))
     converged = False
+    next_dual_test = 0
+    prev_dinf = None
+    cap = rank_cap(sdp.m, sdp.n, p)
     while st.k < p.max_admm_iter:
         info = admm_iteration(sdp, st, p)
+        if info["rp_hat"] <= p.tol:
+            Uh = 0.5 * (st.U + st.V)
+            y = -st.lam
+            info["gap"] = pd_gap(sdp, Uh, y)
+            if abs(info["gap"]) <= p.tol:
+                if not p.kkt_dinf:
+                    converged = True
+                elif st.k >= next_dual_test:
+                    info["d_inf"] = dual_infeasibility(sdp, y)
+                    if info["d_inf"] <= p.tol:
+                        converged = True
+                    else:
+                        next_dual_test = st.k + max(p.dinf_every, st.k // 10)
+                        r = st.U.shape[1]
+                        if (prev_dinf is not None and info["d_inf"] > 0.9 * prev_dinf
+                                and p.escape_scale > 0 and r < cap):
+                            _, z = min_eig_pair_dual_slack(sdp, y)
+                            r_new = max(next_rank(r, cap, p), r + 1)
+                            tau = p.escape_scale * float(np.linalg.norm(Uh)) / math.sqrt(r)
+                            add = np.zeros((sdp.n, r_new - r))
+                            add[:, 0] = tau * z
+                            st.U = np.concatenate([st.U, add], axis=1)
+                            st.V = np.concatenate([st.V, add], axis=1)
+                            st.growths += 1
+                            info["grow_to"] = r_new
+                            prev_dinf = None
+                        else:
+                            prev_dinf = info["d_inf"]
         if trace is not None:
             trace.append(info)
-        if max(info["rp"], info["rs"], info["rp_hat"]) <= p.tol:
-            converged = True
+        if converged:
             break
     return st, converged
 
@@ -472,9 +531,11 @@ def kkt_report(sdp: SDP, Uh, y, min_eig: Optional[float] = None) -> dict:
         r_P=primal_infeasibility(sdp, Uh, Uh),
         r_D=dual_stationarity(sdp, Uh, -y),
         gap=(pobj - dobj) / (1.0 + abs(pobj) + abs(dobj)),
+        p_infeas=float(np.linalg.norm(sdp.A_of(Uh, Uh) - sdp.b)) / (1.0 + sdp.b_one),
     )
     if min_eig is not None:
-        rep["r_S"] = max(0.0, -min_eig) / (1.0 + sdp.c_one)
+        rep["lambda_min"] = min_eig
+        rep["d_infeas"] = max(0.0, -min_eig) / (1.0 + sdp.c_one)
     return rep
 
 
@@ -500,11 +561,11 @@ def lorads(sdp: SDP, p: Params = Params(), U0=None, lam0=None, rho0=None,
     t2 = time.perf_counter()
     Uh = 0.5 * (st.U + st.V)
     y = -st.lam
-    rep = kkt_report(sdp, Uh, y)
+    rep = kkt_report(sdp, Uh, y, min_eig_dual_slack(sdp, y))
     if trace is not None:
         trace["phase1"] = tr1
         trace["phase2"] = tr2
     return dict(U=st.U, V=st.V, U_hat=Uh, lam=st.lam, y=y, rank=Uh.shape[1],
                 converged=converged, admm_iters=st.k, cg_iters=st.cg_iters, rho=st.rho,
-                alm_outer=ph1["outer"], lbfgs_iters=ph1["inner"], growths=ph1["growths"],
+                alm_outer=ph1["outer"], lbfgs_iters=ph1["inner"], growths=ph1["growths"] + st.growths,
                 t_phase1=t1 - t0, t_phase2=t2 - t1, **rep)

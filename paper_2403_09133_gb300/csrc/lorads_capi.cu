@@ -86,7 +86,7 @@ struct lorads_problem {
   Arena prob_mem;
   DevProblem dp{};
   bool diag_separable = false;
-  double C_fro = 0, C_inf = 0, b_inf = 0;
+  double C_fro = 0, C_inf = 0, b_inf = 0, b_one = 0, c_one = 0;
   // solver state
   Arena state_mem;
   double* dU = nullptr;
@@ -217,7 +217,7 @@ static int assemble(lorads_problem* p) {
   std::vector<double> C_val;
   build_sym_csr(n, cent, C_rp, C_col, C_dummy, C_val);
   // norms of the data
-  double cf = 0.0, cinf = 0.0;
+  double cf = 0.0, cinf = 0.0, cone = 0.0;
   for (int64_t j = 0; j < n; ++j) {
     double rs = 0.0;
     for (int32_t q = C_rp[j]; q < C_rp[j + 1]; ++q) {
@@ -225,12 +225,18 @@ static int assemble(lorads_problem* p) {
       rs += std::fabs(C_val[q]);
     }
     cinf = std::max(cinf, rs);
+    cone += rs;
   }
-  double binf = 0.0;
-  for (double x : p->b) binf = std::max(binf, std::fabs(x));
+  double binf = 0.0, bone = 0.0;
+  for (double x : p->b) {
+    binf = std::max(binf, std::fabs(x));
+    bone += std::fabs(x);
+  }
   p->C_fro = std::sqrt(cf);
   p->C_inf = cinf;
   p->b_inf = binf;
+  p->c_one = cone;
+  p->b_one = bone;
   // diagonal-separable constraints: U_0 rows can be scaled onto the constraints
   std::vector<double> row_norm(n, -1.0);
   bool dsep = true;
@@ -303,6 +309,8 @@ static int assemble(lorads_problem* p) {
   dp.b_inf = binf;
   dp.C_fro = p->C_fro;
   dp.C_inf = cinf;
+  dp.b_one = bone;
+  dp.c_one = cone;
   bool diag_only = true;
   for (int64_t i = 0; i < m; ++i) diag_only = diag_only && (con_r[i] == con_c[i]);
   // row-local form needs at most one constraint per row
@@ -359,8 +367,8 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   dv.rho_max = prm->rho_max;
   dv.rho_growth = prm->rho_growth;
   dv.rho_every = std::max(1, prm->rho_every);
-  dv.gamma = prm->gamma_fixed > 0 ? prm->gamma_fixed
-                                  : prm->gamma_scale * (p->C_inf > 0 ? p->C_inf : 1.0);
+  const double gscale = prm->gamma_scale >= 0 ? prm->gamma_scale : (p->diag_separable ? 1.0 : 2.0);
+  dv.gamma = prm->gamma_fixed > 0 ? prm->gamma_fixed : gscale * (p->C_inf > 0 ? p->C_inf : 1.0);
   dv.max_admm_iter = prm->max_admm_iter;
   dv.cg_max_iter = prm->cg_max_iter;
   dv.cg_rel_tol = prm->cg_rel_tol;
@@ -381,6 +389,13 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   dv.team_mult = prm->team_mult > 0 ? prm->team_mult : 1;
   if (dv.team_mult != 1 && dv.team_mult != 2 && dv.team_mult != 4 && dv.team_mult != 8)
     return LORADS_ERR_ARG;
+  dv.kkt_dinf = prm->kkt_dinf ? 1 : 0;
+  dv.lanczos_steps = prm->lanczos_steps;
+  dv.dinf_every = std::max(1, prm->dinf_every);
+  dv.escape_scale = prm->escape_scale;
+  if (!(prm->escape_scale >= 0.0)) return LORADS_ERR_ARG;
+  if (prm->lanczos_steps < 0 || prm->lanczos_steps > LANCZOS_MAX) return LORADS_ERR_ARG;
+  if (dv.kkt_dinf && prm->lanczos_steps == 0) return LORADS_ERR_ARG;
   if (!dv.phase1) {
     if (!p->has_start) return LORADS_ERR_STATE;
     if (p->start_r > 256) return LORADS_ERR_ARG;
@@ -491,6 +506,9 @@ static void to_result(const SolveOut& out, lorads_result& r) {
   r.rank_growths = out.growths;
   r.time_phase1_s = out.t_phase1_ns * 1e-9;
   r.time_phase2_s = out.t_phase2_ns * 1e-9;
+  r.p_infeas = out.p_infeas;
+  r.d_infeas = out.d_infeas;
+  r.lambda_min = out.lambda_min;
 }
 
 static void record_solution(lorads_problem* p, const SolveOut& out, const lorads_result& r) {
@@ -730,7 +748,7 @@ void lorads_default_params(lorads_params* prm) {
   prm->rho_max = 5000.0;
   prm->rho_growth = 1.2;
   prm->rho_every = 5;
-  prm->gamma_scale = 1.0;
+  prm->gamma_scale = -1.0;
   prm->gamma_fixed = 0.0;
   prm->max_admm_iter = 5000;
   prm->cg_max_iter = 1000;
@@ -751,6 +769,10 @@ void lorads_default_params(lorads_params* prm) {
   prm->threads = 0;
   prm->grid = 0;
   prm->team_mult = 0;
+  prm->kkt_dinf = 1;
+  prm->lanczos_steps = 128;
+  prm->dinf_every = 10;
+  prm->escape_scale = 0.3;
 }
 
 int lorads_set_start(lorads_problem* p, int32_t r, const double* U0, const double* lambda0,

@@ -48,6 +48,7 @@ struct DevProblem {
   // diagonal entry on its own row with b/a > 0): U_0 row j gets norm row_norm[j] (< 0: keep)
   const double* row_norm;
   double b_inf, C_fro, C_inf;
+  double b_one, c_one;   // ||b||_1 and ||vec(C)||_1 (the normalisations of Appendix B)
   // every constraint is a diagonal entry: the Hessian of eq. linU is row-local; then
   // row_con[j] is the constraint on row j (-1: none) and row_a[j] its value (0: none)
   int a_diag_only;

@@ -10,7 +10,7 @@ constexpr int GRID_THREADS_MAX = 320;     // grid solver: CTA size chosen per pr
 
 // one CTA per problem; CTAs take problems from a queue (batches), or a single problem
 template <typename T>
-__global__ void __launch_bounds__(SOLVER_THREADS)
+__global__ void __launch_bounds__(SOLVER_THREADS, 1)
 solve_block_kernel(const SolverArgs<T>* args, int count, int* queue) {
   __shared__ double red[33 * MAXRED];
   __shared__ SolverArgs<T> sa;
@@ -30,7 +30,7 @@ solve_block_kernel(const SolverArgs<T>* args, int count, int* queue) {
 
 // one problem over the whole grid (cooperative launch: all CTAs co-resident)
 template <typename T>
-__global__ void __launch_bounds__(GRID_THREADS_MAX)
+__global__ void __launch_bounds__(GRID_THREADS_MAX, 1)
 solve_grid_kernel(const SolverArgs<T>* args, GridCtl* ctl, double* partials, long long spin) {
   __shared__ double red[33 * MAXRED];
   __shared__ SolverArgs<T> sa;

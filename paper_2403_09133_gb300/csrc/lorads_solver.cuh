@@ -35,12 +35,19 @@ struct DevParams {
   double rho0;
   long long time_limit_ns;
   int team_mult;   // lanes per row = team_mult * the minimum for ld (autotuned for batches)
+  int kkt_dinf;    // the Appendix B dual infeasibility is part of the final test
+  int lanczos_steps;
+  int dinf_every;
+  double escape_scale;   // Phase II rank growth along the lambda_min eigenvector (0: off)
 };
+
+constexpr int LANCZOS_MAX = 512;   // Lanczos steps of one lambda_min estimate, at most
 
 struct SolveOut {
   int status, rank, ld, admm_iters, cg_iters, hess_applies, alm_outer, lbfgs_iters, growths;
   int pad;
   double objective, dual_objective, r_P, r_P_split, r_stop, r_D, gap, rho, gamma, sigma;
+  double p_infeas, d_infeas, lambda_min;
   long long t_phase1_ns, t_phase2_ns;
 };
 
@@ -68,6 +75,8 @@ struct SolverArgs {
   double* S;      // lbfgs_mem * n * ld_cap
   double* Y;
   double* tmp;    // n * ld_cap (rank growth, U_hat)
+  // Phase II reuses grad / grad_old / dir as the three n x 4 Lanczos blocks and S as the
+  // Lanczos coefficients (8 per step; S holds ring * n * ld_cap >= 8 n doubles)
   long long ld_cap;
   SolveOut* out;
 };
@@ -154,11 +163,14 @@ struct Solver {
   // counters
   int cg_iters, hess, admm_iters, alm_outer, lbfgs_iters, growths;
   double last_rs;
+  double last_lmin;   // latest lambda_min(C - A^T y) estimate ...
+  int lmin_at;        // ... and the Phase II iteration count it belongs to (-1: none)
+  double uh_norm2;    // ||U_hat||_F^2 from the latest gap test
 
   __device__ Solver(const SolverArgs<T>& a, Scope& s)
       : A(a), sc(s), P(a.P), prm(a.prm), n(a.P.n), m(a.P.m), r(0), ld(0), status(ST_OK),
         cg_iters(0), hess(0), admm_iters(0), alm_outer(0), lbfgs_iters(0), growths(0),
-        last_rs(0.0) {}
+        last_rs(0.0), last_lmin(NAN), lmin_at(-1), uh_norm2(0.0) {}
 
   __device__ void set_rank(int rr) {
     r = rr;
@@ -934,6 +946,8 @@ struct Solver {
   __device__ bool phase2(double rho, double& rho_out) {
     const double gamma = prm.gamma;
     const bool local = P.a_diag_only != 0;
+    int next_dual_test = 0;
+    double prev_dinf = NAN;
     for (int k = 0; k < prm.max_admm_iter; ++k) {
       double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
       if (local) {
@@ -962,9 +976,44 @@ struct Solver {
       const double rs = gamma * sqrt(v[2]) / (1.0 + sqrt(v[3]));
       last_rs = rs;
       if (!(rp == rp) || !(rs == rs)) { status = ST_NAN; break; }
-      if (fmax(rp, fmax(rs, rph)) <= prm.tol) {
-        rho_out = rho;
-        return true;
+      // final test on X = U_hat U_hat^T, y = -lambda^{k+1}: the paper's primal test, then
+      // the Appendix B gap, then the Appendix B dual infeasibility (rate-limited)
+      if (rph <= prm.tol) {
+        double gap;
+        if (!gap_check(gap)) return false;
+        if (fabs(gap) <= prm.tol) {
+          bool done = !prm.kkt_dinf;
+          if (!done && admm_iters >= next_dual_test) {
+            if (!lanczos_lambda_min(last_lmin)) return false;
+            lmin_at = admm_iters;
+            const double dinf = fmax(0.0, -last_lmin) / (1.0 + P.c_one);
+            done = dinf <= prm.tol;
+            if (!done) {
+              next_dual_test = admm_iters + max(prm.dinf_every, admm_iters / 10);
+              // a dual infeasibility that fell by less than 10% since the previous test (a
+              // stationary point of the rank-r problem): grow the rank along the eigenvector
+              // of lambda_min
+              if (prev_dinf == prev_dinf && dinf > 0.9 * prev_dinf && prm.escape_scale > 0.0 &&
+                  r < prm.rank_cap) {
+                double zn2 = 0.0, lm;
+                if (!lanczos_lambda_min(lm, true, &zn2)) return false;
+                const int K = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
+                int r_new = (int)ceil(prm.rank_factor * r - 1e-9);
+                if (r_new <= r) r_new = r + 1;
+                if (r_new > prm.rank_cap) r_new = prm.rank_cap;
+                if (!grow_rank_phase2(r_new, A.Y + 2 * K, zn2)) return false;
+                ++growths;
+                prev_dinf = NAN;
+              } else {
+                prev_dinf = dinf;
+              }
+            }
+          }
+          if (done) {
+            rho_out = rho;
+            return true;
+          }
+        }
       }
       if ((long long)v[4] > prm.time_limit_ns) { status = ST_TIMEOUT; break; }
       if ((k + 1) % prm.rho_every == 0) rho = fmin(rho * prm.rho_growth, prm.rho_max);
@@ -974,8 +1023,8 @@ struct Solver {
     return true;
   }
 
-  // U_hat, objective, dual stationarity, output infeasibility, b^T lambda
-  __device__ bool output(double* res) {
+  // U_hat = (U + V)/2 into tmp
+  __device__ bool form_u_hat() {
     for (int j = tm.id; j < n; j += tm.count) {
       Frag<double> u, w;
       frag_load(u, A.U, j, ld, tm);
@@ -987,7 +1036,347 @@ struct Solver {
         for (int e = 0; e < CHUNK; ++e) u.v[k][e] *= 0.5;
       frag_store(u, A.tmp, j, ld, tm);
     }
+    return sc.sync();
+  }
+
+  // Appendix B primal-dual gap of X = U_hat U_hat^T, y = -lambda:
+  // (<C, X> - b^T y) / (1 + |<C, X>| + |b^T y|), in FP64 from the masters
+  __device__ bool gap_check(double& gap) {
+    if (!form_u_hat()) return false;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (P.a_diag_only) {
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> Uh, mCU;
+        frag_load(Uh, A.tmp, j, ld, tm);
+        spmm_row<double>(P, A.tmp, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCU);
+        const double o = -frag_dot(Uh, mCU, tm), u2 = frag_dot(Uh, Uh, tm);
+        if (tm.lane == 0) {
+          v[0] += o;
+          v[2] += u2;
+        }
+      }
+    } else {
+      const WarpRow wr = make_warp_row(ld, sc.tid(), sc.nthreads(), prm.team_mult);
+      for (int j = wr.warp; j < n; j += wr.nwarps) {
+        Frag<double> Uh, mCU;
+        frag_load(Uh, A.tmp, j, ld, wr.st);
+        spmm_row_warp<double>(P, A.tmp, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, wr, mCU);
+        if (wr.sub == 0) {
+          const double o = -frag_dot(Uh, mCU, wr.st), u2 = frag_dot(Uh, Uh, wr.st);
+          if (wr.st.lane == 0) {
+            v[0] += o;
+            v[2] += u2;
+          }
+        }
+      }
+    }
+    for (int i = sc.tid(); i < m; i += sc.nthreads()) v[1] += P.b[i] * A.lam[i];
+    if (!sc.reduce(v, 3)) return false;
+    uh_norm2 = v[2];
+    const double pobj = v[0], dobj = -v[1];
+    gap = (pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+    return true;
+  }
+
+  // lambda_min(C - A^T y), y = -lambda: Lanczos on M = -(C + A^T(lambda)) from four random
+  // start columns at once (an n x 4 block in the factor layout of width 4), K =
+  // min(lanczos_steps, n) steps each, no reorthogonalisation; the estimate is -max_c theta_c,
+  // theta_c the largest eigenvalue of column c's tridiagonal (Sturm-count multisection).
+  // Column c stops early when its beta vanishes (its Krylov space is exhausted).
+  // With want_vec the Ritz vector of the estimate is rebuilt too: the eigenvector s of the
+  // chosen T_c by inverse iteration, then a second pass of the same recurrence (the stored
+  // alpha / beta, the same start) accumulates z = sum_k s_k q_k into A.Y + 2K (n entries);
+  // zn2 receives ||z||^2.
+  __device__ __noinline__ bool lanczos_lambda_min(double& lmin, bool want_vec = false,
+                                                  double* zn2 = nullptr) {
+    constexpr int NC = 4;
+    const int K = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
+    if (K <= 0) {
+      lmin = NAN;
+      return true;
+    }
+    double* Qp = A.dir;     // raw q_{k-1} (true vector: qps * Qp)
+    double* Q = A.grad;     // raw q_k     (true vector: qs * Q)
+    double* W = A.grad_old;
+    double* hist = A.S;     // alpha_k[c] at hist[8k + c], beta_k[c] at hist[8k + 4 + c]
+    const Team t4 = make_team(NC, sc.tid(), sc.nthreads(), 1);     // one thread per row
+    const WarpRow w4 = make_warp_row(NC, sc.tid(), sc.nthreads(), 1);
+    const uint64_t key = stream_key(prm.seed, 4000);
+    double v[NC] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = sc.tid(); j < n; j += sc.nthreads())
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double x = normal_at(key, (uint64_t)j * NC + c);
+        Q[(long long)j * NC + c] = x;
+        Qp[(long long)j * NC + c] = 0.0;
+        v[c] += x * x;
+      }
+    if (!sc.reduce(v, NC)) return false;
+    double qs[NC], qps[NC], bp[NC], qs0[NC];
+    int len[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      qs[c] = v[c] > 0.0 ? 1.0 / sqrt(v[c]) : 0.0;
+      qs0[c] = qs[c];
+      qps[c] = 0.0;
+      bp[c] = 0.0;
+      len[c] = v[c] > 0.0 ? K : 0;
+    }
+    for (int k = 0; k < K; ++k) {
+      // W = M q_k - beta_{k-1} q_{k-1};  alpha_k = q_k . W
+      double a[NC] = {0.0, 0.0, 0.0, 0.0};
+      const bool diag = P.a_diag_only != 0;
+      const int j0 = diag ? t4.id : w4.warp, js = diag ? t4.count : w4.nwarps;
+      for (int j = j0; j < n; j += js) {
+        Frag<double> mq;
+        if (diag) {
+          spmm_row<double>(P, Q, NC, j, A.lam, nullptr, 0.0, -1.0, 0.0, 0.0, t4, mq);
+        } else {
+          spmm_row_warp<double>(P, Q, NC, j, A.lam, nullptr, 0.0, -1.0, 0.0, 0.0, w4, mq);
+          if (w4.sub != 0) continue;
+        }
+        const long long o = (long long)j * NC;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const double w = qs[c] * mq.v[0][c] - bp[c] * qps[c] * Qp[o + c];
+          W[o + c] = w;
+          a[c] += qs[c] * Q[o + c] * w;
+        }
+      }
+      if (!sc.reduce(a, NC)) return false;
+      // W -= alpha_k q_k;  beta_k = ||W||
+      double b2[NC] = {0.0, 0.0, 0.0, 0.0};
+      for (int j = sc.tid(); j < n; j += sc.nthreads()) {
+        const long long o = (long long)j * NC;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const double w = W[o + c] - a[c] * qs[c] * Q[o + c];
+          W[o + c] = w;
+          b2[c] += w * w;
+        }
+      }
+      if (!sc.reduce(b2, NC)) return false;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double beta = sqrt(b2[c]);
+        if (sc.is_leader()) {
+          hist[8 * k + c] = a[c];
+          hist[8 * k + 4 + c] = beta;
+        }
+        const bool live = len[c] > k + 1;
+        const bool breakdown = !(beta > 1e-12 * (fabs(a[c]) + bp[c]) && beta > 1e-300);
+        if (live && breakdown) len[c] = k + 1;
+        qps[c] = qs[c];
+        qs[c] = len[c] > k + 1 ? 1.0 / beta : 0.0;
+        bp[c] = len[c] > k + 1 ? beta : 0.0;
+      }
+      double* t = Qp;
+      Qp = Q;
+      Q = W;
+      W = t;
+    }
+    if (!sc.sync()) return false;       // the coefficients written by the leader
+    // largest eigenvalue of each T_c: warp c of every CTA, 32-point multisection on the
+    // Sturm count (identical in every CTA, so every thread ends with the same estimate)
+    __shared__ double theta[NC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < NC) {
+      const int c = warp, L = len[c];
+      double th = -INFINITY;
+      if (L > 0) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int i = lane; i < L; i += 32) {
+          const double ai = hist[8 * i + c];
+          const double bl = i > 0 ? fabs(hist[8 * (i - 1) + 4 + c]) : 0.0;
+          const double br = i + 1 < L ? fabs(hist[8 * i + 4 + c]) : 0.0;
+          lo = fmin(lo, ai - bl - br);
+          hi = fmax(hi, ai + bl + br);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+          hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+        }
+        for (int round = 0; round < 11; ++round) {
+          const double width = hi - lo;
+          const double x = lo + width * (double)(lane + 1) / 33.0;
+          int below = 0;      // eigenvalues of T_c below x
+          double d = 1.0;
+          for (int i = 0; i < L; ++i) {
+            const double ai = hist[8 * i + c];
+            if (i == 0) {
+              d = ai - x;
+            } else {
+              const double bi = hist[8 * (i - 1) + 4 + c];
+              d = (ai - x) - bi * bi / d;
+            }
+            if (fabs(d) < 1e-300) d = -1e-300;
+            below += d < 0.0;
+          }
+          // lanes whose x lies above every eigenvalue form a suffix; the top eigenvalue
+          // lies between the last x below it and the first x above it
+          const unsigned above = __ballot_sync(0xffffffffu, below >= L);
+          const int f = above ? __ffs(above) - 1 : 32;
+          const double nlo = f == 0 ? lo : lo + width * (double)f / 33.0;
+          const double nhi = f == 32 ? hi : lo + width * (double)(f + 1) / 33.0;
+          lo = nlo;
+          hi = nhi;
+        }
+        th = 0.5 * (lo + hi);
+      }
+      if (lane == 0) theta[c] = th;
+    }
+    __syncthreads();
+    double best = -INFINITY;
+    int cs = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (theta[c] > best) {
+        best = theta[c];
+        cs = c;
+      }
+    __syncthreads();
+    lmin = best > -INFINITY ? -best : NAN;
+    if (!want_vec) return true;
+    // eigenvector of T_cs for theta by two steps of inverse iteration (Thomas elimination of
+    // T_cs - theta I; pivots below 1e-300 are nudged), one thread
+    const int L = len[cs];
+    double* sv = A.Y;          // s (L entries)
+    double* cp = A.Y + K;      // elimination scratch
+    double* zv = A.Y + 2 * K;  // the Ritz vector
+    if (sc.is_leader() && L > 0) {
+      for (int i = 0; i < L; ++i) sv[i] = 1.0;
+      for (int it = 0; it < 2; ++it) {
+        double piv = hist[c8(0, cs)] - best;
+        if (fabs(piv) < 1e-300) piv = 1e-300;
+        cp[0] = L > 1 ? hist[c8(0, cs) + 4] / piv : 0.0;
+        sv[0] = sv[0] / piv;
+        for (int i = 1; i < L; ++i) {
+          const double bl = hist[c8(i - 1, cs) + 4];
+          piv = (hist[c8(i, cs)] - best) - bl * cp[i - 1];
+          if (fabs(piv) < 1e-300) piv = 1e-300;
+          cp[i] = i + 1 < L ? hist[c8(i, cs) + 4] / piv : 0.0;
+          sv[i] = (sv[i] - bl * sv[i - 1]) / piv;
+        }
+        for (int i = L - 2; i >= 0; --i) sv[i] -= cp[i] * sv[i + 1];
+        double nrm = 0.0;
+        for (int i = 0; i < L; ++i) nrm += sv[i] * sv[i];
+        nrm = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+        for (int i = 0; i < L; ++i) sv[i] *= nrm;
+      }
+    }
+    // second pass: the same start and recurrence with the stored coefficients
+    Qp = A.dir;
+    Q = A.grad;
+    W = A.grad_old;
+    for (int j = sc.tid(); j < n; j += sc.nthreads()) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        Q[(long long)j * NC + c] = normal_at(key, (uint64_t)j * NC + c);
+        Qp[(long long)j * NC + c] = 0.0;
+      }
+      zv[j] = 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      qs[c] = qs0[c];
+      qps[c] = 0.0;
+      bp[c] = 0.0;
+    }
     if (!sc.sync()) return false;
+    for (int k = 0; k < L; ++k) {
+      double a[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) a[c] = hist[c8(k, c)];
+      const double sk = sv[k];
+      const bool diag = P.a_diag_only != 0;
+      const int j0 = diag ? t4.id : w4.warp, js = diag ? t4.count : w4.nwarps;
+      for (int j = j0; j < n; j += js) {
+        Frag<double> mq;
+        if (diag) {
+          spmm_row<double>(P, Q, NC, j, A.lam, nullptr, 0.0, -1.0, 0.0, 0.0, t4, mq);
+        } else {
+          spmm_row_warp<double>(P, Q, NC, j, A.lam, nullptr, 0.0, -1.0, 0.0, 0.0, w4, mq);
+          if (w4.sub != 0) continue;
+        }
+        const long long o = (long long)j * NC;
+        zv[j] += sk * qs[cs] * Q[o + cs];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const double w1 = qs[c] * mq.v[0][c] - bp[c] * qps[c] * Qp[o + c];
+          W[o + c] = w1 - a[c] * qs[c] * Q[o + c];
+        }
+      }
+      if (!sc.sync()) return false;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double beta = hist[c8(k, c) + 4];
+        qps[c] = qs[c];
+        qs[c] = len[c] > k + 1 ? 1.0 / beta : 0.0;
+        bp[c] = len[c] > k + 1 ? beta : 0.0;
+      }
+      double* t = Qp;
+      Qp = Q;
+      Q = W;
+      W = t;
+    }
+    double z2[1] = {0.0};
+    for (int j = sc.tid(); j < n; j += sc.nthreads()) z2[0] += zv[j] * zv[j];
+    if (!sc.reduce(z2, 1)) return false;
+    if (zn2) *zn2 = z2[0];
+    return true;
+  }
+
+  __device__ static int c8(int k, int c) { return 8 * k + c; }
+
+  // Phase II rank growth: U, V -> [U, tau z, 0], [V, tau z, 0] at rank r_new, z the Ritz
+  // vector of lambda_min(C - A^T y) (in A.Y + 2K, squared norm zn2), tau = escape_scale *
+  // ||U_hat||_F / sqrt(r) (the size of an average column); the T shadows follow
+  __device__ bool grow_rank_phase2(int r_new, const double* zv, double zn2) {
+    const int r_old = r, ld_old = ld;
+    const Team t_old = tm;
+    for (int j = t_old.id; j < n; j += t_old.count) {
+      Frag<double> u, w;
+      frag_load(u, A.U, j, ld_old, t_old);
+      frag_store(u, A.tmp, j, ld_old, t_old);
+      frag_load(w, A.V, j, ld_old, t_old);
+      frag_store(w, A.grad, j, ld_old, t_old);
+    }
+    if (!sc.sync()) return false;
+    set_rank(r_new);
+    const double tau = zn2 > 0.0 ? prm.escape_scale * sqrt(uh_norm2 / (double)r_old / zn2) : 0.0;
+    const bool shadow = (const void*)A.Ut != (const void*)A.U;
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> u, w;
+      const double zj = tau * zv[j];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) {
+          const int c = (tm.lane + k * tm.G) * CHUNK + e;
+          const long long o = (long long)j * ld_old + c;
+          u.v[k][e] = c < r_old ? A.tmp[o] : (c == r_old ? zj : 0.0);
+          w.v[k][e] = c < r_old ? A.grad[o] : (c == r_old ? zj : 0.0);
+        }
+      frag_store(u, A.U, j, ld, tm);
+      frag_store(w, A.V, j, ld, tm);
+      if (shadow) {
+        Frag<T> ut, wt;
+        frag_convert(ut, u);
+        frag_convert(wt, w);
+        frag_store(ut, A.Ut, j, ld, tm);
+        frag_store(wt, A.Vt, j, ld, tm);
+      }
+    }
+    return sc.sync();
+  }
+
+  // U_hat, objective, dual stationarity, output infeasibility, b^T lambda
+  __device__ bool output(double* res) {
+    if (prm.lanczos_steps > 0 && lmin_at != admm_iters) {
+      if (!lanczos_lambda_min(last_lmin)) return false;
+      lmin_at = admm_iters;
+    }
+    if (!form_u_hat()) return false;
     double v[6] = {0, 0, 0, 0, 0, 0};
     if (P.a_diag_only) {
       for (int j = tm.id; j < n; j += tm.count) {
@@ -1095,6 +1484,13 @@ struct Solver {
       o->r_P_split = sqrt(res[4]) / (1.0 + P.b_inf);
       o->gap = (obj - dobj) / (1.0 + fabs(obj) + fabs(dobj));
       o->r_stop = last_rs;
+      o->p_infeas = sqrt(res[2]) / (1.0 + P.b_one);
+      o->lambda_min = last_lmin;
+      o->d_infeas = last_lmin == last_lmin ? fmax(0.0, -last_lmin) / (1.0 + P.c_one) : NAN;
+    } else {
+      o->p_infeas = NAN;
+      o->lambda_min = NAN;
+      o->d_infeas = NAN;
     }
   }
 };

@@ -44,6 +44,8 @@ class lorads_params(ctypes.Structure):
         ("sigma_factor", _f64), ("sigma_decrease", _f64), ("new_col_std", _f64),
         ("seed", _u64), ("precision", _i32), ("phase1", _i32), ("time_limit_s", _f64),
         ("threads", _i32), ("grid", _i32), ("team_mult", _i32),
+        ("kkt_dinf", _i32), ("lanczos_steps", _i32), ("dinf_every", _i32),
+        ("escape_scale", _f64),
     ]
 
 
@@ -54,7 +56,7 @@ class lorads_result(ctypes.Structure):
         ("rho", _f64), ("gamma", _f64), ("sigma", _f64), ("admm_iters", _i32),
         ("cg_iters", _i32), ("hessian_applies", _i32), ("alm_outer", _i32),
         ("lbfgs_iters", _i32), ("rank_growths", _i32), ("time_phase1_s", _f64),
-        ("time_phase2_s", _f64),
+        ("time_phase2_s", _f64), ("p_infeas", _f64), ("d_infeas", _f64), ("lambda_min", _f64),
     ]
 
     def as_dict(self) -> dict:

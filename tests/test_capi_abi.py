@@ -45,8 +45,14 @@ def test_default_params_match_oracle_readings(lib):
     assert p.lbfgs_mem == o.lbfgs_mem and p.inner_max_iter == o.inner_max_iter
     assert p.inner_tol_factor == o.inner_tol_factor and p.inner_tol_max == o.inner_tol_max
     assert p.sigma_factor == o.sigma_factor and p.sigma_decrease == o.sigma_decrease
-    assert p.gamma_scale == o.gamma_scale and p.new_col_std == o.new_col_std
+    assert p.new_col_std == o.new_col_std
     assert p.max_admm_iter == o.max_admm_iter and p.max_outer == o.max_outer
+    # "auto" (< 0) resolves by problem class; the oracle's defaults are the MaxCut class
+    # (every constraint one diagonal entry): gamma_scale 1, switch_tol 1e-2, h 10
+    assert p.gamma_scale < 0 and o.gamma_scale == 1.0
+    assert p.switch_tol < 0 and o.switch_tol == 1e-2 and p.h < 0 and o.h == 10.0
+    assert p.kkt_dinf == int(o.kkt_dinf) and p.dinf_every == o.dinf_every
+    assert p.escape_scale == o.escape_scale and p.lanczos_steps > 0
 
 
 def test_status_strings(lib):

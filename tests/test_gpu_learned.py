@@ -23,7 +23,7 @@ def test_trained_start_against_bm_and_untrained(cuda):
     trained = L.lorads_gnn_create(5)
     hist = LN.train(trained, samples, epochs=15, lr=2e-3)
     assert hist[-1] < 0.5 * hist[0]
-    kw = dict(tol=1e-4)
+    kw = dict(tol=1e-6)
     rows_t = LN.evaluate(trained, held, **kw)
     rows_u = LN.evaluate(untrained, held, **kw)
     L.lorads_gnn_destroy(trained)
@@ -37,6 +37,6 @@ def test_trained_start_against_bm_and_untrained(cuda):
     it_bm = np.mean([rows_t[i]["bm_iters"] for i in ok])
     it_tr = np.mean([rows_t[i]["ln_iters"] for i in ok])
     it_un = np.mean([rows_u[i]["ln_iters"] for i in ok])
-    print(f"\nmean ADMM iterations to eq. stop <= 1e-4 on {len(ok)} held-out graphs: "
+    print(f"\nmean ADMM iterations to the final test at 1e-6 on {len(ok)} held-out graphs: "
           f"BM start {it_bm:.0f}, untrained network {it_un:.0f}, trained network {it_tr:.0f}")
     assert it_tr < it_un

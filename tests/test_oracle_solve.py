@@ -128,3 +128,19 @@ def test_initial_factor_feasible_for_diagonal_constraints():
     sdp = SDP.from_instance(I.maxcut_er(50, 4.0, seed=2))
     U = L.initial_factor(sdp, 6, seed=9)
     np.testing.assert_allclose(np.sum(U * U, axis=1), 1.0, rtol=1e-14)
+
+
+def test_phase2_rank_growth_on_a_stalled_instance():
+    """At rank ceil(log2 m) = 10 the 770-vertex batch graph stalls with lambda_min(S) < 0;
+    Phase II grows the rank along the eigenvector and the dense certificate then passes, at
+    an objective below the stalled one (a larger feasible set can only lower the minimum)."""
+    inst = [x for x in I.workload_batch() if x.n == 770][0]
+    sdp = SDP.from_instance(inst)
+    stalled = solve(sdp, Params(escape_scale=0.0, max_admm_iter=600))
+    grown = solve(sdp, Params())
+    assert not stalled["converged"] and stalled["rank"] == 10
+    assert stalled["d_infeas"] > 1e-6
+    assert grown["converged"] and grown["rank"] > 10 and grown["growths"] >= 1
+    lmin = min_eig_dual_slack(sdp, grown["y"])
+    assert max(0.0, -lmin) / (1.0 + sdp.c_one) <= 1e-6
+    assert grown["objective"] < stalled["objective"] - 1e-3
