@@ -2,7 +2,10 @@
 
 One step = one whole solve (Algorithm 2: Phase I, Phase II with CG, output and residuals)
 of the workload with its data already resident on the device, in the chosen (mixed
-FP32/FP64) form; the plain FP64 form is timed on the same workload for comparison.
+FP32/FP64) form; the plain FP64 form is timed on the same workload for comparison.  A solve
+ends when the output passes the final test at 1e-6: the paper's primal infeasibility, then
+the Appendix B gap and dual infeasibility (lambda_min(C - A^T y) by Lanczos on the device), so
+the time of a converged step is the time to KKT <= 1e-6 in those measures.
 
 Prints one JSON line (see README of the repository for the keys):
   value       solves per second over all ranks (device-resident inputs, CUDA events)
@@ -48,6 +51,10 @@ def solver_traffic():
         return SOLVER_TRAFFIC["bytes_per_launch"]
     return None
 WORKLOAD = "maxcut_torus_141x141_pm1"
+# Phase II iterations of the FP64 oracle's own full solve of this workload (default
+# parameters, final test at 1e-6; 181 s on one x86 host core): the reference arm and the CPU
+# baseline time a bounded sample and scale it to a whole solve with this count.
+ORACLE_ADMM_ITERS = {WORKLOAD: 1960}
 
 
 def parse():
@@ -129,7 +136,9 @@ class ClockSampler:
 # --------------------------------------------------------------------------------- CPU oracle
 def oracle_sample(inst, seconds, admm_iters_gpu):
     """Times the FP64 CPU oracle on a bounded sample: Phase I in full, then Phase II
-    iterations until `seconds` elapse; scales to one solve with the GPU's iteration count."""
+    iterations until `seconds` elapse; scales to one solve of `admm_iters_gpu` iterations
+    (the oracle's own count for this workload).  The final test's eigenvalue checks are not
+    in the sample (one dense/ARPACK check at the last iteration of the full solve)."""
     from oracle import SDP, Params
     import oracle.lorads as OL
     sdp = SDP.from_instance(inst)
@@ -277,15 +286,20 @@ def run_gpu(args):
         "config": {"workload": args.workload, "n": inst.n, "m": inst.m,
                    "r0": rm["rank"], "form": "mixed", "parallelism": "replicas",
                    "l2": "256 MB buffer written between timed solves"},
-        "solve": {k: rm[k] for k in ("status", "objective", "r_P", "r_P_split", "r_stop", "r_D",
-                                    "gap", "admm_iters", "cg_iters", "hessian_applies",
-                                    "alm_outer", "lbfgs_iters", "rank", "time_phase1_s",
-                                    "time_phase2_s")},
-        "kkt_reached": rm["status"] == 0,
+        "solve": {k: rm[k] for k in ("status", "objective", "dual_objective", "r_P", "r_P_split",
+                                    "r_stop", "r_D", "gap", "p_infeas", "d_infeas", "lambda_min",
+                                    "admm_iters", "cg_iters", "hessian_applies", "alm_outer",
+                                    "lbfgs_iters", "rank", "rank_growths", "gamma",
+                                    "time_phase1_s", "time_phase2_s")},
+        "kkt": {"tol": 1e-6, "reached": rm["status"] == 0,
+                "primal_r_P_binf": rm["r_P"], "appendix_b_p_infeas": rm["p_infeas"],
+                "appendix_b_d_infeas": rm["d_infeas"], "appendix_b_gap": rm["gap"]},
         "plain_fp64": {"ms_per_solve": t_fp64 * 1e3, "status": rf["status"],
                        "time_phase1_s": rf["time_phase1_s"], "time_phase2_s": rf["time_phase2_s"],
                        "objective": rf["objective"], "admm_iters": rf["admm_iters"],
-                       "cg_iters": rf["cg_iters"],
+                       "cg_iters": rf["cg_iters"], "d_infeas": rf["d_infeas"], "gap": rf["gap"],
+                       "objective_rel_diff_vs_mixed":
+                           abs(rf["objective"] - rm["objective"]) / abs(rf["objective"]),
                        "cg_operator_gbs": bytes_fp64 / t_fp64 / 1e9},
         "mixed_speedup_vs_fp64": t_fp64 / t_mixed,
         "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
@@ -304,7 +318,8 @@ def run_gpu(args):
     if not args.no_learned:
         line["learned_warm_start"] = learned_bench(args)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(inst, args.oracle_seconds, rm["admm_iters"])
+        line["cpu_baseline"] = oracle_sample(
+            inst, args.oracle_seconds, ORACLE_ADMM_ITERS.get(args.workload, rm["admm_iters"]))
     if world > 1:
         dist.destroy_process_group()
     return line
@@ -352,6 +367,7 @@ def batch_bench(args, stream):
             "solves_per_s": len(insts) / t_batch, "tuned_threads": th, "tuned_team_mult": mu,
             "converged": int(sum(r["status"] == 0 for r in res)),
             "admm_iters_total": int(sum(r["admm_iters"] for r in res)),
+            "rank_grown_in_phase2": int(sum(r["rank_growths"] > 0 for r in res)),
             "plain_fp64_sequential_s_est": t_seq_scaled,
             "speedup_vs_sequential_fp64": t_seq_scaled / t_batch,
             "sample": f"{len(sample)} one-problem FP64 solves scaled x{len(probs) / len(sample):.0f}"}
@@ -359,8 +375,9 @@ def batch_bench(args, stream):
 
 def mc_bench(args, stream):
     """Matrix completion at n = 40,000 (n1 = n2 = 20,000), rank-5 M, 15,694,167 observed
-    entries (the size of the paper's MC_40000), r0 = 24, library defaults (switch 1e-3,
-    h = 1): one solve per form after a warm-up, plus the FP32 Hessian operator at this size."""
+    entries (the size of the paper's MC_40000), r0 = 24, library defaults for non-diagonal
+    constraints (switch 1e-3, h = 1, gamma = 2 ||C||_inf): one solve per form after a warm-up,
+    plus the FP32 Hessian operator at this size."""
     import torch
     from paper_2403_09133_gb300 import instances as I
     from paper_2403_09133_gb300 import lorads as L
@@ -370,7 +387,7 @@ def mc_bench(args, stream):
     prob = L.Problem(inst)
     out = {"n": inst.n, "m": inst.m, "two_nuclear_norm": nuclear2}
     for form, prec in (("mixed", L.LORADS_PREC_MIXED), ("fp64", L.LORADS_PREC_FP64)):
-        prm = prob.params(precision=prec)    # switch_tol 1e-3, h 1 ("auto" for non-diagonal A)
+        prm = prob.params(precision=prec)    # "auto": switch_tol 1e-3, h 1, gamma 2 ||C||_inf
         L.lorads_solve(prob.handle, prm, stream)          # warm-up (assembly, first touch)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -380,7 +397,8 @@ def mc_bench(args, stream):
         e1.synchronize()
         out[form] = {"seconds": e0.elapsed_time(e1) * 1e-3, "status": r["status"],
                      "objective_rel_err_vs_2nuclear": abs(r["objective"] - nuclear2) / nuclear2,
-                     "r_P": r["r_P"], "admm_iters": r["admm_iters"], "cg_iters": r["cg_iters"],
+                     "r_P": r["r_P"], "gap": r["gap"], "d_infeas": r["d_infeas"],
+                     "admm_iters": r["admm_iters"], "cg_iters": r["cg_iters"],
                      "time_phase1_s": r["time_phase1_s"], "time_phase2_s": r["time_phase2_s"]}
     # the CG operator at this size (FP32), CUDA events, L2 flushed
     r_, ld = 24, 24
@@ -414,7 +432,7 @@ def mc_bench(args, stream):
 def learned_bench(args):
     """Learned warm start (small): 32 solver-labelled training graphs (n in [100, 300]),
     15 epochs on the GPU, then 8 held-out graphs solved from the Burer-Monteiro start and from
-    the trained network, to eq. stop <= 1e-4."""
+    the trained network, to the final test at 1e-6."""
     from paper_2403_09133_gb300 import learned as LN
     from paper_2403_09133_gb300 import lorads as L
     t0 = time.perf_counter()
@@ -422,10 +440,10 @@ def learned_bench(args):
     g = L.lorads_gnn_create(5)
     hist = LN.train(g, samples, epochs=15, lr=2e-3)
     t1 = time.perf_counter()
-    rows = LN.evaluate(g, LN.make_graphs(8, 400_000, 100, 300), tol=1e-4)
+    rows = LN.evaluate(g, LN.make_graphs(8, 400_000, 100, 300), tol=1e-6)
     L.lorads_gnn_destroy(g)
     return {"train_graphs": 32, "epochs": 15, "loss_first": hist[0], "loss_last": hist[-1],
-            "seconds_data_and_training": t1 - t0, "eval_tol": 1e-4,
+            "seconds_data_and_training": t1 - t0, "eval_tol": 1e-6,
             "eval": LN.summarize(rows)}
 
 
@@ -434,7 +452,7 @@ def run_reference(args):
     if rank != 0:
         return None
     inst = make_instance(args.workload)
-    iters = 5000
+    iters = ORACLE_ADMM_ITERS.get(args.workload, 5000)
     vals = []
     last = None
     for it in range(args.warmup + args.steps):

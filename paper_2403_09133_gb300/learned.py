@@ -149,7 +149,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--eval-tol", type=float, default=1e-4)
+    ap.add_argument("--eval-tol", type=float, default=1e-6)
     a = ap.parse_args()
     t0 = time.perf_counter()
     train_graphs = make_graphs(a.train, 100_000, a.n_lo, a.n_hi)
