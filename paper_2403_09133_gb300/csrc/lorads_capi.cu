@@ -416,7 +416,7 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   const bool mixed = sizeof(T) == 4;
   int dev_sms = 0;
   CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
-  size_t bytes = Arena::need(NS, 8) * 7 + Arena::need(NS, sizeof(T)) * (mixed ? 7 : 5) +
+  size_t bytes = Arena::need(NS, 8) * 8 + Arena::need(NS, sizeof(T)) * (mixed ? 7 : 5) +
                  Arena::need(m, 8) * 2 + Arena::need(NS * ring, 8) * 2 +
                  Arena::need(1, sizeof(SolverArgs<T>)) + Arena::need(1, sizeof(SolveOut)) +
                  Arena::need(1, sizeof(GridCtl)) +
@@ -447,6 +447,7 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   h.grad_old = a.take<double>(NS);
   h.dir = a.take<double>(NS);
   h.tmp = a.take<double>(NS);
+  h.CWn = a.take<double>(NS);
   h.S = a.take<double>(NS * ring);
   h.Y = a.take<double>(NS * ring);
   h.ld_cap = ld_cap;
@@ -1084,6 +1085,7 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   h.grad_old = a.take<double>(NS);
   h.dir = a.take<double>(NS);
   h.tmp = a.take<double>(NS);
+  h.CWn = a.take<double>(NS);
   h.S = a.take<double>(NS * ring);
   h.Y = a.take<double>(NS * ring);
   h.ld_cap = ld_cap;
@@ -1093,8 +1095,8 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   double* dpartials = a.take<double>((size_t)dev_sms * 8 * MAXRED * 3);
   int* dqueue = a.take<int>(4);
   if (!h.U || !h.V || !h.Ut || !h.Vt || !h.Dl || !h.R || !h.Pd || !h.HP || !h.Sv || !h.lam || !h.e ||
-      !h.grad || !h.grad_old || !h.dir || !h.tmp || !h.S || !h.Y || !dargs || !dout || !dctl ||
-      !dpartials || !dqueue)
+      !h.grad || !h.grad_old || !h.dir || !h.tmp || !h.CWn || !h.S || !h.Y || !dargs || !dout ||
+      !dctl || !dpartials || !dqueue)
     return LORADS_ERR_TOO_LARGE;
   h.out = dout;
   if (!dv.phase1) {

@@ -75,6 +75,7 @@ struct SolverArgs {
   double* S;      // lbfgs_mem * n * ld_cap
   double* Y;
   double* tmp;    // n * ld_cap (rank growth, U_hat)
+  double* CWn;    // n * ld_cap: -(C W) of the row-local Phase II pipeline
   // Phase II reuses grad / grad_old / dir as the three n x 4 Lanczos blocks and S as the
   // Lanczos coefficients (8 per step; S holds ring * n * ld_cap >= 8 n doubles)
   long long ld_cap;
@@ -166,11 +167,12 @@ struct Solver {
   double last_lmin;   // latest lambda_min(C - A^T y) estimate ...
   int lmin_at;        // ... and the Phase II iteration count it belongs to (-1: none)
   double uh_norm2;    // ||U_hat||_F^2 from the latest gap test
+  double rs_num, rs_den;   // ||V^{k+1} - V^k||^2, ||V^k||^2 of the row-local loop (< 0: unused)
 
   __device__ Solver(const SolverArgs<T>& a, Scope& s)
       : A(a), sc(s), P(a.P), prm(a.prm), n(a.P.n), m(a.P.m), r(0), ld(0), status(ST_OK),
         cg_iters(0), hess(0), admm_iters(0), alm_outer(0), lbfgs_iters(0), growths(0),
-        last_rs(0.0), last_lmin(NAN), lmin_at(-1), uh_norm2(0.0) {}
+        last_rs(0.0), last_lmin(NAN), lmin_at(-1), uh_norm2(0.0), rs_num(-1.0), rs_den(0.0) {}
 
   __device__ void set_rank(int rr) {
     r = rr;
@@ -762,7 +764,7 @@ struct Solver {
   // block diagonal, (H x)_j = rho a_j^2 (x_j . W_j) W_j + gamma x_j.  CG runs as the
   // Chronopoulos-Gear recurrence (one grid reduction of r.r and r.Hr per iteration; the
   // same iterates as textbook CG in exact arithmetic), each iteration one pass whose loads
-  // are independent.  The V-step's final pass also performs the dual step.
+  // are independent (phase2_local below).
   // ----------------------------------------------------------------------------------
   __device__ __forceinline__ void local_h(const Frag<T>& x, const Frag<T>& Wj, T a, T rho,
                                           T gamma, Frag<T>& out) const {
@@ -771,145 +773,6 @@ struct Solver {
     for (int k = 0; k < KMAX; ++k)
 #pragma unroll
       for (int e = 0; e < CHUNK; ++e) out.v[k][e] = fma(q, Wj.v[k][e], gamma * x.v[k][e]);
-  }
-
-  __device__ bool cg_solve_local(const double* Wm, const T* Wt, double* Xm, T* Xt, double rho,
-                                 double gamma, bool fuse_dual, double* v) {
-    const T rho_t = (T)rho, gamma_t = (T)gamma;
-    const T* ra = rowa<T>(P);
-    // warm-start residual R_0 = G - H W (FP64), w_0 = H r_0
-    double g3[3] = {0.0, 0.0, 0.0};
-    for (int j = tm.id; j < n; j += tm.count) {
-      Frag<double> Wj, mC;
-      frag_load(Wj, Wm, j, ld, tm);
-      spmm_row<double>(P, Wm, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mC);
-      Frag<double> accR = mC, accG = mC;
-      const int i = P.row_con[j];
-      if (i >= 0) {
-        const double a = P.row_a[j];
-        const double qi = a * frag_dot(Wj, Wj, tm);
-        const double w = rho * P.b[i] - A.lam[i];
-        frag_axpy(accG, a * w, Wj);
-        frag_axpy(accR, a * (w - rho * qi), Wj);
-      }
-      frag_axpy(accG, gamma, Wj);
-      Frag<T> r, Wjt, w;
-      frag_convert(r, accR);
-      frag_convert(Wjt, Wj);
-      local_h(r, Wjt, ra[j], rho_t, gamma_t, w);
-      frag_store(r, A.R, j, ld, tm);
-      frag_store(w, A.HP, j, ld, tm);
-      const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(w, r, tm);
-      const double d3 = frag_dot(accG, accG, tm);
-      if (tm.lane == 0) {
-        g3[0] += d1;
-        g3[1] += d2;
-        g3[2] += d3;
-      }
-    }
-    if (!sc.reduce(g3, 3)) return false;
-    ++hess;
-    double gam = g3[0], del = g3[1];
-    const double target = fmax(prm.cg_rel_tol * sqrt(gam), prm.cg_abs_floor * sqrt(g3[2]));
-    double alpha = del > 0.0 ? gam / del : 0.0, beta = 0.0;
-    int it = 0;
-    while (sqrt(gam) > target && it < prm.cg_max_iter && del > 0.0) {
-      const T a_t = (T)alpha, b_t = (T)beta;
-      double z[2] = {0.0, 0.0};
-      for (int j = tm.id; j < n; j += tm.count) {
-        Frag<T> r, w, pp, ss, x, Wjt;
-        frag_load(r, A.R, j, ld, tm);
-        frag_load(w, A.HP, j, ld, tm);
-        frag_load(Wjt, Wt, j, ld, tm);
-        if (it > 0) {
-          frag_load(pp, A.Pd, j, ld, tm);
-          frag_load(ss, A.Sv, j, ld, tm);
-          frag_load(x, A.Dl, j, ld, tm);
-        } else {
-          frag_zero(pp);
-          frag_zero(ss);
-          frag_zero(x);
-        }
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-#pragma unroll
-          for (int e = 0; e < CHUNK; ++e) {
-            pp.v[k][e] = fma(b_t, pp.v[k][e], r.v[k][e]);
-            ss.v[k][e] = fma(b_t, ss.v[k][e], w.v[k][e]);
-            x.v[k][e] = fma(a_t, pp.v[k][e], x.v[k][e]);
-            r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
-          }
-        local_h(r, Wjt, ra[j], rho_t, gamma_t, w);
-        frag_store(pp, A.Pd, j, ld, tm);
-        frag_store(ss, A.Sv, j, ld, tm);
-        frag_store(x, A.Dl, j, ld, tm);
-        frag_store(r, A.R, j, ld, tm);
-        frag_store(w, A.HP, j, ld, tm);
-        const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(w, r, tm);
-        if (tm.lane == 0) {
-          z[0] += d1;
-          z[1] += d2;
-        }
-      }
-      if (!sc.reduce(z, 2)) return false;
-      ++hess;
-      ++it;
-      const double gam_new = z[0], del_new = z[1];
-      if (!(gam_new == gam_new) || !(del_new == del_new)) {
-        status = ST_NAN;
-        break;
-      }
-      if (sqrt(gam_new) <= target) break;
-      beta = gam_new / gam;
-      const double denom = del_new - beta * gam_new / alpha;
-      gam = gam_new;
-      del = denom;                 // loop ends if rounding made it non-positive
-      alpha = denom > 0.0 ? gam_new / denom : 0.0;
-    }
-    cg_iters += it;
-    // X = W + x; in the V-step also the dual step lambda += rho (A(U V^T) - b)
-    for (int j = tm.id; j < n; j += tm.count) {
-      Frag<double> Wj, Xj;
-      frag_load(Wj, Wm, j, ld, tm);
-      if (it > 0) {
-        Frag<T> x;
-        frag_load(x, A.Dl, j, ld, tm);
-        frag_convert(Xj, x);
-        frag_axpy(Xj, 1.0, Wj);
-      } else {
-        Xj = Wj;
-      }
-      if (fuse_dual) {
-        Frag<double> Xo;
-        frag_load(Xo, Xm, j, ld, tm);
-        const double o2 = frag_dot(Xo, Xo, tm);
-        frag_axpy(Xo, -1.0, Xj);
-        const double d2 = frag_dot(Xo, Xo, tm);
-        const int i = P.row_con[j];
-        double e = 0.0, eh = 0.0;
-        if (i >= 0) {
-          const double a = P.row_a[j];
-          Frag<double> H = Wj;
-          frag_axpy(H, 1.0, Xj);
-          e = a * frag_dot(Wj, Xj, tm) - P.b[i];
-          eh = 0.25 * a * frag_dot(H, H, tm) - P.b[i];
-        }
-        if (tm.lane == 0) {
-          if (i >= 0) A.lam[i] += rho * e;
-          v[0] += e * e;
-          v[1] += eh * eh;
-          v[2] += d2;
-          v[3] += o2;
-        }
-      }
-      frag_store(Xj, Xm, j, ld, tm);
-      if ((const void*)Xt != (const void*)Xm) {
-        Frag<T> Xs;
-        frag_convert(Xs, Xj);
-        frag_store(Xs, Xt, j, ld, tm);
-      }
-    }
-    return fuse_dual ? true : sc.sync();
   }
 
   // dual step lambda += rho (A(U V^T) - b); partial sums of ||e||^2 and of the output
@@ -943,31 +806,56 @@ struct Solver {
     }
   }
 
+  // Final test on X = U_hat U_hat^T, y = -lambda^{k+1} once the primal test has passed:
+  // the Appendix B gap, then the Appendix B dual infeasibility (rate-limited); a dual
+  // infeasibility that fell by less than 10% since the previous failed test (a stationary
+  // point of the rank-r problem) grows the rank along the eigenvector of lambda_min.
+  // Returns 1 (done), 0 (continue), 2 (rank grown: U, V changed), -1 (device error).
+  __device__ int final_test(int& next_dual_test, double& prev_dinf) {
+    double gap;
+    if (!gap_check(gap)) return -1;
+    if (!(fabs(gap) <= prm.tol)) return 0;
+    if (!prm.kkt_dinf) return 1;
+    if (admm_iters < next_dual_test) return 0;
+    if (!lanczos_lambda_min(last_lmin)) return -1;
+    lmin_at = admm_iters;
+    const double dinf = fmax(0.0, -last_lmin) / (1.0 + P.c_one);
+    if (dinf <= prm.tol) return 1;
+    next_dual_test = admm_iters + max(prm.dinf_every, admm_iters / 10);
+    if (prev_dinf == prev_dinf && dinf > 0.9 * prev_dinf && prm.escape_scale > 0.0 &&
+        r < prm.rank_cap) {
+      double zn2 = 0.0, lm;
+      if (!lanczos_lambda_min(lm, true, &zn2)) return -1;
+      const int K = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
+      int r_new = (int)ceil(prm.rank_factor * r - 1e-9);
+      if (r_new <= r) r_new = r + 1;
+      if (r_new > prm.rank_cap) r_new = prm.rank_cap;
+      if (!grow_rank_phase2(r_new, A.Y + 2 * K, zn2)) return -1;
+      ++growths;
+      prev_dinf = NAN;
+      return 2;
+    }
+    prev_dinf = dinf;
+    return 0;
+  }
+
   __device__ bool phase2(double rho, double& rho_out) {
+    if (P.a_diag_only) return phase2_local(rho, rho_out);
     const double gamma = prm.gamma;
-    const bool local = P.a_diag_only != 0;
     int next_dual_test = 0;
     double prev_dinf = NAN;
     for (int k = 0; k < prm.max_admm_iter; ++k) {
       double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      if (local) {
-        // U-step (eq. linU, W = V^k) and V-step (eq. linV, W = U^{k+1}) with the dual step
-        if (!cg_solve_local(A.V, A.Vt, A.U, A.Ut, rho, gamma, false, v)) return false;
-        if (status != ST_OK) break;
-        if (!cg_solve_local(A.U, A.Ut, A.V, A.Vt, rho, gamma, true, v)) return false;
-        if (status != ST_OK) break;
-      } else {
-        double dv[2];
-        // U-step: eq. linU with W = V^k, CG warm-started from V^k
-        if (!cg_solve(A.V, A.Vt, A.U, A.Ut, rho, gamma, false, dv)) return false;
-        if (status != ST_OK) break;
-        // V-step: eq. linV with W = U^{k+1}, CG warm-started from U^{k+1}
-        if (!cg_solve(A.U, A.Ut, A.V, A.Vt, rho, gamma, true, dv)) return false;
-        if (status != ST_OK) break;
-        dual_step(rho, v);
-        v[2] = dv[0];
-        v[3] = dv[1];
-      }
+      double dv[2];
+      // U-step: eq. linU with W = V^k, CG warm-started from V^k
+      if (!cg_solve(A.V, A.Vt, A.U, A.Ut, rho, gamma, false, dv)) return false;
+      if (status != ST_OK) break;
+      // V-step: eq. linV with W = U^{k+1}, CG warm-started from U^{k+1}
+      if (!cg_solve(A.U, A.Ut, A.V, A.Vt, rho, gamma, true, dv)) return false;
+      if (status != ST_OK) break;
+      dual_step(rho, v);
+      v[2] = dv[0];
+      v[3] = dv[1];
       if (sc.is_leader()) v[4] = (double)(globaltimer_ns() - t_start);
       if (!sc.reduce(v, 5)) return false;
       admm_iters = k + 1;
@@ -976,47 +864,338 @@ struct Solver {
       const double rs = gamma * sqrt(v[2]) / (1.0 + sqrt(v[3]));
       last_rs = rs;
       if (!(rp == rp) || !(rs == rs)) { status = ST_NAN; break; }
-      // final test on X = U_hat U_hat^T, y = -lambda^{k+1}: the paper's primal test, then
-      // the Appendix B gap, then the Appendix B dual infeasibility (rate-limited)
       if (rph <= prm.tol) {
-        double gap;
-        if (!gap_check(gap)) return false;
-        if (fabs(gap) <= prm.tol) {
-          bool done = !prm.kkt_dinf;
-          if (!done && admm_iters >= next_dual_test) {
-            if (!lanczos_lambda_min(last_lmin)) return false;
-            lmin_at = admm_iters;
-            const double dinf = fmax(0.0, -last_lmin) / (1.0 + P.c_one);
-            done = dinf <= prm.tol;
-            if (!done) {
-              next_dual_test = admm_iters + max(prm.dinf_every, admm_iters / 10);
-              // a dual infeasibility that fell by less than 10% since the previous test (a
-              // stationary point of the rank-r problem): grow the rank along the eigenvector
-              // of lambda_min
-              if (prev_dinf == prev_dinf && dinf > 0.9 * prev_dinf && prm.escape_scale > 0.0 &&
-                  r < prm.rank_cap) {
-                double zn2 = 0.0, lm;
-                if (!lanczos_lambda_min(lm, true, &zn2)) return false;
-                const int K = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
-                int r_new = (int)ceil(prm.rank_factor * r - 1e-9);
-                if (r_new <= r) r_new = r + 1;
-                if (r_new > prm.rank_cap) r_new = prm.rank_cap;
-                if (!grow_rank_phase2(r_new, A.Y + 2 * K, zn2)) return false;
-                ++growths;
-                prev_dinf = NAN;
-              } else {
-                prev_dinf = dinf;
-              }
-            }
-          }
-          if (done) {
-            rho_out = rho;
-            return true;
-          }
+        const int t = final_test(next_dual_test, prev_dinf);
+        if (t < 0) return false;
+        if (t == 1) {
+          rho_out = rho;
+          return true;
         }
       }
       if ((long long)v[4] > prm.time_limit_ns) { status = ST_TIMEOUT; break; }
       if ((k + 1) % prm.rho_every == 0) rho = fmin(rho * prm.rho_growth, prm.rho_max);
+    }
+    if (status == ST_OK) status = ST_MAXITER;
+    rho_out = rho;
+    return true;
+  }
+
+  // ----------------------------------------------------------------------------------
+  // Phase II, row-local form (every constraint a diagonal entry): the subproblems' Hessians
+  // are block diagonal, so a CG solve needs no neighbour data; only the warm-start residual
+  // R_0 = G - H W reads neighbours, through (C W)_j.  The loop is pipelined: -(C W) is kept
+  // per row in FP64 (A.CWn) and advanced with -(C delta) of each CG correction (in T, read
+  // from the neighbours' delta after the CG's last barrier), recomputed exactly in FP64 every
+  // 32 iterations; so the pass that forms X = W + delta also forms the next subproblem's R_0
+  // (U-step finish + V-step R_0; V-step finish + dual step + next U-step R_0), one grid
+  // reduction each.  Same iterates as the unpipelined form up to rounding.
+  // ----------------------------------------------------------------------------------
+  // R_0 and w_0 = H r_0 of the local subproblem with fixed factor W on row j, given
+  // mCWj = -(C W)_j:  R_0j = -(C W)_j + a (rho b_i - lambda_i - rho q_i) W_j, q_i = a W_j.W_j;
+  // ||G||^2 with G_j = R_0j + (a rho q_i + gamma) W_j (only its norm is used) in T
+  // (lam_i: lambda of row j's constraint, when it has one)
+  __device__ __forceinline__ void local_r0_row(int j, const Frag<double>& Wj, const Frag<T>& Wjt,
+                                               const Frag<double>& mCWj, double lam_i, double rho,
+                                               double gamma, double* g3) {
+    Frag<double> accR = mCWj;
+    double cg = gamma;
+    const int i = P.row_con[j];
+    if (i >= 0) {
+      const double a = P.row_a[j];
+      const double qi = a * frag_dot(Wj, Wj, tm);
+      frag_axpy(accR, a * (rho * P.b[i] - lam_i - rho * qi), Wj);
+      cg += a * rho * qi;
+    }
+    Frag<T> rt, wt, gt;
+    frag_convert(rt, accR);
+    local_h(rt, Wjt, rowa<T>(P)[j], (T)rho, (T)gamma, wt);
+    frag_store(rt, A.R, j, ld, tm);
+    frag_store(wt, A.HP, j, ld, tm);
+    gt = rt;
+    frag_axpy(gt, (T)cg, Wjt);
+    const double d1 = (double)frag_dot(rt, rt, tm), d2 = (double)frag_dot(wt, rt, tm);
+    const double d3 = (double)frag_dot(gt, gt, tm);
+    if (tm.lane == 0) {
+      g3[0] += d1;
+      g3[1] += d2;
+      g3[2] += d3;
+    }
+  }
+
+  // -(C X)_j for X = W + delta (delta = A.Dl when have_delta): exact FP64 sum over the
+  // neighbours' W and delta when exact, else mCWj - (C delta)_j with the product in T
+  __device__ __forceinline__ void local_mcx_row(int j, const double* Wm, bool have_delta,
+                                                bool exact, const Frag<double>& mCWj,
+                                                Frag<double>& out) {
+    if (exact) {
+      Frag<double> acc;
+      frag_zero(acc);
+      for (int q = P.C_rp[j]; q < P.C_rp[j + 1]; ++q) {
+        const int k = P.C_col[q];
+        Frag<double> Wk;
+        frag_load(Wk, Wm, k, ld, tm);
+        if (have_delta) {
+          Frag<T> dk;
+          Frag<double> dd;
+          frag_load(dk, A.Dl, k, ld, tm);
+          frag_convert(dd, dk);
+          frag_axpy(Wk, 1.0, dd);
+        }
+        frag_axpy(acc, -P.C_val[q], Wk);
+      }
+      out = acc;
+      return;
+    }
+    out = mCWj;
+    if (!have_delta) return;
+    Frag<T> mcd;
+    spmm_row<T>(P, A.Dl, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, T(0), tm, mcd);
+    Frag<double> md;
+    frag_convert(md, mcd);
+    frag_axpy(out, 1.0, md);
+  }
+
+  // the U-step's R_0 from W = V with -(C V) computed exactly (start, and after rank growth)
+  __device__ bool local_prologue(double rho, double gamma, double* g3) {
+    g3[0] = g3[1] = g3[2] = 0.0;
+    const bool shadow = (const void*)A.Vt != (const void*)A.V;
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Wj, mCW;
+      Frag<T> Wjt;
+      frag_load(Wj, A.V, j, ld, tm);
+      if (shadow) frag_load(Wjt, A.Vt, j, ld, tm);
+      else frag_convert(Wjt, Wj);
+      local_mcx_row(j, A.V, false, true, Wj, mCW);
+      frag_store(mCW, A.CWn, j, ld, tm);
+      const int i = P.row_con[j];
+      local_r0_row(j, Wj, Wjt, mCW, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3);
+    }
+    if (!sc.reduce(g3, 3)) return false;
+    ++hess;
+    return true;
+  }
+
+  // CG-CG iterations on H delta = r_0 from the R / HP left by the R_0 pass (row-local H).
+  // The FP64 scalar recurrence after each reduction is evaluated by lane 0 of every warp and
+  // shared by shuffles (every warp computes the same values from the same reduced sums), and
+  // the stop test compares squares: FP64 divides and square roots are slow on this part and
+  // would otherwise run in every thread.
+  __device__ bool cg_local_loop(const T* Wt, double rho, double gamma, const double* g3,
+                                int& it) {
+    const T rho_t = (T)rho, gamma_t = (T)gamma;
+    const T* ra = rowa<T>(P);
+    const unsigned full = 0xffffffffu;
+    const bool lead = (threadIdx.x & 31) == 0;
+    double gam = 0.0, del = 0.0, alpha = 0.0, beta = 0.0, target2 = 0.0;
+    int go = 0;
+    T a_t = T(0), b_t = T(0);
+    if (lead) {
+      gam = g3[0];
+      del = g3[1];
+      target2 = fmax(prm.cg_rel_tol * prm.cg_rel_tol * gam,
+                     prm.cg_abs_floor * prm.cg_abs_floor * g3[2]);
+      alpha = del > 0.0 ? gam / del : 0.0;
+      go = (gam > target2 && del > 0.0) ? 1 : 0;
+      a_t = (T)alpha;
+    }
+    go = __shfl_sync(full, go, 0);
+    a_t = __shfl_sync(full, a_t, 0);
+    it = 0;
+    while (go && it < prm.cg_max_iter) {
+      double z[2] = {0.0, 0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<T> r, w, pp, ss, x, Wjt;
+        frag_load(r, A.R, j, ld, tm);
+        frag_load(w, A.HP, j, ld, tm);
+        frag_load(Wjt, Wt, j, ld, tm);
+        if (it > 0) {
+          frag_load(pp, A.Pd, j, ld, tm);
+          frag_load(ss, A.Sv, j, ld, tm);
+          frag_load(x, A.Dl, j, ld, tm);
+        } else {
+          frag_zero(pp);
+          frag_zero(ss);
+          frag_zero(x);
+        }
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+          for (int e = 0; e < CHUNK; ++e) {
+            pp.v[k][e] = fma(b_t, pp.v[k][e], r.v[k][e]);
+            ss.v[k][e] = fma(b_t, ss.v[k][e], w.v[k][e]);
+            x.v[k][e] = fma(a_t, pp.v[k][e], x.v[k][e]);
+            r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
+          }
+        local_h(r, Wjt, ra[j], rho_t, gamma_t, w);
+        frag_store(pp, A.Pd, j, ld, tm);
+        frag_store(ss, A.Sv, j, ld, tm);
+        frag_store(x, A.Dl, j, ld, tm);
+        frag_store(r, A.R, j, ld, tm);
+        frag_store(w, A.HP, j, ld, tm);
+        const T d1 = frag_dot(r, r, tm), d2 = frag_dot(w, r, tm);
+        if (tm.lane == 0) {
+          z[0] += (double)d1;
+          z[1] += (double)d2;
+        }
+      }
+      if (!sc.reduce(z, 2)) return false;
+      ++hess;
+      ++it;
+      int state = 0;                 // 0: go on, 1: stop, 2: NaN
+      if (lead) {
+        const double gam_new = z[0], del_new = z[1];
+        if (!(gam_new == gam_new) || !(del_new == del_new)) {
+          state = 2;
+        } else if (gam_new <= target2) {
+          state = 1;
+        } else {
+          beta = gam_new / gam;
+          const double denom = del_new - beta * gam_new / alpha;
+          gam = gam_new;
+          del = denom;
+          alpha = denom > 0.0 ? gam_new / denom : 0.0;
+          state = denom > 0.0 ? 0 : 1;     // stop if rounding made it non-positive
+          a_t = (T)alpha;
+          b_t = (T)beta;
+        }
+      }
+      state = __shfl_sync(full, state, 0);
+      if (state == 2) {
+        status = ST_NAN;
+        break;
+      }
+      if (state == 1) break;
+      a_t = __shfl_sync(full, a_t, 0);
+      b_t = __shfl_sync(full, b_t, 0);
+    }
+    cg_iters += it;
+    return true;
+  }
+
+  __device__ bool phase2_local(double rho, double& rho_out) {
+    const double gamma = prm.gamma;
+    const double tol2_primal = prm.tol * (1.0 + P.b_inf) * prm.tol * (1.0 + P.b_inf);
+    const bool shadow = (const void*)A.Ut != (const void*)A.U;
+    int next_dual_test = 0;
+    double prev_dinf = NAN;
+    double g3[3];
+    if (!local_prologue(rho, gamma, g3)) return false;
+    for (int k = 0; k < prm.max_admm_iter; ++k) {
+      const bool exact = (k + 1) % 32 == 0;
+      // U-step: CG on eq. linU (W = V^k) from the R_0 of the previous pass
+      int it;
+      if (!cg_local_loop(A.Vt, rho, gamma, g3, it)) return false;
+      if (status != ST_OK) break;
+      // U^{k+1} = V^k + delta, -(C U^{k+1}), and the V-step's R_0 (W = U^{k+1})
+      g3[0] = g3[1] = g3[2] = 0.0;
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> Wj, Xj, mCW, mCX;
+        frag_load(Wj, A.V, j, ld, tm);
+        frag_load(mCW, A.CWn, j, ld, tm);
+        Xj = Wj;
+        if (it > 0) {
+          Frag<T> x;
+          Frag<double> xd;
+          frag_load(x, A.Dl, j, ld, tm);
+          frag_convert(xd, x);
+          frag_axpy(Xj, 1.0, xd);
+        }
+        local_mcx_row(j, A.V, it > 0, exact, mCW, mCX);
+        Frag<T> Xt;
+        frag_convert(Xt, Xj);
+        frag_store(Xj, A.U, j, ld, tm);
+        if (shadow) frag_store(Xt, A.Ut, j, ld, tm);
+        frag_store(mCX, A.CWn, j, ld, tm);
+        const int i = P.row_con[j];
+        local_r0_row(j, Xj, Xt, mCX, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3);
+      }
+      if (!sc.reduce(g3, 3)) return false;
+      ++hess;
+      // V-step: CG on eq. linV (W = U^{k+1})
+      if (!cg_local_loop(A.Ut, rho, gamma, g3, it)) return false;
+      if (status != ST_OK) break;
+      // V^{k+1} = U^{k+1} + delta, the dual step, -(C V^{k+1}) and the next U-step's R_0
+      const double rho_next =
+          ((k + 1) % prm.rho_every == 0) ? fmin(rho * prm.rho_growth, prm.rho_max) : rho;
+      double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> Wj, Xj, Vo, mCW, mCX;
+        Frag<T> x, Vot;
+        frag_load(Wj, A.U, j, ld, tm);
+        frag_load(Vo, A.V, j, ld, tm);
+        frag_load(mCW, A.CWn, j, ld, tm);
+        Xj = Wj;
+        if (it > 0) {
+          Frag<double> xd;
+          frag_load(x, A.Dl, j, ld, tm);
+          frag_convert(xd, x);
+          frag_axpy(Xj, 1.0, xd);
+        } else {
+          frag_zero(x);
+        }
+        // eq. stop's second term (reported): ||V^{k+1} - V^k||, ||V^k|| in T
+        Frag<double> dW = Wj;
+        frag_axpy(dW, -1.0, Vo);
+        Frag<T> dV;
+        frag_convert(dV, dW);
+        frag_axpy(dV, T(1), x);
+        frag_convert(Vot, Vo);
+        const double d2 = (double)frag_dot(dV, dV, tm), o2 = (double)frag_dot(Vot, Vot, tm);
+        // dual step lambda_i += rho (a U_j.V_j - b_i) and the output's row residual
+        const int i = P.row_con[j];
+        double e = 0.0, eh = 0.0, lam_new = 0.0;
+        if (i >= 0) {
+          const double a = P.row_a[j];
+          Frag<double> H = Wj;
+          frag_axpy(H, 1.0, Xj);
+          e = a * frag_dot(Wj, Xj, tm) - P.b[i];
+          eh = 0.25 * a * frag_dot(H, H, tm) - P.b[i];
+          lam_new = A.lam[i] + rho * e;     // every lane of the team holds the same value
+        }
+        if (tm.lane == 0) {
+          if (i >= 0) A.lam[i] = lam_new;
+          v[0] += e * e;
+          v[1] += eh * eh;
+          v[2] += d2;
+          v[3] += o2;
+        }
+        local_mcx_row(j, A.U, it > 0, exact, mCW, mCX);
+        Frag<T> Xt;
+        frag_convert(Xt, Xj);
+        frag_store(Xj, A.V, j, ld, tm);
+        if (shadow) frag_store(Xt, A.Vt, j, ld, tm);
+        frag_store(mCX, A.CWn, j, ld, tm);
+        local_r0_row(j, Xj, Xt, mCX, lam_new, rho_next, gamma, v + 5);
+      }
+      if (sc.is_leader()) v[4] = (double)(globaltimer_ns() - t_start);
+      if (!sc.reduce(v, 8)) return false;
+      ++hess;
+      g3[0] = v[5];
+      g3[1] = v[6];
+      g3[2] = v[7];
+      admm_iters = k + 1;
+      // squared forms of the tests (no per-thread square roots); eq. stop's second term is
+      // formed once, when the result is written
+      rs_num = v[2];
+      rs_den = v[3];
+      if (!(v[0] == v[0]) || !(v[2] == v[2])) { status = ST_NAN; break; }
+      if (v[1] <= tol2_primal) {
+        const int t = final_test(next_dual_test, prev_dinf);
+        if (t < 0) return false;
+        if (t == 1) {
+          rho_out = rho;
+          return true;
+        }
+        if (t == 2) {
+          // U, V and the rank changed: the pipelined R_0 is stale
+          if ((long long)v[4] > prm.time_limit_ns) { status = ST_TIMEOUT; break; }
+          rho = rho_next;
+          if (!local_prologue(rho, gamma, g3)) return false;
+          continue;
+        }
+      }
+      if ((long long)v[4] > prm.time_limit_ns) { status = ST_TIMEOUT; break; }
+      rho = rho_next;
     }
     if (status == ST_OK) status = ST_MAXITER;
     rho_out = rho;
@@ -1483,7 +1662,7 @@ struct Solver {
       o->r_P = sqrt(res[2]) / (1.0 + P.b_inf);
       o->r_P_split = sqrt(res[4]) / (1.0 + P.b_inf);
       o->gap = (obj - dobj) / (1.0 + fabs(obj) + fabs(dobj));
-      o->r_stop = last_rs;
+      o->r_stop = rs_num >= 0.0 ? prm.gamma * sqrt(rs_num) / (1.0 + sqrt(rs_den)) : last_rs;
       o->p_infeas = sqrt(res[2]) / (1.0 + P.b_one);
       o->lambda_min = last_lmin;
       o->d_infeas = last_lmin == last_lmin ? fmax(0.0, -last_lmin) / (1.0 + P.c_one) : NAN;
