@@ -888,21 +888,24 @@ struct Solver {
   // from the neighbours' delta after the CG's last barrier), recomputed exactly in FP64 every
   // 32 iterations; so the pass that forms X = W + delta also forms the next subproblem's R_0
   // (U-step finish + V-step R_0; V-step finish + dual step + next U-step R_0), one grid
-  // reduction each.  Same iterates as the unpipelined form up to rounding.
+  // reduction each.  The T shadows of U^{k+1} and V^{k+1} are advanced as shadow(W) + delta
+  // and re-rounded from the FP64 masters at the same exact steps.  Same iterates as the
+  // unpipelined form up to rounding.
   // ----------------------------------------------------------------------------------
   // R_0 and w_0 = H r_0 of the local subproblem with fixed factor W on row j, given
   // mCWj = -(C W)_j:  R_0j = -(C W)_j + a (rho b_i - lambda_i - rho q_i) W_j, q_i = a W_j.W_j;
   // ||G||^2 with G_j = R_0j + (a rho q_i + gamma) W_j (only its norm is used) in T
   // (lam_i: lambda of row j's constraint, when it has one)
-  __device__ __forceinline__ void local_r0_row(int j, const Frag<double>& Wj, const Frag<T>& Wjt,
-                                               const Frag<double>& mCWj, double lam_i, double rho,
-                                               double gamma, double* g3) {
+  // Returns q_i = a ||W_j||^2 (0 without a constraint).
+  __device__ __forceinline__ double local_r0_row(int j, const Frag<double>& Wj, const Frag<T>& Wjt,
+                                                 const Frag<double>& mCWj, double lam_i, double rho,
+                                                 double gamma, double* g3) {
     Frag<double> accR = mCWj;
-    double cg = gamma;
+    double cg = gamma, qi = 0.0;
     const int i = P.row_con[j];
     if (i >= 0) {
       const double a = P.row_a[j];
-      const double qi = a * frag_dot(Wj, Wj, tm);
+      qi = a * frag_dot(Wj, Wj, tm);
       frag_axpy(accR, a * (rho * P.b[i] - lam_i - rho * qi), Wj);
       cg += a * rho * qi;
     }
@@ -920,6 +923,7 @@ struct Solver {
       g3[1] += d2;
       g3[2] += d3;
     }
+    return qi;
   }
 
   // -(C X)_j for X = W + delta (delta = A.Dl when have_delta): exact FP64 sum over the
@@ -1090,8 +1094,10 @@ struct Solver {
       g3[0] = g3[1] = g3[2] = 0.0;
       for (int j = tm.id; j < n; j += tm.count) {
         Frag<double> Wj, Xj, mCW, mCX;
+        Frag<T> Xt;
         frag_load(Wj, A.V, j, ld, tm);
         frag_load(mCW, A.CWn, j, ld, tm);
+        frag_load(Xt, A.Vt, j, ld, tm);           // (the master itself in the FP64 form)
         Xj = Wj;
         if (it > 0) {
           Frag<T> x;
@@ -1099,15 +1105,16 @@ struct Solver {
           frag_load(x, A.Dl, j, ld, tm);
           frag_convert(xd, x);
           frag_axpy(Xj, 1.0, xd);
+          frag_axpy(Xt, T(1), x);                 // shadow of U^{k+1} = shadow(V^k) + delta
         }
+        if (exact) frag_convert(Xt, Xj);          // re-rounded from the master every 32
         local_mcx_row(j, A.V, it > 0, exact, mCW, mCX);
-        Frag<T> Xt;
-        frag_convert(Xt, Xj);
         frag_store(Xj, A.U, j, ld, tm);
         if (shadow) frag_store(Xt, A.Ut, j, ld, tm);
         frag_store(mCX, A.CWn, j, ld, tm);
         const int i = P.row_con[j];
-        local_r0_row(j, Xj, Xt, mCX, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3);
+        const double qU = local_r0_row(j, Xj, Xt, mCX, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3);
+        if (i >= 0 && tm.lane == 0) A.e[i] = qU;  // a ||U_j^{k+1}||^2 for the output residual
       }
       if (!sc.reduce(g3, 3)) return false;
       ++hess;
@@ -1119,11 +1126,12 @@ struct Solver {
           ((k + 1) % prm.rho_every == 0) ? fmin(rho * prm.rho_growth, prm.rho_max) : rho;
       double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       for (int j = tm.id; j < n; j += tm.count) {
-        Frag<double> Wj, Xj, Vo, mCW, mCX;
-        Frag<T> x, Vot;
+        Frag<double> Wj, Xj, mCW, mCX;
+        Frag<T> x, Wt, Vot;
         frag_load(Wj, A.U, j, ld, tm);
-        frag_load(Vo, A.V, j, ld, tm);
         frag_load(mCW, A.CWn, j, ld, tm);
+        frag_load(Wt, A.Ut, j, ld, tm);           // (the masters themselves in the FP64 form)
+        frag_load(Vot, A.Vt, j, ld, tm);
         Xj = Wj;
         if (it > 0) {
           Frag<double> xd;
@@ -1133,25 +1141,29 @@ struct Solver {
         } else {
           frag_zero(x);
         }
-        // eq. stop's second term (reported): ||V^{k+1} - V^k||, ||V^k|| in T
-        Frag<double> dW = Wj;
-        frag_axpy(dW, -1.0, Vo);
-        Frag<T> dV;
-        frag_convert(dV, dW);
+        // eq. stop's second term (reported only): ||V^{k+1} - V^k||, ||V^k|| from the shadows
+        Frag<T> Xt = Wt, dV = Wt;
+        frag_axpy(Xt, T(1), x);                   // shadow of V^{k+1} = shadow(U^{k+1}) + delta
+        frag_axpy(dV, T(-1), Vot);
         frag_axpy(dV, T(1), x);
-        frag_convert(Vot, Vo);
         const double d2 = (double)frag_dot(dV, dV, tm), o2 = (double)frag_dot(Vot, Vot, tm);
-        // dual step lambda_i += rho (a U_j.V_j - b_i) and the output's row residual
+        if (exact) frag_convert(Xt, Xj);          // re-rounded from the master every 32
+        // dual step lambda_i += rho (a U_j.V_j - b_i)
         const int i = P.row_con[j];
-        double e = 0.0, eh = 0.0, lam_new = 0.0;
+        double e = 0.0, lam_new = 0.0;
         if (i >= 0) {
-          const double a = P.row_a[j];
-          Frag<double> H = Wj;
-          frag_axpy(H, 1.0, Xj);
-          e = a * frag_dot(Wj, Xj, tm) - P.b[i];
-          eh = 0.25 * a * frag_dot(H, H, tm) - P.b[i];
+          e = P.row_a[j] * frag_dot(Wj, Xj, tm) - P.b[i];
           lam_new = A.lam[i] + rho * e;     // every lane of the team holds the same value
         }
+        local_mcx_row(j, A.U, it > 0, exact, mCW, mCX);
+        frag_store(Xj, A.V, j, ld, tm);
+        if (shadow) frag_store(Xt, A.Vt, j, ld, tm);
+        frag_store(mCX, A.CWn, j, ld, tm);
+        const double qV = local_r0_row(j, Xj, Xt, mCX, lam_new, rho_next, gamma, v + 5);
+        // the output's row residual a ||(U_j + V_j)/2||^2 - b_i from a||U_j||^2 (pass A),
+        // a U_j.V_j = e + b_i and a||V_j||^2
+        double eh = 0.0;
+        if (i >= 0) eh = 0.25 * (A.e[i] + 2.0 * (e + P.b[i]) + qV) - P.b[i];
         if (tm.lane == 0) {
           if (i >= 0) A.lam[i] = lam_new;
           v[0] += e * e;
@@ -1159,13 +1171,6 @@ struct Solver {
           v[2] += d2;
           v[3] += o2;
         }
-        local_mcx_row(j, A.U, it > 0, exact, mCW, mCX);
-        Frag<T> Xt;
-        frag_convert(Xt, Xj);
-        frag_store(Xj, A.V, j, ld, tm);
-        if (shadow) frag_store(Xt, A.Vt, j, ld, tm);
-        frag_store(mCX, A.CWn, j, ld, tm);
-        local_r0_row(j, Xj, Xt, mCX, lam_new, rho_next, gamma, v + 5);
       }
       if (sc.is_leader()) v[4] = (double)(globaltimer_ns() - t_start);
       if (!sc.reduce(v, 8)) return false;
