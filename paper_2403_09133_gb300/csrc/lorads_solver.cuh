@@ -980,30 +980,32 @@ struct Solver {
   }
 
   // CG-CG iterations on H delta = r_0 from the R / HP left by the R_0 pass (row-local H).
-  // The FP64 scalar recurrence after each reduction is evaluated by lane 0 of every warp and
-  // shared by shuffles (every warp computes the same values from the same reduced sums), and
-  // the stop test compares squares: FP64 divides and square roots are slow on this part and
-  // would otherwise run in every thread.
+  // The FP64 scalar recurrence after each reduction is evaluated by thread 0 of every CTA
+  // and shared through shared memory (every CTA computes the same values from the same
+  // reduced sums), and the stop test compares squares: FP64 divides issue at a small
+  // fraction of the FP32 rate on this part, and evaluated in every warp they would queue on
+  // each SM's FP64 unit.
   __device__ bool cg_local_loop(const T* Wt, double rho, double gamma, const double* g3,
                                 int& it) {
     const T rho_t = (T)rho, gamma_t = (T)gamma;
     const T* ra = rowa<T>(P);
-    const unsigned full = 0xffffffffu;
-    const bool lead = (threadIdx.x & 31) == 0;
+    const bool lead = threadIdx.x == 0;
+    __shared__ double shs[3];      // state (0 go on, 1 stop, 2 NaN), alpha, beta
     double gam = 0.0, del = 0.0, alpha = 0.0, beta = 0.0, target2 = 0.0;
-    int go = 0;
-    T a_t = T(0), b_t = T(0);
     if (lead) {
       gam = g3[0];
       del = g3[1];
       target2 = fmax(prm.cg_rel_tol * prm.cg_rel_tol * gam,
                      prm.cg_abs_floor * prm.cg_abs_floor * g3[2]);
       alpha = del > 0.0 ? gam / del : 0.0;
-      go = (gam > target2 && del > 0.0) ? 1 : 0;
-      a_t = (T)alpha;
+      shs[0] = (gam > target2 && del > 0.0) ? 0.0 : 1.0;
+      shs[1] = alpha;
+      shs[2] = 0.0;
     }
-    go = __shfl_sync(full, go, 0);
-    a_t = __shfl_sync(full, a_t, 0);
+    __syncthreads();
+    int go = shs[0] == 0.0;
+    T a_t = (T)shs[1], b_t = T(0);
+    __syncthreads();
     it = 0;
     while (go && it < prm.cg_max_iter) {
       double z[2] = {0.0, 0.0};
@@ -1045,8 +1047,8 @@ struct Solver {
       if (!sc.reduce(z, 2)) return false;
       ++hess;
       ++it;
-      int state = 0;                 // 0: go on, 1: stop, 2: NaN
       if (lead) {
+        int state = 0;                 // 0: go on, 1: stop, 2: NaN
         const double gam_new = z[0], del_new = z[1];
         if (!(gam_new == gam_new) || !(del_new == del_new)) {
           state = 2;
@@ -1059,18 +1061,21 @@ struct Solver {
           del = denom;
           alpha = denom > 0.0 ? gam_new / denom : 0.0;
           state = denom > 0.0 ? 0 : 1;     // stop if rounding made it non-positive
-          a_t = (T)alpha;
-          b_t = (T)beta;
         }
+        shs[0] = (double)state;
+        shs[1] = alpha;
+        shs[2] = beta;
       }
-      state = __shfl_sync(full, state, 0);
+      __syncthreads();
+      const int state = (int)shs[0];
+      a_t = (T)shs[1];
+      b_t = (T)shs[2];
+      __syncthreads();
       if (state == 2) {
         status = ST_NAN;
         break;
       }
       if (state == 1) break;
-      a_t = __shfl_sync(full, a_t, 0);
-      b_t = __shfl_sync(full, b_t, 0);
     }
     cg_iters += it;
     return true;
