@@ -535,7 +535,7 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   int grid = prm->grid;
   if (grid <= 0) grid = (p->n < 512) ? 1 : dev_sms;
   const int threads = (grid == 1 && prm->threads > 0) ? prm->threads : SOLVER_THREADS;
-  if (threads % 32 != 0 || threads > SOLVER_THREADS) return LORADS_ERR_ARG;
+  if (threads % 32 != 0 || threads > BLOCK_THREADS_MAX) return LORADS_ERR_ARG;
   cudaError_t le;
   if (grid == 1) {
     le = Launch<T>::solve_block(dargs, 1, p->dqueue, 1, threads, s);
@@ -642,7 +642,7 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
 template <typename T>
 static int autotune_batch(lorads_problem* const* ps, int count, const lorads_params* prm,
                           cudaStream_t s, int* threads_out, int* mult_out) {
-  const int cand_threads[] = {128, 256};
+  const int cand_threads[] = {128, 256, 384};
   const int cand_mult[] = {1, 2, 4};
   std::vector<lorads_problem*> sample;
   const int want = std::min(count, 24);
@@ -844,7 +844,7 @@ int lorads_solve_batch(lorads_problem* const* ps, int32_t count, const lorads_pa
     if (threads <= 0) threads = th;
     if (mult <= 0) mult = mu;
   }
-  if (threads % 32 != 0 || threads > SOLVER_THREADS) return LORADS_ERR_ARG;
+  if (threads % 32 != 0 || threads > BLOCK_THREADS_MAX) return LORADS_ERR_ARG;
   if (tuned_threads) *tuned_threads = threads;
   if (tuned_team_mult) *tuned_team_mult = mult;
   st = mixed ? run_batch_once<float>(ps, count, prm, s, threads, mult, res, nullptr)

@@ -5,12 +5,13 @@
 
 namespace lorads {
 
-constexpr int SOLVER_THREADS = 256;       // one-CTA solver (small problems, batches)
+constexpr int SOLVER_THREADS = 256;       // one-CTA solver: default CTA size ...
+constexpr int BLOCK_THREADS_MAX = 384;    // ... and the largest (batches autotune 128..384)
 constexpr int GRID_THREADS_MAX = 320;     // grid solver: CTA size chosen per problem
 
 // one CTA per problem; CTAs take problems from a queue (batches), or a single problem
 template <typename T>
-__global__ void __launch_bounds__(SOLVER_THREADS, 1)
+__global__ void __launch_bounds__(BLOCK_THREADS_MAX, 1)
 solve_block_kernel(const SolverArgs<T>* args, int count, int* queue) {
   __shared__ double red[33 * MAXRED];
   __shared__ SolverArgs<T> sa;
