@@ -184,9 +184,11 @@ int lorads_solve(lorads_problem *p, const lorads_params *prm, void *stream, lora
 
 /* Solves count independent problems (same device) in one persistent launch: one CTA per
  * problem, CTAs take problems from a device-side queue, largest problems first, so uneven
- * sizes balance across the SMs.  prm applies to every problem ("auto" fields resolved per
+ * sizes balance across the SMs.  The device work (queue reset and the persistent kernel) is
+ * captured as a CUDA graph on a private stream and the graph is launched on `stream`.
+ * prm applies to every problem ("auto" fields resolved per
  * problem).  When prm->threads or prm->team_mult is 0 the library autotunes them first: it
- * times every (CTA size in {128, 256}) x (lanes-per-row multiplier in {1, 2, 4}) on a
+ * times every (CTA size in {128, 256, 384}) x (lanes-per-row multiplier in {1, 2, 4}) on a
  * sample of up to 24 problems (Phase II capped at 200 iterations) and keeps the fastest;
  * the choice is returned in *tuned_threads / *tuned_team_mult (either may be NULL).  res
  * (may be NULL) receives count reports; each problem's solution is then available through

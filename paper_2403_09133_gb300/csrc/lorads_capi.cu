@@ -602,20 +602,33 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   dqueue = reinterpret_cast<int*>(reinterpret_cast<char*>(dargs) + sizeof(SolverArgs<T>) * count);
   int st = LORADS_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
   do {
     if ((st = check_cuda(cudaMemcpyAsync(dargs, sorted.data(), sizeof(SolverArgs<T>) * count,
                                          cudaMemcpyHostToDevice, s))) != LORADS_OK) break;
-    if ((st = check_cuda(cudaMemsetAsync(dqueue, 0, 16, s))) != LORADS_OK) break;
     int dev_sms = 0, per_sm = 0;
     if ((st = check_cuda(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount,
                                                 device))) != LORADS_OK) break;
     if ((st = check_cuda(Launch<T>::block_capacity(threads, &per_sm))) != LORADS_OK) break;
     const int grid = std::max(1, std::min(count, std::max(1, per_sm) * dev_sms));
+    // the device work (queue reset + the persistent kernel) as one CUDA graph: captured on a
+    // private stream (the legacy default stream cannot be captured), launched on the caller's
+    if ((st = check_cuda(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) != LORADS_OK)
+      break;
+    if ((st = check_cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) !=
+        LORADS_OK) break;
+    const cudaError_t c1 = cudaMemsetAsync(dqueue, 0, 16, cap);
+    const cudaError_t c2 = Launch<T>::solve_block(dargs, count, dqueue, grid, threads, cap);
+    const cudaError_t c3 = cudaStreamEndCapture(cap, &graph);
+    if ((st = check_cuda(c1 != cudaSuccess ? c1 : (c2 != cudaSuccess ? c2 : c3))) != LORADS_OK)
+      break;
+    if ((st = check_cuda(cudaGraphInstantiate(&gexec, graph, 0))) != LORADS_OK) break;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    if ((st = check_cuda(Launch<T>::solve_block(dargs, count, dqueue, grid, threads, s))) !=
-        LORADS_OK) break;
+    if ((st = check_cuda(cudaGraphLaunch(gexec, s))) != LORADS_OK) break;
     cudaEventRecord(e1, s);
     if ((st = check_cuda(cudaStreamSynchronize(s))) != LORADS_OK) break;
     float ms = 0.f;
@@ -633,6 +646,9 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   } while (false);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cap) cudaStreamDestroy(cap);
   cudaFree(dargs);
   return st;
 }
