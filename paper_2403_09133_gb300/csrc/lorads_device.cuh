@@ -257,24 +257,95 @@ struct GridCtl {
   double result[MAXRED];
 };
 
-// deterministic CTA-wide sum of k values; every thread receives the sums in v
-__device__ inline void block_reduce(double* v, int k, double* red /* smem [33*MAXRED] */) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  for (int i = 0; i < k; ++i) {
-    double x = v[i];
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane == 0) red[warp * MAXRED + i] = x;
+// Sum over the 32 lanes of a warp of K values (K a power of two, <= 16) by recursive halving:
+// each round a lane keeps half of its remaining values and adds the partner's copy of that
+// half (the partner keeps the other half), so after log2 K rounds a lane holds one value
+// index, completed by a butterfly over the remaining lane offsets.  K - 1 + 5 - log2 K FP64
+// adds per lane instead of 5 K (FP64 issues at a small fraction of the FP32 rate here).
+// The order of the additions is fixed, so the sums are deterministic; lanes holding the same
+// index hold bitwise equal sums.  Returns the index held in w[0].
+template <int K>
+__device__ __forceinline__ int warp_sum_scatter(double* w) {
+  const int lane = threadIdx.x & 31;
+  int ix = 0, off = 16;
+#pragma unroll
+  for (int h = K / 2; h >= 1; h >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const double keep = up ? w[i + h] : w[i];
+      const double give = up ? w[i] : w[i + h];
+      w[i] = keep + __shfl_xor_sync(0xffffffffu, give, off);
+    }
+    if (up) ix += h;
+    off >>= 1;
   }
+#pragma unroll
+  for (; off > 0; off >>= 1) w[0] += __shfl_xor_sync(0xffffffffu, w[0], off);
+  return ix;
+}
+
+// the lane that stores the warp sum of its value index (the first of its group)
+template <int K>
+__device__ __forceinline__ bool scatter_writer() {
+  return ((threadIdx.x & 31) & (32 / K - 1)) == 0;
+}
+
+template <int K>
+__device__ __forceinline__ void block_reduce_k(double* v, int k, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double w[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) w[i] = i < k ? v[i] : 0.0;
+  int ix = warp_sum_scatter<K>(w);
+  if (scatter_writer<K>() && ix < k) red[warp * MAXRED + ix] = w[0];
   __syncthreads();
   if (warp == 0) {
-    for (int i = 0; i < k; ++i) {
-      double x = lane < nw ? red[lane * MAXRED + i] : 0.0;
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-      if (lane == 0) red[32 * MAXRED + i] = x;
-    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) w[i] = (lane < nw && i < k) ? red[lane * MAXRED + i] : 0.0;
+    ix = warp_sum_scatter<K>(w);
+    if (scatter_writer<K>() && ix < k) red[32 * MAXRED + ix] = w[0];
   }
   __syncthreads();
   for (int i = 0; i < k; ++i) v[i] = red[32 * MAXRED + i];
+}
+
+// deterministic CTA-wide sum of k (< MAXRED) values; every thread receives the sums in v
+__device__ inline void block_reduce(double* v, int k, double* red /* smem [33*MAXRED] */) {
+  if (k <= 1) block_reduce_k<1>(v, k, red);
+  else if (k <= 2) block_reduce_k<2>(v, k, red);
+  else if (k <= 4) block_reduce_k<4>(v, k, red);
+  else if (k <= 8) block_reduce_k<8>(v, k, red);
+  else block_reduce_k<16>(v, k, red);
+}
+
+// Warp 0 of a CTA: the sum over nb CTAs of the k partials each left in partials[b * MAXRED + i],
+// into red[32 * MAXRED + i].  Lane l adds the CTAs l, l + 32, ...; the loads of a lane are
+// issued together (32 / K CTAs per round trip), then the lanes combine by warp_sum_scatter.
+template <int K>
+__device__ __forceinline__ void grid_partials_k(const double* partials, int k, int nb,
+                                                double* red) {
+  constexpr int TC = 32 / K;
+  const int lane = threadIdx.x & 31;
+  double w[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) w[i] = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 32 * TC) {
+    double buf[TC][K];
+#pragma unroll
+    for (int t = 0; t < TC; ++t) {
+      const int b = b0 + lane + 32 * t;
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        buf[t][i] = (b < nb && i < k) ? __ldcg(partials + b * MAXRED + i) : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < TC; ++t)
+#pragma unroll
+      for (int i = 0; i < K; ++i) w[i] += buf[t][i];
+  }
+  const int ix = warp_sum_scatter<K>(w);
+  if (scatter_writer<K>() && ix < k) red[32 * MAXRED + ix] = w[0];
 }
 
 struct BlockScope {
@@ -340,29 +411,11 @@ struct GridScope {
       __syncwarp();
       if (k > 0) {
         const int nb = gridDim.x;
-        for (int i0 = 0; i0 < k; i0 += 4) {
-          double x[4] = {0.0, 0.0, 0.0, 0.0};
-          for (int b0 = 0; b0 < nb; b0 += 256) {
-            double buf[8][4];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-              const int b = b0 + lane + 32 * t;
-#pragma unroll
-              for (int ii = 0; ii < 4; ++ii)
-                buf[t][ii] = (b < nb && i0 + ii < k) ? __ldcg(partials + b * MAXRED + i0 + ii) : 0.0;
-            }
-#pragma unroll
-            for (int t = 0; t < 8; ++t)
-#pragma unroll
-              for (int ii = 0; ii < 4; ++ii) x[ii] += buf[t][ii];
-          }
-#pragma unroll
-          for (int ii = 0; ii < 4; ++ii) {
-            double y = x[ii];
-            for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
-            if (lane == 0 && i0 + ii < k) red[32 * MAXRED + i0 + ii] = y;
-          }
-        }
+        if (k <= 1) grid_partials_k<1>(partials, k, nb, red);
+        else if (k <= 2) grid_partials_k<2>(partials, k, nb, red);
+        else if (k <= 4) grid_partials_k<4>(partials, k, nb, red);
+        else if (k <= 8) grid_partials_k<8>(partials, k, nb, red);
+        else grid_partials_k<16>(partials, k, nb, red);
       }
     }
     __syncthreads();
