@@ -991,13 +991,18 @@ struct Solver {
     const T* ra = rowa<T>(P);
     const bool lead = threadIdx.x == 0;
     __shared__ double shs[3];      // state (0 go on, 1 stop, 2 NaN), alpha, beta
-    double gam = 0.0, del = 0.0, alpha = 0.0, beta = 0.0, target2 = 0.0;
+    // thread 0 carries gamma = r.r and ga = gamma * alpha: with D = delta_new ga - gamma_new^2
+    // the Chronopoulos-Gear update alpha_new = gamma_new / (delta_new - beta gamma_new / alpha)
+    // is gamma_new ga / D and beta = gamma_new / gamma = gamma_new D / (gamma D), both from the
+    // one reciprocal 1 / (gamma D) (the denominator is positive exactly when D is)
+    double gam = 0.0, ga = 0.0, target2 = 0.0;
     if (lead) {
       gam = g3[0];
-      del = g3[1];
+      const double del = g3[1];
       target2 = fmax(prm.cg_rel_tol * prm.cg_rel_tol * gam,
                      prm.cg_abs_floor * prm.cg_abs_floor * g3[2]);
-      alpha = del > 0.0 ? gam / del : 0.0;
+      const double alpha = del > 0.0 ? gam / del : 0.0;
+      ga = gam * alpha;
       shs[0] = (gam > target2 && del > 0.0) ? 0.0 : 1.0;
       shs[1] = alpha;
       shs[2] = 0.0;
@@ -1050,17 +1055,22 @@ struct Solver {
       if (lead) {
         int state = 0;                 // 0: go on, 1: stop, 2: NaN
         const double gam_new = z[0], del_new = z[1];
+        double alpha = 0.0, beta = 0.0;
         if (!(gam_new == gam_new) || !(del_new == del_new)) {
           state = 2;
         } else if (gam_new <= target2) {
           state = 1;
         } else {
-          beta = gam_new / gam;
-          const double denom = del_new - beta * gam_new / alpha;
-          gam = gam_new;
-          del = denom;
-          alpha = denom > 0.0 ? gam_new / denom : 0.0;
-          state = denom > 0.0 ? 0 : 1;     // stop if rounding made it non-positive
+          const double D = del_new * ga - gam_new * gam_new;
+          if (D > 0.0) {
+            const double inv = 1.0 / (gam * D);
+            beta = gam_new * D * inv;
+            alpha = gam_new * ga * gam * inv;
+            ga = gam_new * alpha;
+            gam = gam_new;
+          } else {
+            state = 1;                     // rounding made the denominator non-positive
+          }
         }
         shs[0] = (double)state;
         shs[1] = alpha;
