@@ -107,6 +107,9 @@ typedef struct lorads_params {
                            /*    (up to rank_max) with the eigenvector z of lambda_min as new */
                            /*    column of U and V, scaled to escape_scale ||U_hat||_F/sqrt(r)*/
                            /*    (0.3; 0 = never)                                             */
+  int32_t group;           /* CTAs per problem in lorads_solve_batch (1, 2, 4): a group     */
+                           /*    shares one problem through bounded barriers; 0 = 2 when the  */
+                           /*    largest problem has n >= 1024, else 1 (0)                    */
 } lorads_params;
 
 /* ---------------------------------------------------------------- result */
@@ -182,9 +185,9 @@ int lorads_set_start(lorads_problem *p, int32_t r, const double *U0, const doubl
  * max_admm_iter iterations with LORADS_ERR_MAXITER. */
 int lorads_solve(lorads_problem *p, const lorads_params *prm, void *stream, lorads_result *res);
 
-/* Solves count independent problems (same device) in one persistent launch: one CTA per
- * problem, CTAs take problems from a device-side queue, largest problems first, so uneven
- * sizes balance across the SMs.  The device work (queue reset and the persistent kernel) is
+/* Solves count independent problems (same device) in one persistent launch: one CTA (or a
+ * group of prm->group CTAs, a cooperative launch) per problem, taking problems from a
+ * device-side queue, largest problems first, so uneven sizes balance across the SMs.  The device work (queue reset and the persistent kernel) is
  * captured as a CUDA graph on a private stream and the graph is launched on `stream`.
  * prm applies to every problem ("auto" fields resolved per
  * problem).  When prm->threads or prm->team_mult is 0 the library autotunes them first: it

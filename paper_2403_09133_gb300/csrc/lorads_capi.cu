@@ -477,7 +477,11 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
       CU(cudaMemsetAsync(h.lam, 0, m * 8, s));
   }
   CU(cudaMemcpyAsync(dargs, &h, sizeof(h), cudaMemcpyHostToDevice, s));
-  CU(cudaMemsetAsync(p->dout, 0, sizeof(SolveOut), s));
+  // the report starts as a device error: a solve that never runs (a launch that failed, a
+  // batch group that stopped at a failed barrier) cannot read as a success
+  SolveOut unreached{};
+  unreached.status = ST_DEVICE;
+  CU(cudaMemcpyAsync(p->dout, &unreached, sizeof(SolveOut), cudaMemcpyHostToDevice, s));
   CU(cudaMemsetAsync(p->dctl, 0, sizeof(GridCtl), s));
   CU(cudaMemsetAsync(p->dpartials, 0xFF, sizeof(double) * (size_t)dev_sms * 8 * MAXRED * 3, s));
   CU(cudaMemsetAsync(p->dqueue, 0, 16, s));
@@ -572,8 +576,8 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
 // ---------------------------------------------------------------------------------------
 template <typename T>
 static int run_batch_once(lorads_problem* const* ps, int count, const lorads_params* prm,
-                          cudaStream_t s, int threads, int team_mult, lorads_result* res,
-                          double* seconds) {
+                          cudaStream_t s, int threads, int team_mult, int group,
+                          lorads_result* res, double* seconds) {
   const int device = ps[0]->device;
   std::vector<SolverArgs<T>> hs(count);
   std::vector<std::pair<double, int>> order(count);
@@ -596,10 +600,30 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   std::stable_sort(order.begin(), order.end());
   std::vector<SolverArgs<T>> sorted(count);
   for (int k = 0; k < count; ++k) sorted[k] = hs[order[k].second];
-  SolverArgs<T>* dargs = nullptr;
-  int* dqueue = nullptr;
-  CU(cudaMalloc((void**)&dargs, sizeof(SolverArgs<T>) * count + 256));
-  dqueue = reinterpret_cast<int*>(reinterpret_cast<char*>(dargs) + sizeof(SolverArgs<T>) * count);
+  int dev_sms = 0, per_sm = 0;
+  CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device));
+  if (group > 1) CU(Launch<T>::group_capacity(threads, &per_sm));
+  else CU(Launch<T>::block_capacity(threads, &per_sm));
+  // one CTA per problem, or groups of `group` CTAs per problem (never more than resident)
+  int grid = std::max(1, std::min(count, std::max(1, per_sm) * dev_sms));
+  int groups = 0;
+  if (group > 1) {
+    groups = std::min(count, std::max(1, per_sm) * dev_sms / group);
+    if (groups < 1) return LORADS_ERR_ARG;
+    grid = groups * group;
+  }
+  // argument block, queue, and for groups their barriers, problem slots and partial sums
+  const size_t a_bytes = (sizeof(SolverArgs<T>) * count + 255) / 256 * 256;
+  const size_t c_bytes = (sizeof(GridCtl) * groups + 255) / 256 * 256;
+  const size_t s_bytes = (sizeof(int) * groups + 255) / 256 * 256;
+  const size_t p_bytes = sizeof(double) * (size_t)grid * MAXRED * (group > 1 ? 1 : 0);
+  char* base = nullptr;
+  CU(cudaMalloc((void**)&base, a_bytes + 256 + c_bytes + s_bytes + p_bytes));
+  SolverArgs<T>* dargs = reinterpret_cast<SolverArgs<T>*>(base);
+  int* dqueue = reinterpret_cast<int*>(base + a_bytes);
+  GridCtl* dctls = reinterpret_cast<GridCtl*>(base + a_bytes + 256);
+  int* dslots = reinterpret_cast<int*>(base + a_bytes + 256 + c_bytes);
+  double* dparts = reinterpret_cast<double*>(base + a_bytes + 256 + c_bytes + s_bytes);
   int st = LORADS_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaStream_t cap = nullptr;
@@ -608,19 +632,19 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   do {
     if ((st = check_cuda(cudaMemcpyAsync(dargs, sorted.data(), sizeof(SolverArgs<T>) * count,
                                          cudaMemcpyHostToDevice, s))) != LORADS_OK) break;
-    int dev_sms = 0, per_sm = 0;
-    if ((st = check_cuda(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount,
-                                                device))) != LORADS_OK) break;
-    if ((st = check_cuda(Launch<T>::block_capacity(threads, &per_sm))) != LORADS_OK) break;
-    const int grid = std::max(1, std::min(count, std::max(1, per_sm) * dev_sms));
-    // the device work (queue reset + the persistent kernel) as one CUDA graph: captured on a
-    // private stream (the legacy default stream cannot be captured), launched on the caller's
+    // the device work (queue and barrier resets + the persistent kernel) as one CUDA graph:
+    // captured on a private stream (the legacy default stream cannot be captured), launched
+    // on the caller's
     if ((st = check_cuda(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) != LORADS_OK)
       break;
     if ((st = check_cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) !=
         LORADS_OK) break;
-    const cudaError_t c1 = cudaMemsetAsync(dqueue, 0, 16, cap);
-    const cudaError_t c2 = Launch<T>::solve_block(dargs, count, dqueue, grid, threads, cap);
+    cudaError_t c1 = cudaMemsetAsync(dqueue, 0, 16, cap);
+    if (c1 == cudaSuccess && group > 1) c1 = cudaMemsetAsync(dctls, 0, c_bytes, cap);
+    const cudaError_t c2 =
+        group > 1 ? Launch<T>::solve_group(dargs, count, dqueue, dctls, dparts, dslots, group,
+                                           50LL * 1000 * 1000, grid, threads, cap)
+                  : Launch<T>::solve_block(dargs, count, dqueue, grid, threads, cap);
     const cudaError_t c3 = cudaStreamEndCapture(cap, &graph);
     if ((st = check_cuda(c1 != cudaSuccess ? c1 : (c2 != cudaSuccess ? c2 : c3))) != LORADS_OK)
       break;
@@ -649,7 +673,7 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   if (gexec) cudaGraphExecDestroy(gexec);
   if (graph) cudaGraphDestroy(graph);
   if (cap) cudaStreamDestroy(cap);
-  cudaFree(dargs);
+  cudaFree(base);
   return st;
 }
 
@@ -657,7 +681,7 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
 // (CTA size, lanes-per-row multiplier) candidate and returns the fastest.
 template <typename T>
 static int autotune_batch(lorads_problem* const* ps, int count, const lorads_params* prm,
-                          cudaStream_t s, int* threads_out, int* mult_out) {
+                          cudaStream_t s, int group, int* threads_out, int* mult_out) {
   const int cand_threads[] = {128, 256, 384};
   const int cand_mult[] = {1, 2, 4};
   std::vector<lorads_problem*> sample;
@@ -671,7 +695,8 @@ static int autotune_batch(lorads_problem* const* ps, int count, const lorads_par
   for (int th : cand_threads)
     for (int mu : cand_mult) {
       double sec = 0.0;
-      int st = run_batch_once<T>(sample.data(), (int)sample.size(), &q, s, th, mu, nullptr, &sec);
+      int st = run_batch_once<T>(sample.data(), (int)sample.size(), &q, s, th, mu, group,
+                                 nullptr, &sec);
       if (st != LORADS_OK) return st;
       if (sec < best) {
         best = sec;
@@ -790,6 +815,7 @@ void lorads_default_params(lorads_params* prm) {
   prm->lanczos_steps = 128;
   prm->dinf_every = 10;
   prm->escape_scale = 0.3;
+  prm->group = 0;
 }
 
 int lorads_set_start(lorads_problem* p, int32_t r, const double* U0, const double* lambda0,
@@ -852,10 +878,16 @@ int lorads_solve_batch(lorads_problem* const* ps, int32_t count, const lorads_pa
   const bool mixed = prm->precision == LORADS_PREC_MIXED;
   int threads = prm->threads, mult = prm->team_mult;
   int st = LORADS_OK;
+  // CTAs per problem: automatic = 2 when the largest problem has n >= 1024 (one CTA then
+  // carries a long solve alone and sets the batch's makespan), else 1
+  int64_t n_max = 0;
+  for (int i = 0; i < count; ++i) n_max = std::max(n_max, ps[i]->n);
+  const int group = prm->group > 0 ? prm->group : (n_max >= 1024 ? 2 : 1);
+  if (group != 1 && group != 2 && group != 4) return LORADS_ERR_ARG;
   if (threads <= 0 || mult <= 0) {
     int th = SOLVER_THREADS, mu = 1;
-    st = mixed ? autotune_batch<float>(ps, count, prm, s, &th, &mu)
-               : autotune_batch<double>(ps, count, prm, s, &th, &mu);
+    st = mixed ? autotune_batch<float>(ps, count, prm, s, group, &th, &mu)
+               : autotune_batch<double>(ps, count, prm, s, group, &th, &mu);
     if (st != LORADS_OK) return st;
     if (threads <= 0) threads = th;
     if (mult <= 0) mult = mu;
@@ -863,8 +895,8 @@ int lorads_solve_batch(lorads_problem* const* ps, int32_t count, const lorads_pa
   if (threads % 32 != 0 || threads > BLOCK_THREADS_MAX) return LORADS_ERR_ARG;
   if (tuned_threads) *tuned_threads = threads;
   if (tuned_team_mult) *tuned_team_mult = mult;
-  st = mixed ? run_batch_once<float>(ps, count, prm, s, threads, mult, res, nullptr)
-             : run_batch_once<double>(ps, count, prm, s, threads, mult, res, nullptr);
+  st = mixed ? run_batch_once<float>(ps, count, prm, s, threads, mult, group, res, nullptr)
+             : run_batch_once<double>(ps, count, prm, s, threads, mult, group, res, nullptr);
   return st;
 }
 
@@ -1127,7 +1159,9 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   }
   // what must start at zero: the report, the grid barrier and the CTA queue
   CU(cudaMemcpyAsync(dargs, &h, sizeof(h), cudaMemcpyHostToDevice, s));
-  CU(cudaMemsetAsync(dout, 0, sizeof(SolveOut), s));
+  SolveOut unreached{};
+  unreached.status = ST_DEVICE;
+  CU(cudaMemcpyAsync(dout, &unreached, sizeof(SolveOut), cudaMemcpyHostToDevice, s));
   CU(cudaMemsetAsync(dctl, 0, sizeof(GridCtl), s));
   CU(cudaMemsetAsync(dpartials, 0xFF, sizeof(double) * (size_t)dev_sms * 8 * MAXRED * 3, s));
   CU(cudaMemsetAsync(dqueue, 0, 16, s));

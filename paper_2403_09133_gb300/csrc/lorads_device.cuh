@@ -348,8 +348,13 @@ __device__ __forceinline__ void grid_partials_k(const double* partials, int k, i
   if (scatter_writer<K>() && ix < k) red[32 * MAXRED + ix] = w[0];
 }
 
+// Scopes: the CTA's shared array `red` holds 34 rows of MAXRED doubles: rows 0..31 the
+// per-warp sums of a reduction, row 32 its results, row 33 per-CTA scalar scratch for the
+// solver (no __shared__ variables are declared inside solver functions, which several kernels
+// instantiate).
 struct BlockScope {
   double* red;
+  __device__ double* scratch() const { return red + 33 * MAXRED; }
   __device__ int tid() const { return threadIdx.x; }
   __device__ int nthreads() const { return blockDim.x; }
   __device__ bool sync() {
@@ -364,16 +369,20 @@ struct BlockScope {
 };
 
 struct GridScope {
-  double* red;             // shared memory
+  double* red;             // shared memory (34 rows of MAXRED, see BlockScope)
   GridCtl* ctl;            // zeroed before launch
   double* partials;        // gridDim.x * MAXRED
   long long spin_limit;    // polls before a barrier gives up
+  int first = 0;           // the scope spans CTAs [first, first + nb) of a cooperative launch
+  int nb = 0;              // (0: the whole grid)
 
-  __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
-  __device__ int nthreads() const { return gridDim.x * blockDim.x; }
-  __device__ bool is_leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+  __device__ int count() const { return nb > 0 ? nb : (int)gridDim.x; }
+  __device__ double* scratch() const { return red + 33 * MAXRED; }
+  __device__ int tid() const { return ((int)blockIdx.x - first) * blockDim.x + threadIdx.x; }
+  __device__ int nthreads() const { return count() * blockDim.x; }
+  __device__ bool is_leader() const { return (int)blockIdx.x == first && threadIdx.x == 0; }
 
-  // Bounded barrier over all CTAs.  With k > 0 it also sums, over CTAs in CTA order, the
+  // Bounded barrier over the scope's CTAs.  With k > 0 it also sums, over CTAs in CTA order, the
   // CTA sums left in red[32*MAXRED + i] by block_reduce.  Arrival is an acq_rel increment of
   // ctl->count; the last CTA resets the count and releases the generation; the others poll
   // the generation with acquire loads (bounded).  Every CTA then loads all partials -- the
@@ -387,7 +396,7 @@ struct GridScope {
         for (int i = 0; i < k; ++i) partials[blockIdx.x * MAXRED + i] = red[32 * MAXRED + i];
         const unsigned my_gen = ld_acquire_u32(&ctl->gen);
         const unsigned arrived = atom_add_acq_rel_u32(&ctl->count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == (unsigned)count() - 1) {
           ctl->count = 0;
           red_add_release_u32(&ctl->gen, 1u);
         } else {
@@ -410,12 +419,13 @@ struct GridScope {
       // lane 0's acquire orders the other lanes' loads through __syncwarp
       __syncwarp();
       if (k > 0) {
-        const int nb = gridDim.x;
-        if (k <= 1) grid_partials_k<1>(partials, k, nb, red);
-        else if (k <= 2) grid_partials_k<2>(partials, k, nb, red);
-        else if (k <= 4) grid_partials_k<4>(partials, k, nb, red);
-        else if (k <= 8) grid_partials_k<8>(partials, k, nb, red);
-        else grid_partials_k<16>(partials, k, nb, red);
+        const int c = count();
+        const double* pp = partials + (size_t)first * MAXRED;
+        if (k <= 1) grid_partials_k<1>(pp, k, c, red);
+        else if (k <= 2) grid_partials_k<2>(pp, k, c, red);
+        else if (k <= 4) grid_partials_k<4>(pp, k, c, red);
+        else if (k <= 8) grid_partials_k<8>(pp, k, c, red);
+        else grid_partials_k<16>(pp, k, c, red);
       }
     }
     __syncthreads();

@@ -13,7 +13,7 @@ constexpr int GRID_THREADS_MAX = 320;     // grid solver: CTA size chosen per pr
 template <typename T>
 __global__ void __launch_bounds__(BLOCK_THREADS_MAX, 1)
 solve_block_kernel(const SolverArgs<T>* args, int count, int* queue) {
-  __shared__ double red[33 * MAXRED];
+  __shared__ double red[34 * MAXRED];
   __shared__ SolverArgs<T> sa;
   __shared__ int inst;
   for (;;) {
@@ -33,12 +33,37 @@ solve_block_kernel(const SolverArgs<T>* args, int count, int* queue) {
 template <typename T>
 __global__ void __launch_bounds__(GRID_THREADS_MAX, 1)
 solve_grid_kernel(const SolverArgs<T>* args, GridCtl* ctl, double* partials, long long spin) {
-  __shared__ double red[33 * MAXRED];
+  __shared__ double red[34 * MAXRED];
   __shared__ SolverArgs<T> sa;
   if (threadIdx.x == 0) sa = *args;
   __syncthreads();
-  GridScope sc{red, ctl, partials, spin};
+  GridScope sc{red, ctl, partials, spin, 0, (int)gridDim.x};
   run_solver<T>(sa, sc);
+}
+
+// batches with several CTAs per problem: CTAs [g * group, (g + 1) * group) form group g,
+// which takes problems from the queue (largest first) and solves each with a scope spanning
+// the group (ctls[g] is its barrier, slots[g] the index its leader fetched).  The launch is
+// cooperative, so every CTA of a group is resident and the group's bounded barriers never
+// wait on a CTA that has not started.
+template <typename T>
+__global__ void __launch_bounds__(BLOCK_THREADS_MAX, 1)
+solve_group_kernel(const SolverArgs<T>* args, int count, int* queue, GridCtl* ctls,
+                   double* partials, int* slots, int group, long long spin) {
+  __shared__ double red[34 * MAXRED];
+  __shared__ SolverArgs<T> sa;
+  const int g = blockIdx.x / group;
+  GridScope sc{red, ctls + g, partials, spin, g * group, group};
+  for (;;) {
+    if (sc.is_leader()) slots[g] = atomicAdd(queue, 1);
+    if (!sc.sync()) return;
+    const int i = __ldcg(slots + g);
+    if (i >= count) return;
+    if (threadIdx.x == 0) sa = args[i];
+    __syncthreads();
+    run_solver<T>(sa, sc);
+    __syncthreads();
+  }
 }
 
 // ---- operators on caller-owned device arrays ----
@@ -104,6 +129,10 @@ struct Launch {
   static cudaError_t solve_grid(const SolverArgs<T>* args, GridCtl* ctl, double* partials,
                                 long long spin, int grid, int threads, cudaStream_t s);
   static cudaError_t grid_capacity(int threads, int* blocks_per_sm);
+  static cudaError_t solve_group(const SolverArgs<T>* args, int count, int* queue, GridCtl* ctls,
+                                 double* partials, int* slots, int group, long long spin,
+                                 int grid, int threads, cudaStream_t s);
+  static cudaError_t group_capacity(int threads, int* blocks_per_sm);
   static cudaError_t op_sddmm(const DevProblem& P, int ld, const T* U, const T* V, double* q,
                               int grid, cudaStream_t s);
   static cudaError_t op_spmm(const DevProblem& P, int ld, const double* w, double gamma,
@@ -119,6 +148,10 @@ struct Launch {
   template <> cudaError_t Launch<T>::solve_grid(const SolverArgs<T>*, GridCtl*, double*,        \
                                                 long long, int, int, cudaStream_t);             \
   template <> cudaError_t Launch<T>::grid_capacity(int, int*);                                  \
+  template <> cudaError_t Launch<T>::solve_group(const SolverArgs<T>*, int, int*, GridCtl*,     \
+                                                 double*, int*, int, long long, int, int,       \
+                                                 cudaStream_t);                                 \
+  template <> cudaError_t Launch<T>::group_capacity(int, int*);                                 \
   template <> cudaError_t Launch<T>::op_sddmm(const DevProblem&, int, const T*, const T*,      \
                                               double*, int, cudaStream_t);                      \
   template <> cudaError_t Launch<T>::op_spmm(const DevProblem&, int, const double*, double,    \
@@ -150,6 +183,20 @@ LORADS_DECLARE_LAUNCH(float)
   template <>                                                                                  \
   cudaError_t Launch<T>::grid_capacity(int threads, int* blocks_per_sm) {                      \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_grid_kernel<T>,  \
+                                                         threads, 0);                          \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t Launch<T>::solve_group(const SolverArgs<T>* args, int count, int* queue,         \
+                                     GridCtl* ctls, double* partials, int* slots, int group,   \
+                                     long long spin, int grid, int threads, cudaStream_t s) {  \
+    void* kargs[] = {(void*)&args,     (void*)&count, (void*)&queue, (void*)&ctls,             \
+                     (void*)&partials, (void*)&slots, (void*)&group, (void*)&spin};            \
+    return cudaLaunchCooperativeKernel((const void*)solve_group_kernel<T>, dim3(grid),         \
+                                       dim3(threads), kargs, 0, s);                            \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t Launch<T>::group_capacity(int threads, int* blocks_per_sm) {                     \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_group_kernel<T>, \
                                                          threads, 0);                          \
   }                                                                                            \
   template <>                                                                                  \

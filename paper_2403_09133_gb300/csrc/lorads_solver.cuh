@@ -990,7 +990,7 @@ struct Solver {
     const T rho_t = (T)rho, gamma_t = (T)gamma;
     const T* ra = rowa<T>(P);
     const bool lead = threadIdx.x == 0;
-    __shared__ double shs[3];      // state (0 go on, 1 stop, 2 NaN), alpha, beta
+    double* shs = sc.scratch() + 4;   // state (0 go on, 1 stop, 2 NaN), alpha, beta
     // thread 0 carries gamma = r.r and ga = gamma * alpha: with D = delta_new ga - gamma_new^2
     // the Chronopoulos-Gear update alpha_new = gamma_new / (delta_new - beta gamma_new / alpha)
     // is gamma_new ga / D and beta = gamma_new / gamma = gamma_new D / (gamma D), both from the
@@ -1377,7 +1377,7 @@ struct Solver {
     if (!sc.sync()) return false;       // the coefficients written by the leader
     // largest eigenvalue of each T_c: warp c of every CTA, 32-point multisection on the
     // Sturm count (identical in every CTA, so every thread ends with the same estimate)
-    __shared__ double theta[NC];
+    double* theta = sc.scratch();     // NC entries
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < NC) {
       const int c = warp, L = len[c];

@@ -45,7 +45,7 @@ class lorads_params(ctypes.Structure):
         ("seed", _u64), ("precision", _i32), ("phase1", _i32), ("time_limit_s", _f64),
         ("threads", _i32), ("grid", _i32), ("team_mult", _i32),
         ("kkt_dinf", _i32), ("lanczos_steps", _i32), ("dinf_every", _i32),
-        ("escape_scale", _f64),
+        ("escape_scale", _f64), ("group", _i32),
     ]
 
 

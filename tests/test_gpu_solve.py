@@ -100,6 +100,9 @@ def test_matrix_completion_small(cuda):
     res, sol = gpu_solve(inst, switch_tol=1e-3, h=5.0, tol=1e-9, max_admm_iter=3000)
     want = 2.0 * np.linalg.svd(inst.mc_P @ inst.mc_Q.T, compute_uv=False).sum()
     assert abs(res["objective"] - want) <= 1e-7 * want
+    # the one-CTA solve of a general (non-diagonal) problem is deterministic
+    again, _ = gpu_solve(inst, switch_tol=1e-3, h=5.0, tol=1e-9, max_admm_iter=3000)
+    assert again["objective"] == res["objective"] and again["admm_iters"] == res["admm_iters"]
 
 
 def test_status_codes(cuda):
