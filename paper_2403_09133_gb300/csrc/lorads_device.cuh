@@ -444,6 +444,11 @@ struct GridScope {
   }
 };
 
+// The scope of a CTA group inside a batch launch: the grid scope's code, as a type of its own
+// so that each kernel instantiates its own solver (no solver instantiation is reached from
+// two kernels).
+struct GroupScope : GridScope {};
+
 // ------------------------------------------------------------------------------------
 // per-row operators (shared by the solver and the operator entry points)
 // ------------------------------------------------------------------------------------

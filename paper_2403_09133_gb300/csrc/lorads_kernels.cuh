@@ -53,7 +53,7 @@ solve_group_kernel(const SolverArgs<T>* args, int count, int* queue, GridCtl* ct
   __shared__ double red[34 * MAXRED];
   __shared__ SolverArgs<T> sa;
   const int g = blockIdx.x / group;
-  GridScope sc{red, ctls + g, partials, spin, g * group, group};
+  GroupScope sc{{red, ctls + g, partials, spin, g * group, group}};
   for (;;) {
     if (sc.is_leader()) slots[g] = atomicAdd(queue, 1);
     if (!sc.sync()) return;

@@ -154,3 +154,15 @@ def test_rank_growth_matches_oracle(cuda, prec):
     assert sol["U_hat"].shape == (100, 14)
     assert res["status"] == 0 and ref["converged"]
     assert abs(res["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+
+
+def test_matrix_completion_grid_scope_both_forms(cuda):
+    """n = 1,000 (the whole-GPU scope) on the general path: both forms pass the final test,
+    agree on the objective, and the FP64 form is deterministic."""
+    inst = I.matrix_completion(500, 500, 3, 60000, seed=4)
+    r64, _ = gpu_solve(inst, precision=L.LORADS_PREC_FP64)
+    r32, _ = gpu_solve(inst, precision=L.LORADS_PREC_MIXED)
+    again, _ = gpu_solve(inst, precision=L.LORADS_PREC_FP64)
+    assert r64["status"] == 0 and r32["status"] == 0
+    assert abs(r64["objective"] - r32["objective"]) <= 1e-5 * abs(r64["objective"])
+    assert again["objective"] == r64["objective"] and again["admm_iters"] == r64["admm_iters"]
