@@ -27,6 +27,7 @@
 #ifndef LORADS_H
 #define LORADS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -54,6 +55,21 @@ enum {
   LORADS_PREC_MIXED = 1   /* CG operators (SDDMM/SpMM bulk, CG vectors) in FP32; masters   */
                           /* U, V, lambda, residual norms, CG alpha/beta, objective in FP64 */
 };
+
+/* ---------------------------------------------------------------- device allocator
+ * Optional replacement for cudaMalloc / cudaFree, given through lorads_params (both set or
+ * both NULL).  alloc returns `bytes` of device memory of the problem's device, 256-byte
+ * aligned, usable by work enqueued on `stream` (the cudaStream_t of the call that
+ * allocates), or NULL when it cannot (the call then returns LORADS_ERR_NOMEM).  free gets
+ * back the pointer, its size and the stream it was allocated for, after every piece of
+ * device work that used it has finished.  Memory that outlives a call (the problem's device
+ * form and its solver state, kept for later solves and for lorads_get_solution /
+ * lorads_get_state) is released through the free of the allocator that made it, at the
+ * latest by lorads_destroy: the two functions and ctx must stay valid until then.  Both
+ * are called from the thread that makes the library call, never concurrently for one
+ * problem.  The Python binding points them at PyTorch's caching allocator. */
+typedef void *(*lorads_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*lorads_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 
 /* ---------------------------------------------------------------- parameters
  * Defaults (lorads_default_params) follow Section 5.1 where the paper states a value and
@@ -110,6 +126,9 @@ typedef struct lorads_params {
   int32_t group;           /* CTAs per problem in lorads_solve_batch (1, 2, 4): a group     */
                            /*    shares one problem through bounded barriers; 0 = 2 when the  */
                            /*    largest problem has n >= 1024, else 1 (0)                    */
+  lorads_alloc_fn dev_alloc; /* device allocator (NULL with dev_free: cudaMalloc / cudaFree) */
+  lorads_free_fn dev_free;
+  void *alloc_ctx;         /* passed to dev_alloc and dev_free                               */
 } lorads_params;
 
 /* ---------------------------------------------------------------- result */
@@ -169,7 +188,8 @@ int lorads_set_b(lorads_problem *p, const double *b);
 void lorads_default_params(lorads_params *prm);
 
 /* Phase II start for prm->phase1 == 0 (e.g. a learned warm start): U0 is n x r row-major
- * (U = V = U0), lambda0 of length m (NULL = 0), rho0 the initial penalty (<= 0: 100). */
+ * (U = V = U0), lambda0 of length m (NULL = 0), rho0 the initial penalty (<= 0: 100).
+ * Replaces a start given by lorads_set_state. */
 int lorads_set_start(lorads_problem *p, int32_t r, const double *U0, const double *lambda0,
                      double rho0);
 
@@ -206,6 +226,55 @@ int lorads_solve_batch(lorads_problem *const *ps, int32_t count, const lorads_pa
 int lorads_get_solution(const lorads_problem *p, double *U, double *V, double *U_hat,
                         double *y, int32_t *r);
 
+/* ---------------------------------------------------------------- checkpoint / resume
+ * A Phase II iterate of Algorithm 1 -- (U^k, V^k, lambda^k) with the penalty rho for the
+ * next iteration, the rank and the counters -- is the whole state the iteration carries from
+ * one step to the next (the CG solves start from W and need no history; the Phase I -> II
+ * switch of Algorithm 2 is the same kind of hand-over, with V = U).  A solve stopped by
+ * max_admm_iter or time_limit_s can therefore be continued later, in this process or
+ * another, by lorads_get_state after it and lorads_set_state + lorads_solve (phase1 = 0)
+ * before the continuation.  The continuation keeps the iteration counter k (so the rho
+ * schedule of Section 5.1, the max_admm_iter cap and the final-test schedule go on where
+ * they stopped), the split penalty gamma of the checkpoint, and it reports totals (ADMM, CG,
+ * Hessian, Phase I counters) including the checkpointed part.  Its iterates agree with an
+ * uninterrupted solve's up to rounding: the resumed solve recomputes the row-local CG's
+ * incrementally kept products -(C W) and, in the MIXED form, re-rounds the FP32 shadows of
+ * U and V from the FP64 masters.  time_limit_s counts per call. */
+typedef struct lorads_state {
+  int64_t n, m;            /* order and constraint count of the problem it belongs to         */
+  int32_t phase;           /* 2: a Phase II iterate (the only kind lorads_set_state takes)    */
+  int32_t rank;            /* r: columns of U and V                                          */
+  int32_t admm_iters;      /* k: Phase II iterations done                                    */
+  int32_t next_dual_test;  /* first k at which the dual-infeasibility test may run again     */
+  int32_t cg_iters;        /* counters of the solve so far (lorads_result meanings)          */
+  int32_t hessian_applies;
+  int32_t alm_outer;
+  int32_t lbfgs_iters;
+  int32_t rank_growths;
+  int32_t reserved;        /* 0                                                              */
+  double rho;              /* penalty of iteration k + 1                                     */
+  double gamma;            /* split penalty of eq. linU / eq. linV                           */
+  double sigma;            /* final Phase I penalty (reported only)                          */
+  double prev_d_infeas;    /* dual infeasibility of the latest failed final test since the  */
+                           /*    last rank growth (NaN: none), for the growth rule            */
+} lorads_state;
+
+/* The state after the last solve of p (lorads_solve, lorads_solve_batch) into *st and the
+ * host buffers U, V (n x st->rank row-major) and lambda (length m, the multiplier of eq. ALF,
+ * lambda = -y); each buffer may be NULL (call once with NULL buffers to learn the rank).
+ * LORADS_ERR_STATE when there is no solve, or it ended in Phase I or with a NaN or device
+ * status. */
+int lorads_get_state(const lorads_problem *p, lorads_state *st, double *U, double *V,
+                     double *lambda);
+
+/* Makes *st with U, V (n x st->rank row-major) and lambda (length m; NULL = 0) the start of
+ * the next solve with prm->phase1 == 0 (replacing lorads_set_start's).  Host data are
+ * copied.  LORADS_ERR_ARG when st->n / st->m differ from p's, st->phase != 2, the rank is
+ * outside [1, min(n, 256)], rho or gamma is not positive, the counters are negative, U or V
+ * is NULL or a value is not finite. */
+int lorads_set_state(lorads_problem *p, const lorads_state *st, const double *U,
+                     const double *V, const double *lambda);
+
 /* Allocation-free solve.  The paper has no counterpart: this is a deployment variant of
  * lorads_solve for callers that must not allocate device memory while they solve -- code
  * that runs between the set-up and the end of a latency-critical loop, processes that
@@ -240,9 +309,10 @@ void lorads_destroy(lorads_problem *p);
 
 const char *lorads_status_string(int code);
 
-/* sizeof(lorads_params) and sizeof(lorads_result) as compiled into the library, so that a
- * binding can check its mirror of the two structs.  Either pointer may be NULL. */
-void lorads_struct_sizes(int64_t *params_bytes, int64_t *result_bytes);
+/* sizeof(lorads_params), sizeof(lorads_result) and sizeof(lorads_state) as compiled into
+ * the library, so that a binding can check its mirror of the structs.  Any pointer may be
+ * NULL. */
+void lorads_struct_sizes(int64_t *params_bytes, int64_t *result_bytes, int64_t *state_bytes);
 
 /* ---------------------------------------------------------------- learned warm start
  * A 3-layer message-passing network over the cost graph proposes the Phase II start

@@ -275,6 +275,10 @@ class AdmmState:
     cg_iters: int = 0
     rp: float = math.inf
     growths: int = 0
+    # final-test schedule: first k at which the dual infeasibility may be tested again, and
+    # the dual infeasibility of the latest failed test since the last rank growth
+    next_dual_test: int = 0
+    prev_dinf: Optional[float] = None
 
 
 def admm_iteration(sdp: SDP, st: AdmmState, p: Params) -> dict:
@@ -315,9 +319,22 @@ def lradmm(sdp: SDP, U0, V0, lam0, rho0: float, p: Params, trace: Optional[list]
     most once per max(dinf_every, k // 10) iterations after a failure)."""
     st = AdmmState(U=U0.copy(), V=V0.copy(), lam=lam0.copy(), rho=rho0,
                    rp=primal_infeasibility(sdp, U0, V0))
+    return _lradmm_loop(sdp, st, p, trace)
+
+
+def lradmm_resume(sdp: SDP, state: AdmmState, p: Params, trace: Optional[list] = None):
+    """Continues Algorithm 1 from a checkpointed iterate: (U^k, V^k, lambda^k), the penalty
+    of iteration k+1, k, and the final-test schedule are all the iteration carries from one
+    step to the next (each CG solve starts from W), so the continuation repeats the
+    uninterrupted run.  `state` is not modified."""
+    st = AdmmState(U=state.U.copy(), V=state.V.copy(), lam=state.lam.copy(), rho=state.rho,
+                   k=state.k, cg_iters=state.cg_iters, rp=state.rp, growths=state.growths,
+                   next_dual_test=state.next_dual_test, prev_dinf=state.prev_dinf)
+    return _lradmm_loop(sdp, st, p, trace)
+
+
+def _lradmm_loop(sdp: SDP, st: AdmmState, p: Params, trace: Optional[list]):
     converged = False
-    next_dual_test = 0
-    prev_dinf = None
     cap = rank_cap(sdp.m, sdp.n, p)
     while st.k < p.max_admm_iter:
         info = admm_iteration(sdp, st, p)
@@ -328,14 +345,14 @@ def lradmm(sdp: SDP, U0, V0, lam0, rho0: float, p: Params, trace: Optional[list]
             if abs(info["gap"]) <= p.tol:
                 if not p.kkt_dinf:
                     converged = True
-                elif st.k >= next_dual_test:
+                elif st.k >= st.next_dual_test:
                     info["d_inf"] = dual_infeasibility(sdp, y)
                     if info["d_inf"] <= p.tol:
                         converged = True
                     else:
-                        next_dual_test = st.k + max(p.dinf_every, st.k // 10)
+                        st.next_dual_test = st.k + max(p.dinf_every, st.k // 10)
                         r = st.U.shape[1]
-                        if (prev_dinf is not None and info["d_inf"] > 0.9 * prev_dinf
+                        if (st.prev_dinf is not None and info["d_inf"] > 0.9 * st.prev_dinf
                                 and p.escape_scale > 0 and r < cap):
                             _, z = min_eig_pair_dual_slack(sdp, y)
                             r_new = max(next_rank(r, cap, p), r + 1)
@@ -346,9 +363,9 @@ def lradmm(sdp: SDP, U0, V0, lam0, rho0: float, p: Params, trace: Optional[list]
                             st.V = np.concatenate([st.V, add], axis=1)
                             st.growths += 1
                             info["grow_to"] = r_new
-                            prev_dinf = None
+                            st.prev_dinf = None
                         else:
-                            prev_dinf = info["d_inf"]
+                            st.prev_dinf = info["d_inf"]
         if trace is not None:
             trace.append(info)
         if converged:

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <cstdint>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -27,27 +28,69 @@ struct Rank1Term {
   double scale;
 };
 
-// one device allocation carved into 256-byte aligned pieces
+// where device memory comes from: the caller's allocator (lorads_params dev_alloc/dev_free)
+// or cudaMalloc / cudaFree
+struct DevAlloc {
+  lorads_alloc_fn alloc = nullptr;
+  lorads_free_fn free = nullptr;
+  void* ctx = nullptr;
+  void* stream = nullptr;
+  static DevAlloc from(const lorads_params* prm, void* stream) {
+    DevAlloc a;
+    if (prm) {
+      a.alloc = prm->dev_alloc;
+      a.free = prm->dev_free;
+      a.ctx = prm->alloc_ctx;
+    }
+    a.stream = stream;
+    return a;
+  }
+  bool valid() const { return (alloc == nullptr) == (free == nullptr); }
+  // nullptr when the memory cannot be had or is not 256-byte aligned
+  void* get(size_t bytes) const {
+    if (!alloc) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      return p;
+    }
+    void* p = alloc(bytes, stream, ctx);
+    if (p && (reinterpret_cast<uintptr_t>(p) & 255) != 0) {
+      free(p, bytes, stream, ctx);
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p, size_t bytes) const {
+    if (!p) return;
+    if (free) free(p, bytes, stream, ctx);
+    else cudaFree(p);
+  }
+};
+
+// one device allocation carved into 256-byte aligned pieces; it remembers the allocator
+// that made it and returns the block there
 struct Arena {
   char* base = nullptr;
   size_t cap = 0;
   size_t used = 0;
+  DevAlloc owner;
   void release() {
-    if (base) cudaFree(base);
+    if (base) owner.put(base, cap);
     base = nullptr;
     cap = used = 0;
   }
-  int reserve(size_t bytes) {
+  int reserve(size_t bytes, const DevAlloc& al) {
     if (bytes <= cap) {
       used = 0;
       return LORADS_OK;
     }
     release();
-    if (cudaMalloc((void**)&base, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      base = nullptr;
-      return LORADS_ERR_NOMEM;
-    }
+    base = static_cast<char*>(al.get(bytes));
+    if (!base) return LORADS_ERR_NOMEM;
+    owner = al;
     cap = bytes;
     used = 0;
     return LORADS_OK;
@@ -75,11 +118,13 @@ struct lorads_problem {
   std::vector<Rank1Term> rank1;
   std::vector<double> b;
   bool has_b = false;
-  // Phase II start (phase1 == 0)
+  // Phase II start (phase1 == 0): lorads_set_start (V = U) or lorads_set_state (a resume)
   int32_t start_r = 0;
-  std::vector<double> start_U, start_lam;
+  std::vector<double> start_U, start_V, start_lam;
   double start_rho = 0.0;
   bool has_start = false;
+  bool start_resume = false;
+  lorads_state start_state{};
   // device problem
   bool assembled = false;
   int assemble_status = LORADS_OK;
@@ -101,6 +146,7 @@ struct lorads_problem {
   int sol_r = 0, sol_ld = 0;
   bool has_solution = false;
   lorads_result last{};
+  SolveOut last_out{};
 };
 
 // ---------------------------------------------------------------------------------------
@@ -151,7 +197,7 @@ static void build_sym_csr(int64_t n, std::vector<SymEntry>& ent, std::vector<int
 }
 
 // assemble the device form of (C, A, b)
-static int assemble(lorads_problem* p) {
+static int assemble(lorads_problem* p, const DevAlloc& al) {
   if (p->assembled) return p->assemble_status;
   if (!p->has_b) return LORADS_ERR_STATE;
   if (cudaSetDevice(p->device) != cudaSuccess) return check_cuda(cudaGetLastError());
@@ -255,7 +301,7 @@ static int assemble(lorads_problem* p) {
                  Arena::need(A_val.size(), 4) + Arena::need(C_col.size(), 4) +
                  Arena::need(C_val.size(), 8) + Arena::need(C_val.size(), 4) +
                  Arena::need(n, 8) + Arena::need(n, 4) * 2 + Arena::need(n, 8) + 4096;
-  int st = p->prob_mem.reserve(bytes);
+  int st = p->prob_mem.reserve(bytes, al);
   if (st != LORADS_OK) return st;
   Arena& a = p->prob_mem;
   auto up = [](void* d, const void* h, size_t b) {
@@ -385,6 +431,22 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   dv.phase1 = prm->phase1 ? 1 : 0;
   dv.r_start = p->start_r;
   dv.rho0 = p->start_rho > 0 ? p->start_rho : 100.0;
+  dv.prev_dinf0 = std::numeric_limits<double>::quiet_NaN();
+  if (!dv.phase1 && p->has_start && p->start_resume) {
+    // continuation of a checkpointed Phase II: its gamma, counters and final-test schedule
+    const lorads_state& q = p->start_state;
+    dv.resume = 1;
+    dv.gamma = q.gamma;
+    dv.k0 = q.admm_iters;
+    dv.next_test0 = q.next_dual_test;
+    dv.cg0 = q.cg_iters;
+    dv.hess0 = q.hessian_applies;
+    dv.outer0 = q.alm_outer;
+    dv.lbfgs0 = q.lbfgs_iters;
+    dv.growths0 = q.rank_growths;
+    dv.prev_dinf0 = q.prev_d_infeas;
+    dv.sigma0 = q.sigma;
+  }
   dv.time_limit_ns = (long long)(prm->time_limit_s * 1e9);
   dv.team_mult = prm->team_mult > 0 ? prm->team_mult : 1;
   if (dv.team_mult != 1 && dv.team_mult != 2 && dv.team_mult != 4 && dv.team_mult != 8)
@@ -403,11 +465,32 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   return LORADS_OK;
 }
 
+// uploads the Phase II start in the solver's layout (n x round4(r) row-major, zero padding):
+// U, V for a resume (else the kernel sets V = U), lambda (zero when not given)
+static int upload_start(const lorads_problem* p, double* dU, double* dV, double* dlam,
+                        cudaStream_t s) {
+  const int64_t n = p->n, m = p->m;
+  const int r = p->start_r, ld = round4(r);
+  CU(cudaMemsetAsync(dU, 0, (size_t)n * ld * 8, s));
+  CU(cudaMemcpy2DAsync(dU, (size_t)ld * 8, p->start_U.data(), (size_t)r * 8, (size_t)r * 8,
+                       (size_t)n, cudaMemcpyHostToDevice, s));
+  if (p->start_resume) {
+    CU(cudaMemsetAsync(dV, 0, (size_t)n * ld * 8, s));
+    CU(cudaMemcpy2DAsync(dV, (size_t)ld * 8, p->start_V.data(), (size_t)r * 8, (size_t)r * 8,
+                         (size_t)n, cudaMemcpyHostToDevice, s));
+  }
+  if (!p->start_lam.empty())
+    CU(cudaMemcpyAsync(dlam, p->start_lam.data(), m * 8, cudaMemcpyHostToDevice, s));
+  else
+    CU(cudaMemsetAsync(dlam, 0, m * 8, s));
+  return LORADS_OK;
+}
+
 // allocates (or reuses) p's state arena, lays out the solver arrays, uploads the Phase II
 // start if any and the argument block, and clears what must start at zero
 template <typename T>
 static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
-                         SolverArgs<T>& h, SolverArgs<T>** dargs_out) {
+                         const DevAlloc& al, SolverArgs<T>& h, SolverArgs<T>** dargs_out) {
   const int64_t n = p->n, m = p->m;
   const int rmax = std::max(dv.rank_cap, dv.phase1 ? 0 : p->start_r);
   const long long ld_cap = round4(rmax);
@@ -421,7 +504,7 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
                  Arena::need(1, sizeof(SolverArgs<T>)) + Arena::need(1, sizeof(SolveOut)) +
                  Arena::need(1, sizeof(GridCtl)) +
                  Arena::need((size_t)dev_sms * 8 * MAXRED * 3, 8) + Arena::need(4, 4) + 4096;
-  int st = p->state_mem.reserve(bytes);
+  int st = p->state_mem.reserve(bytes, al);
   if (st != LORADS_OK) return st;
   Arena& a = p->state_mem;
   h = SolverArgs<T>{};
@@ -464,17 +547,8 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   p->has_solution = false;
   // Phase II start supplied by the caller
   if (!dv.phase1) {
-    const int r = p->start_r, ld = round4(r);
-    std::vector<double> Upad((size_t)n * ld, 0.0);
-    for (int64_t j = 0; j < n; ++j)
-      for (int c = 0; c < r; ++c) Upad[(size_t)j * ld + c] = p->start_U[(size_t)j * r + c];
-    CU(cudaMemcpyAsync(h.U, Upad.data(), Upad.size() * 8, cudaMemcpyHostToDevice, s));
-    // the pageable source must stay alive until the copy is done
-    CU(cudaStreamSynchronize(s));
-    if (!p->start_lam.empty())
-      CU(cudaMemcpyAsync(h.lam, p->start_lam.data(), m * 8, cudaMemcpyHostToDevice, s));
-    else
-      CU(cudaMemsetAsync(h.lam, 0, m * 8, s));
+    st = upload_start(p, h.U, h.V, h.lam, s);
+    if (st != LORADS_OK) return st;
   }
   CU(cudaMemcpyAsync(dargs, &h, sizeof(h), cudaMemcpyHostToDevice, s));
   // the report starts as a device error: a solve that never runs (a launch that failed, a
@@ -518,6 +592,7 @@ static void to_result(const SolveOut& out, lorads_result& r) {
 
 static void record_solution(lorads_problem* p, const SolveOut& out, const lorads_result& r) {
   p->last = r;
+  p->last_out = out;
   p->sol_r = out.rank;
   p->sol_ld = out.ld;
   p->has_solution = out.ld > 0;
@@ -531,7 +606,7 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   if (st != LORADS_OK) return st;
   SolverArgs<T> h;
   SolverArgs<T>* dargs = nullptr;
-  st = prepare_state<T>(p, dv, s, h, &dargs);
+  st = prepare_state<T>(p, dv, s, DevAlloc::from(prm, s), h, &dargs);
   if (st != LORADS_OK) return st;
   int dev_sms = 0;
   CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
@@ -583,16 +658,17 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   std::vector<std::pair<double, int>> order(count);
   lorads_params q = *prm;
   q.team_mult = team_mult;
+  const DevAlloc al = DevAlloc::from(prm, s);
   for (int i = 0; i < count; ++i) {
     lorads_problem* p = ps[i];
     if (p->device != device) return LORADS_ERR_ARG;
-    int st = assemble(p);
+    int st = assemble(p, al);
     if (st != LORADS_OK) return st;
     DevParams dv;
     st = fill_params(p, &q, dv);
     if (st != LORADS_OK) return st;
     SolverArgs<T>* unused = nullptr;
-    st = prepare_state<T>(p, dv, s, hs[i], &unused);
+    st = prepare_state<T>(p, dv, s, al, hs[i], &unused);
     if (st != LORADS_OK) return st;
     // work estimate: rows times (A + C entries per row), for largest-first scheduling
     order[i] = {-(double)p->n * (double)(p->C_row.size() + p->A_con.size() + p->n) / p->n, i};
@@ -617,8 +693,9 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   const size_t c_bytes = (sizeof(GridCtl) * groups + 255) / 256 * 256;
   const size_t s_bytes = (sizeof(int) * groups + 255) / 256 * 256;
   const size_t p_bytes = sizeof(double) * (size_t)grid * MAXRED * (group > 1 ? 1 : 0);
-  char* base = nullptr;
-  CU(cudaMalloc((void**)&base, a_bytes + 256 + c_bytes + s_bytes + p_bytes));
+  const size_t base_bytes = a_bytes + 256 + c_bytes + s_bytes + p_bytes;
+  char* base = static_cast<char*>(al.get(base_bytes));
+  if (!base) return LORADS_ERR_NOMEM;
   SolverArgs<T>* dargs = reinterpret_cast<SolverArgs<T>*>(base);
   int* dqueue = reinterpret_cast<int*>(base + a_bytes);
   GridCtl* dctls = reinterpret_cast<GridCtl*>(base + a_bytes + 256);
@@ -673,7 +750,9 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   if (gexec) cudaGraphExecDestroy(gexec);
   if (graph) cudaGraphDestroy(graph);
   if (cap) cudaStreamDestroy(cap);
-  cudaFree(base);
+  // every use of base has finished (the stream was synchronized, or nothing ran)
+  cudaStreamSynchronize(s);
+  al.put(base, base_bytes);
   return st;
 }
 
@@ -830,6 +909,8 @@ int lorads_set_start(lorads_problem* p, int32_t r, const double* U0, const doubl
   else
     p->start_lam.clear();
   p->start_rho = rho0;
+  p->start_V.clear();
+  p->start_resume = false;
   p->has_start = true;
   return LORADS_OK;
 }
@@ -845,7 +926,9 @@ static int solve_impl(lorads_problem* p, const lorads_params* prm, void* stream,
   if (prm->precision != LORADS_PREC_FP64 && prm->precision != LORADS_PREC_MIXED)
     return LORADS_ERR_ARG;
   if (!(prm->tol > 0) || prm->max_admm_iter < 1 || prm->cg_max_iter < 1) return LORADS_ERR_ARG;
-  int st = assemble(p);
+  const DevAlloc al = DevAlloc::from(prm, stream);
+  if (!al.valid()) return LORADS_ERR_ARG;
+  int st = assemble(p, al);
   if (st != LORADS_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (prm->precision == LORADS_PREC_MIXED) return run_solve<float>(p, prm, s, res);
@@ -873,6 +956,7 @@ int lorads_solve_batch(lorads_problem* const* ps, int32_t count, const lorads_pa
   if (prm->precision != LORADS_PREC_FP64 && prm->precision != LORADS_PREC_MIXED)
     return LORADS_ERR_ARG;
   if (!(prm->tol > 0) || prm->max_admm_iter < 1 || prm->cg_max_iter < 1) return LORADS_ERR_ARG;
+  if (!DevAlloc::from(prm, stream).valid()) return LORADS_ERR_ARG;
   if (res) std::memset(res, 0, sizeof(lorads_result) * count);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const bool mixed = prm->precision == LORADS_PREC_MIXED;
@@ -928,6 +1012,71 @@ int lorads_get_solution(const lorads_problem* p, double* U, double* V, double* U
   return LORADS_OK;
 }
 
+int lorads_get_state(const lorads_problem* p, lorads_state* st, double* U, double* V,
+                     double* lambda) {
+  if (!p) return LORADS_ERR_ARG;
+  const SolveOut& o = p->last_out;
+  if (!p->has_solution || o.phase != 2 ||
+      (o.status != ST_OK && o.status != ST_MAXITER && o.status != ST_TIMEOUT))
+    return LORADS_ERR_STATE;
+  if (st) {
+    *st = lorads_state{};
+    st->n = p->n;
+    st->m = p->m;
+    st->phase = 2;
+    st->rank = o.rank;
+    st->admm_iters = o.admm_iters;
+    st->next_dual_test = o.next_dual_test;
+    st->cg_iters = o.cg_iters;
+    st->hessian_applies = o.hess_applies;
+    st->alm_outer = o.alm_outer;
+    st->lbfgs_iters = o.lbfgs_iters;
+    st->rank_growths = o.growths;
+    st->rho = o.rho;
+    st->gamma = o.gamma;
+    st->sigma = o.sigma;
+    st->prev_d_infeas = o.prev_dinf;
+  }
+  const size_t r = (size_t)p->sol_r, ld = (size_t)p->sol_ld;
+  if (U) CU(cudaMemcpy2D(U, r * 8, p->dU, ld * 8, r * 8, (size_t)p->n, cudaMemcpyDeviceToHost));
+  if (V) CU(cudaMemcpy2D(V, r * 8, p->dV, ld * 8, r * 8, (size_t)p->n, cudaMemcpyDeviceToHost));
+  if (lambda) CU(cudaMemcpy(lambda, p->dlam, (size_t)p->m * 8, cudaMemcpyDeviceToHost));
+  return LORADS_OK;
+}
+
+int lorads_set_state(lorads_problem* p, const lorads_state* st, const double* U, const double* V,
+                     const double* lambda) {
+  if (!p || !st || !U || !V) return LORADS_ERR_ARG;
+  if (st->n != p->n || st->m != p->m || st->phase != 2) return LORADS_ERR_ARG;
+  if (st->rank < 1 || st->rank > std::min<int64_t>(p->n, 256)) return LORADS_ERR_ARG;
+  if (!(st->rho > 0) || !std::isfinite(st->rho) || !(st->gamma > 0) || !std::isfinite(st->gamma))
+    return LORADS_ERR_ARG;
+  if (!std::isfinite(st->sigma) || (!std::isnan(st->prev_d_infeas) && !(st->prev_d_infeas >= 0)))
+    return LORADS_ERR_ARG;
+  if (std::isinf(st->prev_d_infeas)) return LORADS_ERR_ARG;
+  if (st->admm_iters < 0 || st->next_dual_test < 0 || st->cg_iters < 0 ||
+      st->hessian_applies < 0 || st->alm_outer < 0 || st->lbfgs_iters < 0 || st->rank_growths < 0)
+    return LORADS_ERR_ARG;
+  const size_t nr = (size_t)p->n * st->rank;
+  for (size_t t = 0; t < nr; ++t)
+    if (!is_finite_value(U[t]) || !is_finite_value(V[t])) return LORADS_ERR_ARG;
+  if (lambda)
+    for (int64_t i = 0; i < p->m; ++i)
+      if (!is_finite_value(lambda[i])) return LORADS_ERR_ARG;
+  p->start_r = st->rank;
+  p->start_U.assign(U, U + nr);
+  p->start_V.assign(V, V + nr);
+  if (lambda)
+    p->start_lam.assign(lambda, lambda + p->m);
+  else
+    p->start_lam.clear();
+  p->start_rho = st->rho;
+  p->start_state = *st;
+  p->start_resume = true;
+  p->has_start = true;
+  return LORADS_OK;
+}
+
 void lorads_destroy(lorads_problem* p) {
   if (!p) return;
   p->prob_mem.release();
@@ -952,9 +1101,10 @@ const char* lorads_status_string(int code) {
   }
 }
 
-void lorads_struct_sizes(int64_t* params_bytes, int64_t* result_bytes) {
+void lorads_struct_sizes(int64_t* params_bytes, int64_t* result_bytes, int64_t* state_bytes) {
   if (params_bytes) *params_bytes = (int64_t)sizeof(lorads_params);
   if (result_bytes) *result_bytes = (int64_t)sizeof(lorads_result);
+  if (state_bytes) *state_bytes = (int64_t)sizeof(lorads_state);
 }
 
 // ---- operators -----------------------------------------------------------------------
@@ -962,7 +1112,7 @@ static int op_prepare(lorads_problem* p, int32_t prec, int32_t r, int32_t ld) {
   if (!p || (prec != LORADS_PREC_FP64 && prec != LORADS_PREC_MIXED)) return LORADS_ERR_ARG;
   if (r <= 0 || ld < r || (ld % 4) != 0 || team_size_for(ld) * KMAX * CHUNK < ld)
     return LORADS_ERR_ARG;
-  return assemble(p);
+  return assemble(p, DevAlloc{});
 }
 
 static int op_grid(const lorads_problem* p) {
@@ -1091,6 +1241,9 @@ template <typename T>
 static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStream_t s,
                             double* U_hat, int64_t ldu, double* y, lorads_result* res) {
   const int64_t n = p->n, m = p->m;
+  // the solve's state lives in the shared scratch array: an earlier solve's state in p's
+  // arena no longer belongs to the latest solve
+  p->has_solution = false;
   DevParams dv;
   lorads_params q = *prm;
   q.team_mult = 1;
@@ -1148,14 +1301,8 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
     return LORADS_ERR_TOO_LARGE;
   h.out = dout;
   if (!dv.phase1) {
-    const int r = p->start_r, ld = round4(r);
-    CU(cudaMemsetAsync(h.U, 0, NS * sizeof(double), s));
-    CU(cudaMemcpy2DAsync(h.U, (size_t)ld * 8, p->start_U.data(), (size_t)r * 8, (size_t)r * 8,
-                         (size_t)n, cudaMemcpyHostToDevice, s));
-    if (!p->start_lam.empty())
-      CU(cudaMemcpyAsync(h.lam, p->start_lam.data(), m * 8, cudaMemcpyHostToDevice, s));
-    else
-      CU(cudaMemsetAsync(h.lam, 0, m * 8, s));
+    st = upload_start(p, h.U, h.V, h.lam, s);
+    if (st != LORADS_OK) return st;
   }
   // what must start at zero: the report, the grid barrier and the CTA queue
   CU(cudaMemcpyAsync(dargs, &h, sizeof(h), cudaMemcpyHostToDevice, s));
@@ -1193,27 +1340,8 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
     CU(cudaStreamSynchronize(s));
   }
   if (res) {
-    lorads_result r{};
-    r.status = out.status;
-    r.rank = out.rank;
-    r.objective = out.objective;
-    r.dual_objective = out.dual_objective;
-    r.r_P = out.r_P;
-    r.r_P_split = out.r_P_split;
-    r.r_stop = out.r_stop;
-    r.r_D = out.r_D;
-    r.gap = out.gap;
-    r.rho = out.rho;
-    r.gamma = out.gamma;
-    r.sigma = out.sigma;
-    r.admm_iters = out.admm_iters;
-    r.cg_iters = out.cg_iters;
-    r.hessian_applies = out.hess_applies;
-    r.alm_outer = out.alm_outer;
-    r.lbfgs_iters = out.lbfgs_iters;
-    r.rank_growths = out.growths;
-    r.time_phase1_s = out.t_phase1_ns * 1e-9;
-    r.time_phase2_s = out.t_phase2_ns * 1e-9;
+    lorads_result r;
+    to_result(out, r);
     *res = r;
   }
   return out.status;

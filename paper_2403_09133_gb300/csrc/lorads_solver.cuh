@@ -39,13 +39,21 @@ struct DevParams {
   int lanczos_steps;
   int dinf_every;
   double escape_scale;   // Phase II rank growth along the lambda_min eigenvector (0: off)
+  // continuation of a checkpointed Phase II (resume = 1): V is given apart from U, and the
+  // iteration counter, the final-test schedule and the reported counters go on from here
+  int resume;
+  int k0, next_test0, cg0, hess0, outer0, lbfgs0, growths0;
+  double prev_dinf0, sigma0;
 };
 
 constexpr int LANCZOS_MAX = 512;   // Lanczos steps of one lambda_min estimate, at most
 
 struct SolveOut {
   int status, rank, ld, admm_iters, cg_iters, hess_applies, alm_outer, lbfgs_iters, growths;
+  int phase;            // 2 once Phase II has started (U, V, lambda form a Phase II iterate)
+  int next_dual_test;   // final-test schedule at exit (continued by a resume)
   int pad;
+  double prev_dinf;
   double objective, dual_objective, r_P, r_P_split, r_stop, r_D, gap, rho, gamma, sigma;
   double p_infeas, d_infeas, lambda_min;
   long long t_phase1_ns, t_phase2_ns;
@@ -168,11 +176,14 @@ struct Solver {
   int lmin_at;        // ... and the Phase II iteration count it belongs to (-1: none)
   double uh_norm2;    // ||U_hat||_F^2 from the latest gap test
   double rs_num, rs_den;   // ||V^{k+1} - V^k||^2, ||V^k||^2 of the row-local loop (< 0: unused)
+  int ndt;            // first Phase II iteration at which the dual-infeasibility test may run
+  double pdinf;       // dual infeasibility of the latest failed test since the last growth
 
   __device__ Solver(const SolverArgs<T>& a, Scope& s)
       : A(a), sc(s), P(a.P), prm(a.prm), n(a.P.n), m(a.P.m), r(0), ld(0), status(ST_OK),
         cg_iters(0), hess(0), admm_iters(0), alm_outer(0), lbfgs_iters(0), growths(0),
-        last_rs(0.0), last_lmin(NAN), lmin_at(-1), uh_norm2(0.0), rs_num(-1.0), rs_den(0.0) {}
+        last_rs(0.0), last_lmin(NAN), lmin_at(-1), uh_norm2(0.0), rs_num(-1.0), rs_den(0.0),
+        ndt(0), pdinf(NAN) {}
 
   __device__ void set_rank(int rr) {
     r = rr;
@@ -811,18 +822,18 @@ struct Solver {
   // infeasibility that fell by less than 10% since the previous failed test (a stationary
   // point of the rank-r problem) grows the rank along the eigenvector of lambda_min.
   // Returns 1 (done), 0 (continue), 2 (rank grown: U, V changed), -1 (device error).
-  __device__ int final_test(int& next_dual_test, double& prev_dinf) {
+  __device__ int final_test() {
     double gap;
     if (!gap_check(gap)) return -1;
     if (!(fabs(gap) <= prm.tol)) return 0;
     if (!prm.kkt_dinf) return 1;
-    if (admm_iters < next_dual_test) return 0;
+    if (admm_iters < ndt) return 0;
     if (!lanczos_lambda_min(last_lmin)) return -1;
     lmin_at = admm_iters;
     const double dinf = fmax(0.0, -last_lmin) / (1.0 + P.c_one);
     if (dinf <= prm.tol) return 1;
-    next_dual_test = admm_iters + max(prm.dinf_every, admm_iters / 10);
-    if (prev_dinf == prev_dinf && dinf > 0.9 * prev_dinf && prm.escape_scale > 0.0 &&
+    ndt = admm_iters + max(prm.dinf_every, admm_iters / 10);
+    if (pdinf == pdinf && dinf > 0.9 * pdinf && prm.escape_scale > 0.0 &&
         r < prm.rank_cap) {
       double zn2 = 0.0, lm;
       if (!lanczos_lambda_min(lm, true, &zn2)) return -1;
@@ -832,19 +843,17 @@ struct Solver {
       if (r_new > prm.rank_cap) r_new = prm.rank_cap;
       if (!grow_rank_phase2(r_new, A.Y + 2 * K, zn2)) return -1;
       ++growths;
-      prev_dinf = NAN;
+      pdinf = NAN;
       return 2;
     }
-    prev_dinf = dinf;
+    pdinf = dinf;
     return 0;
   }
 
   __device__ bool phase2(double rho, double& rho_out) {
     if (P.a_diag_only) return phase2_local(rho, rho_out);
     const double gamma = prm.gamma;
-    int next_dual_test = 0;
-    double prev_dinf = NAN;
-    for (int k = 0; k < prm.max_admm_iter; ++k) {
+    for (int k = admm_iters; k < prm.max_admm_iter; ++k) {
       double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
       double dv[2];
       // U-step: eq. linU with W = V^k, CG warm-started from V^k
@@ -865,7 +874,7 @@ struct Solver {
       last_rs = rs;
       if (!(rp == rp) || !(rs == rs)) { status = ST_NAN; break; }
       if (rph <= prm.tol) {
-        const int t = final_test(next_dual_test, prev_dinf);
+        const int t = final_test();
         if (t < 0) return false;
         if (t == 1) {
           rho_out = rho;
@@ -1095,11 +1104,9 @@ struct Solver {
     const double gamma = prm.gamma;
     const double tol2_primal = prm.tol * (1.0 + P.b_inf) * prm.tol * (1.0 + P.b_inf);
     const bool shadow = (const void*)A.Ut != (const void*)A.U;
-    int next_dual_test = 0;
-    double prev_dinf = NAN;
     double g3[3];
     if (!local_prologue(rho, gamma, g3)) return false;
-    for (int k = 0; k < prm.max_admm_iter; ++k) {
+    for (int k = admm_iters; k < prm.max_admm_iter; ++k) {
       const bool exact = (k + 1) % 32 == 0;
       // U-step: CG on eq. linU (W = V^k) from the R_0 of the previous pass
       int it;
@@ -1200,7 +1207,7 @@ struct Solver {
       rs_den = v[3];
       if (!(v[0] == v[0]) || !(v[2] == v[2])) { status = ST_NAN; break; }
       if (v[1] <= tol2_primal) {
-        const int t = final_test(next_dual_test, prev_dinf);
+        const int t = final_test();
         if (t < 0) return false;
         if (t == 1) {
           rho_out = rho;
@@ -1630,16 +1637,32 @@ struct Solver {
       rho = fmin(prm.h * sigma, prm.rho_max);
     } else {
       rho = prm.rho0;
+      if (prm.resume) {
+        admm_iters = prm.k0;
+        ndt = prm.next_test0;
+        pdinf = prm.prev_dinf0;
+        cg_iters = prm.cg0;
+        hess = prm.hess0;
+        alm_outer = prm.outer0;
+        lbfgs_iters = prm.lbfgs0;
+        growths = prm.growths0;
+        sigma = prm.sigma0;
+      }
     }
-    // switch: V = U (Algorithm 2), shadows
+    // switch: V = U (Algorithm 2), or the checkpointed V of a resume; shadows
     for (int j = tm.id; j < n; j += tm.count) {
-      Frag<double> u;
+      Frag<double> u, w;
       frag_load(u, A.U, j, ld, tm);
-      frag_store(u, A.V, j, ld, tm);
+      if (prm.resume) frag_load(w, A.V, j, ld, tm);
+      else {
+        w = u;
+        frag_store(u, A.V, j, ld, tm);
+      }
       if ((const void*)A.Ut != (const void*)A.U) {
         Frag<T> s;
         frag_convert(s, u);
         frag_store(s, A.Ut, j, ld, tm);
+        frag_convert(s, w);
         frag_store(s, A.Vt, j, ld, tm);
       }
     }
@@ -1669,6 +1692,9 @@ struct Solver {
     o->alm_outer = alm_outer;
     o->lbfgs_iters = lbfgs_iters;
     o->growths = growths;
+    o->phase = have ? 2 : 1;
+    o->next_dual_test = ndt;
+    o->prev_dinf = pdinf;
     o->rho = rho;
     o->gamma = prm.gamma;
     o->sigma = sigma;

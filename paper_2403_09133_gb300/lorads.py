@@ -32,6 +32,11 @@ LORADS_PREC_MIXED = 1
 
 _i32, _i64, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
 
+# lorads_alloc_fn / lorads_free_fn
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                           ctypes.c_void_p)
+
 
 class lorads_params(ctypes.Structure):
     _fields_ = [
@@ -46,6 +51,7 @@ class lorads_params(ctypes.Structure):
         ("threads", _i32), ("grid", _i32), ("team_mult", _i32),
         ("kkt_dinf", _i32), ("lanczos_steps", _i32), ("dinf_every", _i32),
         ("escape_scale", _f64), ("group", _i32),
+        ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 
 
@@ -57,6 +63,19 @@ class lorads_result(ctypes.Structure):
         ("cg_iters", _i32), ("hessian_applies", _i32), ("alm_outer", _i32),
         ("lbfgs_iters", _i32), ("rank_growths", _i32), ("time_phase1_s", _f64),
         ("time_phase2_s", _f64), ("p_infeas", _f64), ("d_infeas", _f64), ("lambda_min", _f64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class lorads_state(ctypes.Structure):
+    _fields_ = [
+        ("n", _i64), ("m", _i64), ("phase", _i32), ("rank", _i32), ("admm_iters", _i32),
+        ("next_dual_test", _i32), ("cg_iters", _i32), ("hessian_applies", _i32),
+        ("alm_outer", _i32), ("lbfgs_iters", _i32), ("rank_growths", _i32),
+        ("reserved", _i32), ("rho", _f64), ("gamma", _f64), ("sigma", _f64),
+        ("prev_d_infeas", _f64),
     ]
 
     def as_dict(self) -> dict:
@@ -95,7 +114,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                       P, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
         "lorads_destroy": (None, [P]),
         "lorads_status_string": (ctypes.c_char_p, [_i32]),
-        "lorads_struct_sizes": (None, [ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+        "lorads_struct_sizes": (None, [ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                       ctypes.POINTER(_i64)]),
+        "lorads_get_state": (_i32, [P, ctypes.POINTER(lorads_state), P, P, P]),
+        "lorads_set_state": (_i32, [P, ctypes.POINTER(lorads_state), P, P, P]),
         "lorads_solve_static": (_i32, [P, ctypes.POINTER(lorads_params), P, P, _i64, P,
                                        ctypes.POINTER(lorads_result)]),
         "lorads_op_sddmm": (_i32, [P, _i32, _i32, _i32, P, P, P, P]),
@@ -114,10 +136,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    pb, rb = _i64(), _i64()
-    lib.lorads_struct_sizes(ctypes.byref(pb), ctypes.byref(rb))
-    if pb.value != ctypes.sizeof(lorads_params) or rb.value != ctypes.sizeof(lorads_result):
-        raise RuntimeError("lorads_params / lorads_result layout mismatch with liblorads.so")
+    pb, rb, sb = _i64(), _i64(), _i64()
+    lib.lorads_struct_sizes(ctypes.byref(pb), ctypes.byref(rb), ctypes.byref(sb))
+    if (pb.value != ctypes.sizeof(lorads_params) or rb.value != ctypes.sizeof(lorads_result)
+            or sb.value != ctypes.sizeof(lorads_state)):
+        raise RuntimeError("lorads_params / lorads_result / lorads_state layout mismatch "
+                           "with liblorads.so")
     _lib = lib
     return lib
 
@@ -211,8 +235,78 @@ def lorads_get_solution(p, n: int, m: int) -> dict:
     return dict(U=U, V=V, U_hat=Uh, y=y, rank=r.value)
 
 
+def lorads_get_state(p, n: int, m: int) -> dict:
+    """Checkpoint of the last solve: the lorads_state fields plus U, V (n x rank) and lam."""
+    lib = load_library()
+    st = lorads_state()
+    _check(lib.lorads_get_state(p, ctypes.byref(st), None, None, None), "lorads_get_state")
+    U = np.empty((n, st.rank)); V = np.empty((n, st.rank)); lam = np.empty(m)
+    _check(lib.lorads_get_state(p, ctypes.byref(st), U.ctypes.data_as(ctypes.c_void_p),
+                                V.ctypes.data_as(ctypes.c_void_p),
+                                lam.ctypes.data_as(ctypes.c_void_p)), "lorads_get_state")
+    out = st.as_dict()
+    out.update(U=U, V=V, lam=lam)
+    return out
+
+
+def lorads_set_state(p, state: dict) -> int:
+    """Start of the next phase1 = 0 solve from a checkpoint dict (lorads_get_state's form)."""
+    st = lorads_state()
+    for name, _ in lorads_state._fields_:
+        if name in state:
+            setattr(st, name, state[name])
+    U, Up = _host(state["U"], np.float64)
+    V, Vp = _host(state["V"], np.float64)
+    lp = None
+    if state.get("lam") is not None:
+        lam, lp = _host(state["lam"], np.float64)
+    st.rank = U.shape[1] if U.ndim == 2 else st.rank
+    return load_library().lorads_set_state(p, ctypes.byref(st), Up, Vp, lp)
+
+
 def lorads_destroy(p) -> None:
     load_library().lorads_destroy(p)
+
+
+class TorchAllocator:
+    """lorads_params dev_alloc / dev_free backed by PyTorch's caching allocator.
+
+    The library's device arenas (the problem's device form, the solver state, a batch's
+    argument block) then come from the same pool as the caller's tensors.  The object must
+    outlive every problem whose memory it allocated (lorads_destroy returns that memory
+    through it); Problem keeps a reference for that reason."""
+
+    def __init__(self, device=None):
+        import torch
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.bytes_live = 0
+        self.allocs = 0
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                ptr = int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                             int(stream or 0)))
+            except Exception:
+                return None
+            self.bytes_live += int(nbytes)
+            self.allocs += 1
+            return ptr
+
+        def _free(ptr, nbytes, stream, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                return
+            self.bytes_live -= int(nbytes)
+
+        self._alloc = ALLOC_FN(_alloc)
+        self._free = FREE_FN(_free)
+
+    def install(self, prm: lorads_params) -> lorads_params:
+        prm.dev_alloc = self._alloc
+        prm.dev_free = self._free
+        prm.alloc_ctx = None
+        return prm
 
 
 def _stream_ptr(stream):
@@ -241,8 +335,9 @@ def lorads_op_hessian(p, prec: int, r: int, ld: int, rho: float, gamma: float, V
 class Problem:
     """Owns a lorads_problem handle loaded with (C, A, b) of an SDPInstance."""
 
-    def __init__(self, inst):
+    def __init__(self, inst, allocator: Optional[TorchAllocator] = None):
         self.n, self.m = int(inst.n), int(inst.m)
+        self.allocator = allocator
         self.handle = lorads_create(self.n, self.m)
         _check(lorads_set_C(self.handle, inst.C_row, inst.C_col, inst.C_val), "lorads_set_C")
         _check(lorads_add_A_sparse(self.handle, inst.A_con, inst.A_row, inst.A_col, inst.A_val),
@@ -253,6 +348,8 @@ class Problem:
 
     def params(self, **kw) -> lorads_params:
         prm = lorads_default_params()
+        if self.allocator is not None:
+            self.allocator.install(prm)
         for k, v in kw.items():
             if not hasattr(prm, k):
                 raise AttributeError(f"lorads_params has no field {k}")
@@ -265,6 +362,21 @@ class Problem:
 
     def solution(self) -> dict:
         return lorads_get_solution(self.handle, self.n, self.m)
+
+    def get_state(self) -> dict:
+        return lorads_get_state(self.handle, self.n, self.m)
+
+    def set_state(self, state: dict) -> None:
+        _check(lorads_set_state(self.handle, state), "lorads_set_state")
+
+    def save_state(self, path: str) -> None:
+        """Writes the checkpoint of the last solve to an .npz file."""
+        np.savez(path, **self.get_state())
+
+    def load_state(self, path: str) -> None:
+        """Makes an .npz checkpoint the start of the next phase1 = 0 solve."""
+        with np.load(path) as z:
+            self.set_state({k: (z[k] if z[k].ndim else z[k].item()) for k in z.files})
 
     def close(self):
         if self.handle is not None:
@@ -279,9 +391,9 @@ class Problem:
 
 
 def lorads_struct_sizes() -> tuple:
-    pb, rb = _i64(), _i64()
-    load_library().lorads_struct_sizes(ctypes.byref(pb), ctypes.byref(rb))
-    return pb.value, rb.value
+    pb, rb, sb = _i64(), _i64(), _i64()
+    load_library().lorads_struct_sizes(ctypes.byref(pb), ctypes.byref(rb), ctypes.byref(sb))
+    return pb.value, rb.value, sb.value
 
 
 def lorads_solve_static(p, prm: lorads_params, U_hat=None, ldu: int = 0, y=None,

@@ -25,10 +25,17 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_binding_mirrors_structs(lib):
-    pb, rb = ctypes.c_int64(), ctypes.c_int64()
-    lib.lorads_struct_sizes(ctypes.byref(pb), ctypes.byref(rb))
+    pb, rb, sb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib.lorads_struct_sizes(ctypes.byref(pb), ctypes.byref(rb), ctypes.byref(sb))
     assert pb.value == ctypes.sizeof(L.lorads_params)
     assert rb.value == ctypes.sizeof(L.lorads_result)
+    assert sb.value == ctypes.sizeof(L.lorads_state)
+
+
+def test_default_allocator_is_cuda_malloc(lib):
+    # both callbacks NULL: the library's own cudaMalloc / cudaFree
+    p = L.lorads_default_params()
+    assert not p.dev_alloc and not p.dev_free and not p.alloc_ctx
 
 
 def test_binding_exposes_same_names(lib):

@@ -9,6 +9,7 @@ MaxCut SDP (Section 5.3) in min form: min <-L/4, X>, X_jj = 1.
   * Goemans-Williamson: 0.878 SDP <= max cut <= SDP for nonnegative weights.
 Matrix completion (Section 5.4): under exact recovery the optimum is 2 ||M||_*.
 """
+import dataclasses
 import math
 import os
 
@@ -144,3 +145,34 @@ def test_phase2_rank_growth_on_a_stalled_instance():
     lmin = min_eig_dual_slack(sdp, grown["y"])
     assert max(0.0, -lmin) / (1.0 + sdp.c_one) <= 1e-6
     assert grown["objective"] < stalled["objective"] - 1e-3
+
+
+def test_lradmm_resume_repeats_the_uninterrupted_run():
+    """A checkpoint (U^k, V^k, lambda^k, rho, k and the final-test schedule) holds all that
+    Algorithm 1 carries between iterations: continuing from one taken before the first failed
+    dual-infeasibility test, between failed tests and after a Phase II rank growth repeats
+    the uninterrupted run bit for bit.  Rank 2 on a 60-vertex graph stalls (a failed test at
+    k = 409, a second at 987 that grows the rank to 3), so every part of the schedule is used;
+    dropping the remembered dual infeasibility changes the run (the growth comes later)."""
+    sdp = SDP.from_instance(I.maxcut_er(60, 6.0, seed=11))
+    p = Params(r0=2, rank_max=6, max_admm_iter=1500)
+    ph1 = L.lralm(sdp, L.initial_factor(sdp, 2, p.seed), p)
+    rho = min(p.h * ph1["sigma"], p.rho_max)
+    full, conv = L.lradmm(sdp, ph1["U"], ph1["U"], ph1["lam"], rho, p)
+    assert full.U.shape[1] == 3 and full.growths == 1 and not conv
+    for k1 in (300, 700, 1200):
+        part, _ = L.lradmm(sdp, ph1["U"], ph1["U"], ph1["lam"], rho,
+                           dataclasses.replace(p, max_admm_iter=k1))
+        assert part.k == k1
+        res, conv_r = L.lradmm_resume(sdp, part, p)
+        assert conv_r == conv and res.k == full.k and res.cg_iters == full.cg_iters
+        assert res.rho == full.rho and res.growths == full.growths
+        assert np.array_equal(res.U, full.U) and np.array_equal(res.V, full.V)
+        assert np.array_equal(res.lam, full.lam)
+        if k1 == 700:
+            assert part.next_dual_test == 409 + 40 and part.prev_dinf is not None
+            forgetful = dataclasses.replace(part, prev_dinf=None)
+            trace: list = []
+            L.lradmm_resume(sdp, forgetful, p, trace)
+            grown_at = [i["k"] for i in trace if "grow_to" in i]
+            assert grown_at and grown_at[0] > 987
