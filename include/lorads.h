@@ -236,10 +236,12 @@ int lorads_get_solution(const lorads_problem *p, double *U, double *V, double *U
  * before the continuation.  The continuation keeps the iteration counter k (so the rho
  * schedule of Section 5.1, the max_admm_iter cap and the final-test schedule go on where
  * they stopped), the split penalty gamma of the checkpoint, and it reports totals (ADMM, CG,
- * Hessian, Phase I counters) including the checkpointed part.  Its iterates agree with an
- * uninterrupted solve's up to rounding: the resumed solve recomputes the row-local CG's
- * incrementally kept products -(C W) and, in the MIXED form, re-rounds the FP32 shadows of
- * U and V from the FP64 masters.  time_limit_s counts per call. */
+ * Hessian, Phase I counters) including the checkpointed part.  The resumed solve recomputes
+ * the row-local CG's incrementally kept products -(C W) and, in the MIXED form, re-rounds the
+ * FP32 shadows of U and V from the FP64 masters; the uninterrupted solve does the same every
+ * 32 iterations, so from a checkpoint with k a multiple of 32 (same launch geometry) the
+ * continuation repeats the uninterrupted solve bit for bit, and from other k it agrees up
+ * to rounding.  time_limit_s counts per call. */
 typedef struct lorads_state {
   int64_t n, m;            /* order and constraint count of the problem it belongs to         */
   int32_t phase;           /* 2: a Phase II iterate (the only kind lorads_set_state takes)    */
