@@ -178,6 +178,7 @@ def run_gpu(args):
     import torch
     import torch.distributed as dist
     from paper_2403_09133_gb300 import lorads as L
+    from paper_2403_09133_gb300 import shard as S
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -251,10 +252,9 @@ def run_gpu(args):
     t_mixed = max(statistics.median(results["mixed"]["times"]), 1e-12)
     t_fp64 = max(statistics.median(results["fp64"]["times"]), 1e-12)
     t_e2e = statistics.median(e2e_times)
-    if world > 1:
-        tt = torch.tensor([t_mixed, t_fp64, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_mixed, t_fp64, t_e2e = tt.tolist()
+    t_mixed, t_fp64, t_e2e = S.max_over_ranks([t_mixed, t_fp64, t_e2e], device=dev)
+    # the batch is sharded over the ranks (every rank takes part); the rest is rank 0's
+    batch = None if args.no_batch else batch_bench(args, stream, rank, world, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -311,8 +311,8 @@ def run_gpu(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
-    if not args.no_batch:
-        line["batch"] = batch_bench(args, stream)
+    if batch is not None:
+        line["batch"] = batch
     if not args.no_mc:
         line["matrix_completion"] = mc_bench(args, stream)
     if not args.no_learned:
@@ -325,22 +325,29 @@ def run_gpu(args):
     return line
 
 
-def batch_bench(args, stream):
+def batch_bench(args, stream, rank=0, world=1, dev=None):
     """512 uneven ER MaxCuts (n ~ U[64, 2048], degree ~ U[3, 12], seeds 1000+i) in one
-    persistent launch (mixed form, autotuned CTA size and lanes per row), against plain FP64
-    one-problem solves on a sample of 16 of them, scaled to the batch."""
+    persistent launch per GPU (mixed form, autotuned CTA size and lanes per row), against
+    plain FP64 one-problem solves on a sample of 16, scaled to the batch.  With several
+    ranks each solves its share (longest-processing-time partition, no data exchange); the
+    batch time is the maximum over ranks."""
     import torch
     from paper_2403_09133_gb300 import instances as I
     from paper_2403_09133_gb300 import lorads as L
+    from paper_2403_09133_gb300 import shard as S
     insts = I.workload_batch(count=args.batch_count)
-    probs = [L.Problem(x) for x in insts]
+    works = [S.work_estimate(x.n, len(x.C_row) + len(x.A_con)) for x in insts]
+    mine = S.shard(works, rank, world)
+    probs = [L.Problem(insts[i]) for i in mine]
     handles = [p.handle for p in probs]
-    prm = probs[0].params(precision=L.LORADS_PREC_MIXED)
+    prm = L.lorads_default_params()
+    prm.precision = L.LORADS_PREC_MIXED
     res, th, mu = L.lorads_solve_batch(handles, prm, stream)      # tunes + warms up
     prm.threads, prm.team_mult = th, mu
     times = []
     for _ in range(2):
         torch.cuda.synchronize()
+        S.max_over_ranks([0.0], device=dev)                      # start together
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -348,9 +355,10 @@ def batch_bench(args, stream):
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) * 1e-3)
-    t_batch = min(times)
+    t_batch = S.max_over_ranks([min(times)], device=dev)[0]
     sample = list(range(0, len(probs), max(1, len(probs) // 16)))[:16]
-    p64 = probs[0].params(precision=L.LORADS_PREC_FP64)
+    p64 = L.lorads_default_params()
+    p64.precision = L.LORADS_PREC_FP64
     t_seq = 0.0
     for i in sample:
         e0 = torch.cuda.Event(enable_timing=True)
@@ -360,17 +368,20 @@ def batch_bench(args, stream):
         e1.record(stream)
         e1.synchronize()
         t_seq += e0.elapsed_time(e1) * 1e-3
-    t_seq_scaled = t_seq * len(probs) / len(sample)
     for p in probs:
         p.close()
-    return {"count": len(insts), "seconds_one_launch": t_batch,
+    counts = S.sum_over_ranks([
+        t_seq * len(probs) / max(1, len(sample)),
+        sum(r["status"] == 0 for r in res), sum(r["admm_iters"] for r in res),
+        sum(r["rank_growths"] > 0 for r in res)], device=dev)
+    t_seq_scaled = counts[0]
+    return {"count": len(insts), "ranks": world, "seconds_one_launch": t_batch,
             "solves_per_s": len(insts) / t_batch, "tuned_threads": th, "tuned_team_mult": mu,
-            "converged": int(sum(r["status"] == 0 for r in res)),
-            "admm_iters_total": int(sum(r["admm_iters"] for r in res)),
-            "rank_grown_in_phase2": int(sum(r["rank_growths"] > 0 for r in res)),
+            "converged": int(counts[1]), "admm_iters_total": int(counts[2]),
+            "rank_grown_in_phase2": int(counts[3]),
             "plain_fp64_sequential_s_est": t_seq_scaled,
             "speedup_vs_sequential_fp64": t_seq_scaled / t_batch,
-            "sample": f"{len(sample)} one-problem FP64 solves scaled x{len(probs) / len(sample):.0f}"}
+            "sample": f"{len(sample)} one-problem FP64 solves per rank, scaled to its share"}
 
 
 def mc_bench(args, stream):
