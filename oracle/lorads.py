@@ -96,6 +96,8 @@ class Params:
     kkt_dinf: bool = True         # the Appendix B dual infeasibility is part of the stop
     dinf_every: int = 10          # after a failed dual test: wait max(dinf_every, k // 10)
     escape_scale: float = 0.3     # Phase II rank growth along the lambda_min eigenvector
+    subsolver: str = "cg"         # eq. linU / linV: "cg" (Section 4.4) or "row_direct"
+                                  # (exact block solve; every constraint one diagonal entry)
 
 
 # ======================================================================================
@@ -255,6 +257,27 @@ def conjugate_gradient(apply_H: Callable, G, X0, rel_tol: float, abs_floor: floa
     return X, it
 
 
+def row_separable(sdp: SDP) -> bool:
+    """Every constraint is a single diagonal entry, A_i = a_i e_j e_j^T (MaxCut's diag(X) = 1)."""
+    return (sdp.R1 is None and not np.any(sdp.A_off)
+            and np.bincount(sdp.A_con, minlength=sdp.m).max(initial=0) <= 1)
+
+
+def row_block_solve(sdp: SDP, W, G, rho, gamma):
+    """Exact solution of eq. linU / eq. linV for row-separable constraints.  With
+    A_i = a_i e_j e_j^T, <A_i, X W^T> = a_i X_j.W_j, so the matrix rho A^T(A(. W^T)) W + gamma I
+    is block diagonal with the r x r block gamma I + rho s_j W_j W_j^T on row j
+    (s_j = sum of a_i^2 over the constraints on row j, 0 without one).  Section 1 notes that
+    the subproblems may be solved by direct methods as well as by CG; the Sherman-Morrison
+    formula inverts each block:
+        X_j = (G_j - c_j (W_j.G_j) W_j) / gamma,   c_j = rho s_j / (gamma + rho s_j ||W_j||^2)."""
+    s = np.bincount(sdp.A_row, weights=sdp.A_val ** 2, minlength=sdp.n)
+    w2 = np.einsum("ij,ij->i", W, W)
+    wg = np.einsum("ij,ij->i", W, G)
+    c = rho * s / (gamma + rho * s * w2)
+    return (G - (c * wg)[:, None] * W) / gamma
+
+
 def penalty_gamma(sdp: SDP, p: Params) -> float:
     """gamma of eq. prob:penalty.  The paper fixes no value; the U-step moves U along
     -(C + A^T lambda) V / gamma, so gamma is tied to the scale of C through the row-sum
@@ -285,15 +308,24 @@ def admm_iteration(sdp: SDP, st: AdmmState, p: Params) -> dict:
     """One pass of Algorithm 1 (U-step, V-step, dual step) plus the penalty schedule."""
     rho = st.rho
     gamma = penalty_gamma(sdp, p)
-    # U-step: eq. linU, CG warm-started from V^k
+    direct = p.subsolver == "row_direct"
+    if direct and not row_separable(sdp):
+        raise ValueError("row_direct needs every constraint to be one diagonal entry")
+    # U-step: eq. linU, CG warm-started from V^k (or the exact block solve)
     V = st.V
     G = subproblem_rhs(sdp, V, st.lam, rho, gamma)
-    U, itU = conjugate_gradient(lambda X: hessian_apply(sdp, V, X, rho, gamma), G, V,
-                                p.cg_rel_tol, p.cg_abs_floor, p.cg_max_iter)
-    # V-step: eq. linV, CG warm-started from U^{k+1}
+    if direct:
+        U, itU = row_block_solve(sdp, V, G, rho, gamma), 0
+    else:
+        U, itU = conjugate_gradient(lambda X: hessian_apply(sdp, V, X, rho, gamma), G, V,
+                                    p.cg_rel_tol, p.cg_abs_floor, p.cg_max_iter)
+    # V-step: eq. linV, CG warm-started from U^{k+1} (or the exact block solve)
     G = subproblem_rhs(sdp, U, st.lam, rho, gamma)
-    V, itV = conjugate_gradient(lambda X: hessian_apply(sdp, U, X, rho, gamma), G, U,
-                                p.cg_rel_tol, p.cg_abs_floor, p.cg_max_iter)
+    if direct:
+        V, itV = row_block_solve(sdp, U, G, rho, gamma), 0
+    else:
+        V, itV = conjugate_gradient(lambda X: hessian_apply(sdp, U, X, rho, gamma), G, U,
+                                    p.cg_rel_tol, p.cg_abs_floor, p.cg_max_iter)
     # dual step: lambda^{k+1} = lambda^k + rho (A(U^{k+1} V^{k+1 T}) - b)
     e = sdp.A_of(U, V) - sdp.b
     lam = st.lam + rho * e

@@ -30,6 +30,61 @@ def test_cg_maxcut_matches_sherman_morrison(rng):
     np.testing.assert_allclose(U, want, rtol=1e-10, atol=1e-10)
 
 
+def _row_separable_sdp(rng):
+    """n = 7, constraints on rows 0, 1, 2, 4, 6 with a = 1, 2, 0.5, 3, 1 (rows 3 and 5 have
+    none), a random symmetric C."""
+    rows = np.array([0, 1, 2, 4, 6])
+    a = np.array([1.0, 2.0, 0.5, 3.0, 1.0])
+    cr, cc = np.triu_indices(7)
+    keep = rng.random(len(cr)) < 0.5
+    return SDP(7, 5, cr[keep], cc[keep], rng.standard_normal(keep.sum()), np.arange(5), rows,
+               rows, a, rng.standard_normal(5))
+
+
+def test_row_block_solve_matches_dense_solve(rng):
+    """The direct subproblem solve against a dense solve of the nr x nr system built column by
+    column from hessian_apply (non-unit a_i, rows without a constraint)."""
+    sdp = _row_separable_sdp(rng)
+    assert L.row_separable(sdp)
+    r, rho, gamma = 3, 6.0, 0.7
+    W = rng.standard_normal((7, r)); lam = rng.standard_normal(5)
+    G = L.subproblem_rhs(sdp, W, lam, rho, gamma)
+    H = np.zeros((7 * r, 7 * r))
+    for t in range(7 * r):
+        E = np.zeros(7 * r); E[t] = 1.0
+        H[:, t] = L.hessian_apply(sdp, W, E.reshape(7, r), rho, gamma).ravel()
+    want = np.linalg.solve(H, G.ravel()).reshape(7, r)
+    np.testing.assert_allclose(L.row_block_solve(sdp, W, G, rho, gamma), want,
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_row_separable_detection(rng):
+    assert L.row_separable(SDP.from_instance(I.maxcut_er(20, 3.0, seed=1)))
+    assert not L.row_separable(SDP.from_instance(I.matrix_completion(5, 4, 1, 8, seed=1)))
+    assert not L.row_separable(SDP.from_instance(random_general_sdp(6, 4, 2, rng)))
+    with pytest.raises(ValueError):
+        L.admm_iteration(SDP.from_instance(I.matrix_completion(5, 4, 1, 8, seed=1)),
+                         L.AdmmState(U=np.ones((9, 2)), V=np.ones((9, 2)), lam=np.zeros(8),
+                                     rho=1.0), Params(subsolver="row_direct"))
+
+
+@pytest.mark.parametrize("case", ["K10", "torus6x8"])
+def test_row_direct_whole_solve_closed_forms(case):
+    """Algorithm 2 with the direct subproblem solve reaches the closed-form SDP values:
+    K_n: n^2/4; a x b unit torus: n (lambda_max(C_a) + lambda_max(C_b)) / 4."""
+    from oracle import solve
+    if case == "K10":
+        inst, want = I.maxcut_complete(10), 25.0
+    else:
+        inst = I.maxcut_torus(6, 8, seed=None)
+        lmax = lambda k: 4.0 if k % 2 == 0 else 2.0 + 2.0 * math.cos(math.pi / k)
+        want = 48 * (lmax(6) + lmax(8)) / 4
+    sdp = SDP.from_instance(inst)
+    res = solve(sdp, Params(subsolver="row_direct", tol=1e-9, max_admm_iter=6000))
+    assert res["cg_iters"] == 0
+    assert abs(-res["objective"] - want) <= 1e-7 * want
+
+
 def test_cg_two_steps_when_rows_unit(rng):
     """With ||V_i|| = 1 for all i the spectrum is {gamma, gamma + rho}: CG ends in <= 2 steps."""
     sdp = SDP.from_instance(I.maxcut_er(60, 6.0, seed=4))
