@@ -198,8 +198,12 @@ def run_gpu(args):
 
     prob = L.Problem(inst)
     results = {}
-    for form, prec in (("mixed", L.LORADS_PREC_MIXED), ("fp64", L.LORADS_PREC_FP64)):
-        prm = prob.params(precision=prec)
+    forms = (("mixed", L.LORADS_PREC_MIXED, L.LORADS_SUB_CG),
+             ("fp64", L.LORADS_PREC_FP64, L.LORADS_SUB_CG),
+             ("mixed_row_direct", L.LORADS_PREC_MIXED, L.LORADS_SUB_ROW_DIRECT),
+             ("fp64_row_direct", L.LORADS_PREC_FP64, L.LORADS_SUB_ROW_DIRECT))
+    for form, prec, sub in forms:
+        prm = prob.params(precision=prec, subsolver=sub)
         times = []
         res = None
         for it in range(args.warmup + args.steps):
@@ -252,7 +256,10 @@ def run_gpu(args):
     t_mixed = max(statistics.median(results["mixed"]["times"]), 1e-12)
     t_fp64 = max(statistics.median(results["fp64"]["times"]), 1e-12)
     t_e2e = statistics.median(e2e_times)
-    t_mixed, t_fp64, t_e2e = S.max_over_ranks([t_mixed, t_fp64, t_e2e], device=dev)
+    t_mixed_d = max(statistics.median(results["mixed_row_direct"]["times"]), 1e-12)
+    t_fp64_d = max(statistics.median(results["fp64_row_direct"]["times"]), 1e-12)
+    t_mixed, t_fp64, t_e2e, t_mixed_d, t_fp64_d = S.max_over_ranks(
+        [t_mixed, t_fp64, t_e2e, t_mixed_d, t_fp64_d], device=dev)
     # the batch is sharded over the ranks (every rank takes part); the rest is rank 0's
     batch = None if args.no_batch else batch_bench(args, stream, rank, world, dev)
     if rank != 0:
@@ -302,6 +309,17 @@ def run_gpu(args):
                            abs(rf["objective"] - rm["objective"]) / abs(rf["objective"]),
                        "cg_operator_gbs": bytes_fp64 / t_fp64 / 1e9},
         "mixed_speedup_vs_fp64": t_fp64 / t_mixed,
+        # the same workload with the exact row-block subproblem solve instead of CG (every
+        # constraint one diagonal entry; Section 1 admits direct methods for the subproblems)
+        "row_direct": {
+            form: {"ms_per_solve": t * 1e3, "status": r["status"], "admm_iters": r["admm_iters"],
+                   "cg_iters": r["cg_iters"], "objective": r["objective"],
+                   "objective_rel_diff_vs_cg_mixed":
+                       abs(r["objective"] - rm["objective"]) / abs(rm["objective"]),
+                   "r_P": r["r_P"], "gap": r["gap"], "d_infeas": r["d_infeas"],
+                   "speedup_vs_cg_mixed": t_mixed / t}
+            for form, r, t in (("mixed", results["mixed_row_direct"]["res"], t_mixed_d),
+                               ("fp64", results["fp64_row_direct"]["res"], t_fp64_d))},
         "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",

@@ -56,6 +56,12 @@ enum {
                           /* U, V, lambda, residual norms, CG alpha/beta, objective in FP64 */
 };
 
+/* ---------------------------------------------------------------- Phase II subproblem solvers */
+enum {
+  LORADS_SUB_CG = 0,          /* warm-started CG (Section 4.4)                               */
+  LORADS_SUB_ROW_DIRECT = 1   /* exact row-block solve (every constraint one diagonal entry) */
+};
+
 /* ---------------------------------------------------------------- device allocator
  * Optional replacement for cudaMalloc / cudaFree, given through lorads_params (both set or
  * both NULL).  alloc returns `bytes` of device memory of the problem's device, 256-byte
@@ -126,6 +132,12 @@ typedef struct lorads_params {
   int32_t group;           /* CTAs per problem in lorads_solve_batch (1, 2, 4): a group     */
                            /*    shares one problem through bounded barriers; 0 = 2 when the  */
                            /*    largest problem has n >= 1024, else 1 (0)                    */
+  int32_t subsolver;       /* Phase II subproblems eq. linU / linV: LORADS_SUB_CG (Section   */
+                           /*    4.4) or LORADS_SUB_ROW_DIRECT, for problems whose            */
+                           /*    every constraint is one diagonal entry, at most one per row  */
+                           /*    (the matrix is then block diagonal, gamma I + rho a_j^2 W_j  */
+                           /*    W_j^T per row, inverted by Sherman-Morrison; Section 1 admits */
+                           /*    direct methods): LORADS_ERR_UNSUPPORTED otherwise (0)        */
   lorads_alloc_fn dev_alloc; /* device allocator (NULL with dev_free: cudaMalloc / cudaFree) */
   lorads_free_fn dev_free;
   void *alloc_ctx;         /* passed to dev_alloc and dev_free                               */

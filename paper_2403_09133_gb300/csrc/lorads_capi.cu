@@ -456,6 +456,9 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   dv.dinf_every = std::max(1, prm->dinf_every);
   dv.escape_scale = prm->escape_scale;
   if (!(prm->escape_scale >= 0.0)) return LORADS_ERR_ARG;
+  dv.subsolver = prm->subsolver;
+  if (prm->subsolver != 0 && prm->subsolver != 1) return LORADS_ERR_ARG;
+  if (prm->subsolver == 1 && !p->dp.a_diag_only) return LORADS_ERR_UNSUPPORTED;
   if (prm->lanczos_steps < 0 || prm->lanczos_steps > LANCZOS_MAX) return LORADS_ERR_ARG;
   if (dv.kkt_dinf && prm->lanczos_steps == 0) return LORADS_ERR_ARG;
   if (!dv.phase1) {

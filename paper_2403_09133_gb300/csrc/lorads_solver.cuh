@@ -39,6 +39,7 @@ struct DevParams {
   int lanczos_steps;
   int dinf_every;
   double escape_scale;   // Phase II rank growth along the lambda_min eigenvector (0: off)
+  int subsolver;         // 0: CG on eq. linU / linV; 1: exact row-block solve (row-local form)
   // continuation of a checkpointed Phase II (resume = 1): V is given apart from U, and the
   // iteration counter, the final-test schedule and the reported counters go on from here
   int resume;
@@ -851,7 +852,8 @@ struct Solver {
   }
 
   __device__ bool phase2(double rho, double& rho_out) {
-    if (P.a_diag_only) return phase2_local(rho, rho_out);
+    if (P.a_diag_only)
+      return prm.subsolver == 1 ? phase2_local_direct(rho, rho_out) : phase2_local(rho, rho_out);
     const double gamma = prm.gamma;
     for (int k = admm_iters; k < prm.max_admm_iter; ++k) {
       double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -906,9 +908,13 @@ struct Solver {
   // ||G||^2 with G_j = R_0j + (a rho q_i + gamma) W_j (only its norm is used) in T
   // (lam_i: lambda of row j's constraint, when it has one)
   // Returns q_i = a ||W_j||^2 (0 without a constraint).
+  // With dout (the direct subproblem solve) it stores delta_j = H_j^{-1} R_0j instead of R_0
+  // and H R_0: H_j = gamma I + rho a_j^2 W_j W_j^T is inverted by Sherman-Morrison,
+  // delta_j = (R_0j - c (W_j.R_0j) W_j) / gamma, c = rho a_j^2 / (gamma + rho a_j^2 ||W_j||^2)
+  // (a_j = 0 without a constraint), in T with the shadow of W like the CG it replaces.
   __device__ __forceinline__ double local_r0_row(int j, const Frag<double>& Wj, const Frag<T>& Wjt,
                                                  const Frag<double>& mCWj, double lam_i, double rho,
-                                                 double gamma, double* g3) {
+                                                 double gamma, double* g3, T* dout = nullptr) {
     Frag<double> accR = mCWj;
     double cg = gamma, qi = 0.0;
     const int i = P.row_con[j];
@@ -920,6 +926,19 @@ struct Solver {
     }
     Frag<T> rt, wt, gt;
     frag_convert(rt, accR);
+    if (dout != nullptr) {
+      const T at = rowa<T>(P)[j];
+      const T sa = (T)rho * at * at;
+      const T c = sa / ((T)gamma + sa * frag_dot(Wjt, Wjt, tm));
+      const T cw = -c * frag_dot(Wjt, rt, tm);
+      const T ig = T(1) / (T)gamma;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) wt.v[k][e] = fma(cw, Wjt.v[k][e], rt.v[k][e]) * ig;
+      frag_store(wt, dout, j, ld, tm);
+      return qi;
+    }
     local_h(rt, Wjt, rowa<T>(P)[j], (T)rho, (T)gamma, wt);
     frag_store(rt, A.R, j, ld, tm);
     frag_store(wt, A.HP, j, ld, tm);
@@ -935,11 +954,11 @@ struct Solver {
     return qi;
   }
 
-  // -(C X)_j for X = W + delta (delta = A.Dl when have_delta): exact FP64 sum over the
+  // -(C X)_j for X = W + delta (delta = D when have_delta): exact FP64 sum over the
   // neighbours' W and delta when exact, else mCWj - (C delta)_j with the product in T
-  __device__ __forceinline__ void local_mcx_row(int j, const double* Wm, bool have_delta,
-                                                bool exact, const Frag<double>& mCWj,
-                                                Frag<double>& out) {
+  __device__ __forceinline__ void local_mcx_row(int j, const double* Wm, const T* D,
+                                                bool have_delta, bool exact,
+                                                const Frag<double>& mCWj, Frag<double>& out) {
     if (exact) {
       Frag<double> acc;
       frag_zero(acc);
@@ -950,7 +969,7 @@ struct Solver {
         if (have_delta) {
           Frag<T> dk;
           Frag<double> dd;
-          frag_load(dk, A.Dl, k, ld, tm);
+          frag_load(dk, D, k, ld, tm);
           frag_convert(dd, dk);
           frag_axpy(Wk, 1.0, dd);
         }
@@ -962,14 +981,15 @@ struct Solver {
     out = mCWj;
     if (!have_delta) return;
     Frag<T> mcd;
-    spmm_row<T>(P, A.Dl, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, T(0), tm, mcd);
+    spmm_row<T>(P, D, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, T(0), tm, mcd);
     Frag<double> md;
     frag_convert(md, mcd);
     frag_axpy(out, 1.0, md);
   }
 
-  // the U-step's R_0 from W = V with -(C V) computed exactly (start, and after rank growth)
-  __device__ bool local_prologue(double rho, double gamma, double* g3) {
+  // the U-step's R_0 from W = V with -(C V) computed exactly (start, and after rank growth);
+  // with dout the U-step's direct solution delta instead (the reduction is then a barrier)
+  __device__ bool local_prologue(double rho, double gamma, double* g3, T* dout = nullptr) {
     g3[0] = g3[1] = g3[2] = 0.0;
     const bool shadow = (const void*)A.Vt != (const void*)A.V;
     for (int j = tm.id; j < n; j += tm.count) {
@@ -978,10 +998,10 @@ struct Solver {
       frag_load(Wj, A.V, j, ld, tm);
       if (shadow) frag_load(Wjt, A.Vt, j, ld, tm);
       else frag_convert(Wjt, Wj);
-      local_mcx_row(j, A.V, false, true, Wj, mCW);
+      local_mcx_row(j, A.V, A.Dl, false, true, Wj, mCW);
       frag_store(mCW, A.CWn, j, ld, tm);
       const int i = P.row_con[j];
-      local_r0_row(j, Wj, Wjt, mCW, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3);
+      local_r0_row(j, Wj, Wjt, mCW, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3, dout);
     }
     if (!sc.reduce(g3, 3)) return false;
     ++hess;
@@ -1130,7 +1150,7 @@ struct Solver {
           frag_axpy(Xt, T(1), x);                 // shadow of U^{k+1} = shadow(V^k) + delta
         }
         if (exact) frag_convert(Xt, Xj);          // re-rounded from the master every 32
-        local_mcx_row(j, A.V, it > 0, exact, mCW, mCX);
+        local_mcx_row(j, A.V, A.Dl, it > 0, exact, mCW, mCX);
         frag_store(Xj, A.U, j, ld, tm);
         if (shadow) frag_store(Xt, A.Ut, j, ld, tm);
         frag_store(mCX, A.CWn, j, ld, tm);
@@ -1177,7 +1197,7 @@ struct Solver {
           e = P.row_a[j] * frag_dot(Wj, Xj, tm) - P.b[i];
           lam_new = A.lam[i] + rho * e;     // every lane of the team holds the same value
         }
-        local_mcx_row(j, A.U, it > 0, exact, mCW, mCX);
+        local_mcx_row(j, A.U, A.Dl, it > 0, exact, mCW, mCX);
         frag_store(Xj, A.V, j, ld, tm);
         if (shadow) frag_store(Xt, A.Vt, j, ld, tm);
         frag_store(mCX, A.CWn, j, ld, tm);
@@ -1218,6 +1238,128 @@ struct Solver {
           if ((long long)v[4] > prm.time_limit_ns) { status = ST_TIMEOUT; break; }
           rho = rho_next;
           if (!local_prologue(rho, gamma, g3)) return false;
+          continue;
+        }
+      }
+      if ((long long)v[4] > prm.time_limit_ns) { status = ST_TIMEOUT; break; }
+      rho = rho_next;
+    }
+    if (status == ST_OK) status = ST_MAXITER;
+    rho_out = rho;
+    return true;
+  }
+
+  // ----------------------------------------------------------------------------------
+  // Phase II, row-local form with the direct subproblem solve (subsolver 1).  Section 1
+  // allows direct methods for the subproblems; here each row block of eq. linU / linV is
+  // inverted by Sherman-Morrison (local_r0_row with dout), so a subproblem costs no CG
+  // iteration and no reduction: the pass that forms a subproblem's R_0 also forms its
+  // solution delta.  Two passes per iteration:
+  //   A: U^{k+1} = V^k + delta_U, -(C U^{k+1}), and delta_V from the V-step's R_0; barrier
+  //   B: V^{k+1} = U^{k+1} + delta_V, the dual step, -(C V^{k+1}), and delta_U from the next
+  //      U-step's R_0; one grid reduction of the test sums.
+  // delta_U lives in A.Dl and delta_V in A.Pd, so no pass writes what its neighbours read.
+  // -(C W) and the T shadows are kept and refreshed every 32 iterations as in phase2_local.
+  // ----------------------------------------------------------------------------------
+  __device__ bool phase2_local_direct(double rho, double& rho_out) {
+    const double gamma = prm.gamma;
+    const double tol2_primal = prm.tol * (1.0 + P.b_inf) * prm.tol * (1.0 + P.b_inf);
+    const bool shadow = (const void*)A.Ut != (const void*)A.U;
+    T* const dU = A.Dl;
+    T* const dV = A.Pd;
+    double g3[3];
+    if (!local_prologue(rho, gamma, g3, dU)) return false;
+    for (int k = admm_iters; k < prm.max_admm_iter; ++k) {
+      const bool exact = (k + 1) % 32 == 0;
+      // pass A: U-step finish and the V-step's solution
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> Wj, Xj, mCW, mCX, xd;
+        Frag<T> Xt, x;
+        frag_load(Wj, A.V, j, ld, tm);
+        frag_load(mCW, A.CWn, j, ld, tm);
+        frag_load(Xt, A.Vt, j, ld, tm);           // (the master itself in the FP64 form)
+        frag_load(x, dU, j, ld, tm);
+        frag_convert(xd, x);
+        Xj = Wj;
+        frag_axpy(Xj, 1.0, xd);
+        frag_axpy(Xt, T(1), x);                   // shadow of U^{k+1} = shadow(V^k) + delta
+        if (exact) frag_convert(Xt, Xj);          // re-rounded from the master every 32
+        local_mcx_row(j, A.V, dU, true, exact, mCW, mCX);
+        frag_store(Xj, A.U, j, ld, tm);
+        if (shadow) frag_store(Xt, A.Ut, j, ld, tm);
+        frag_store(mCX, A.CWn, j, ld, tm);
+        const int i = P.row_con[j];
+        const double qU =
+            local_r0_row(j, Xj, Xt, mCX, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3, dV);
+        if (i >= 0 && tm.lane == 0) A.e[i] = qU;  // a ||U_j^{k+1}||^2 for the output residual
+      }
+      if (!sc.sync()) return false;
+      ++hess;
+      // pass B: V-step finish, dual step, and the next U-step's solution
+      const double rho_next =
+          ((k + 1) % prm.rho_every == 0) ? fmin(rho * prm.rho_growth, prm.rho_max) : rho;
+      double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> Wj, Xj, mCW, mCX, xd;
+        Frag<T> x, Wt, Vot;
+        frag_load(Wj, A.U, j, ld, tm);
+        frag_load(mCW, A.CWn, j, ld, tm);
+        frag_load(Wt, A.Ut, j, ld, tm);           // (the masters themselves in the FP64 form)
+        frag_load(Vot, A.Vt, j, ld, tm);
+        frag_load(x, dV, j, ld, tm);
+        frag_convert(xd, x);
+        Xj = Wj;
+        frag_axpy(Xj, 1.0, xd);
+        // eq. stop's second term (reported only): ||V^{k+1} - V^k||, ||V^k|| from the shadows
+        Frag<T> Xt = Wt, dVk = Wt;
+        frag_axpy(Xt, T(1), x);                   // shadow of V^{k+1} = shadow(U^{k+1}) + delta
+        frag_axpy(dVk, T(-1), Vot);
+        frag_axpy(dVk, T(1), x);
+        const double d2 = (double)frag_dot(dVk, dVk, tm), o2 = (double)frag_dot(Vot, Vot, tm);
+        if (exact) frag_convert(Xt, Xj);          // re-rounded from the master every 32
+        // dual step lambda_i += rho (a U_j.V_j - b_i)
+        const int i = P.row_con[j];
+        double e = 0.0, lam_new = 0.0;
+        if (i >= 0) {
+          e = P.row_a[j] * frag_dot(Wj, Xj, tm) - P.b[i];
+          lam_new = A.lam[i] + rho * e;     // every lane of the team holds the same value
+        }
+        local_mcx_row(j, A.U, dV, true, exact, mCW, mCX);
+        frag_store(Xj, A.V, j, ld, tm);
+        if (shadow) frag_store(Xt, A.Vt, j, ld, tm);
+        frag_store(mCX, A.CWn, j, ld, tm);
+        const double qV = local_r0_row(j, Xj, Xt, mCX, lam_new, rho_next, gamma, g3, dU);
+        // the output's row residual a ||(U_j + V_j)/2||^2 - b_i from a||U_j||^2 (pass A),
+        // a U_j.V_j = e + b_i and a||V_j||^2
+        double eh = 0.0;
+        if (i >= 0) eh = 0.25 * (A.e[i] + 2.0 * (e + P.b[i]) + qV) - P.b[i];
+        if (tm.lane == 0) {
+          if (i >= 0) A.lam[i] = lam_new;
+          v[0] += e * e;
+          v[1] += eh * eh;
+          v[2] += d2;
+          v[3] += o2;
+        }
+      }
+      if (sc.is_leader()) v[4] = (double)(globaltimer_ns() - t_start);
+      if (!sc.reduce(v, 5)) return false;
+      ++hess;
+      admm_iters = k + 1;
+      rs_num = v[2];
+      rs_den = v[3];
+      if (!(v[0] == v[0]) || !(v[2] == v[2])) { status = ST_NAN; break; }
+      if (v[1] <= tol2_primal) {
+        const int t = final_test();
+        if (t < 0) return false;
+        if (t == 1) {
+          rho_out = rho;
+          return true;
+        }
+        if (t == 2) {
+          // U, V and the rank changed: the pipelined delta_U is stale
+          if ((long long)v[4] > prm.time_limit_ns) { status = ST_TIMEOUT; break; }
+          rho = rho_next;
+          if (!local_prologue(rho, gamma, g3, dU)) return false;
           continue;
         }
       }

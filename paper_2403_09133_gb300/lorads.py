@@ -29,6 +29,8 @@ LORADS_ERR_TOO_LARGE = -10
 LORADS_STATIC_SCRATCH_BYTES = 32 << 20
 LORADS_PREC_FP64 = 0
 LORADS_PREC_MIXED = 1
+LORADS_SUB_CG = 0
+LORADS_SUB_ROW_DIRECT = 1
 
 _i32, _i64, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
 
@@ -50,7 +52,7 @@ class lorads_params(ctypes.Structure):
         ("seed", _u64), ("precision", _i32), ("phase1", _i32), ("time_limit_s", _f64),
         ("threads", _i32), ("grid", _i32), ("team_mult", _i32),
         ("kkt_dinf", _i32), ("lanczos_steps", _i32), ("dinf_every", _i32),
-        ("escape_scale", _f64), ("group", _i32),
+        ("escape_scale", _f64), ("group", _i32), ("subsolver", _i32),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 

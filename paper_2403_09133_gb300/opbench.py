@@ -53,6 +53,8 @@ def main():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--op", default="hessian", choices=["hessian", "spmm", "sddmm", "all", "solve"])
     ap.add_argument("--admm-cap", type=int, default=20, help="--op solve: Phase II iterations")
+    ap.add_argument("--subsolver", default="cg", choices=["cg", "row_direct"],
+                    help="--op solve: Phase II subproblem solver")
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--seed", type=int, default=2)
@@ -66,7 +68,9 @@ def main():
         prec = L.LORADS_PREC_MIXED if a.prec == "mixed" else L.LORADS_PREC_FP64
         out = []
         for it in range(a.warmup + a.iters):
-            res = prob.solve(precision=prec, max_admm_iter=a.admm_cap)
+            res = prob.solve(precision=prec, max_admm_iter=a.admm_cap,
+                             subsolver=L.LORADS_SUB_ROW_DIRECT if a.subsolver == "row_direct"
+                             else L.LORADS_SUB_CG)
             out.append(res)
         prob.close()
         last = out[-1]

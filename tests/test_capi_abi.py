@@ -60,6 +60,7 @@ def test_default_params_match_oracle_readings(lib):
     assert p.switch_tol < 0 and o.switch_tol == 1e-2 and p.h < 0 and o.h == 10.0
     assert p.kkt_dinf == int(o.kkt_dinf) and p.dinf_every == o.dinf_every
     assert p.escape_scale == o.escape_scale and p.lanczos_steps > 0
+    assert p.subsolver == L.LORADS_SUB_CG and o.subsolver == "cg"
 
 
 def test_status_strings(lib):

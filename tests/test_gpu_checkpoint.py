@@ -110,6 +110,25 @@ def test_resume_follows_the_trajectory(cuda, case, prec, k1):
           f"U={np.array_equal(got['U'], ref_st['U'])} lam={np.array_equal(got['lam'], ref_st['lam'])}")
 
 
+@pytest.mark.parametrize("prec", [L.LORADS_PREC_FP64, L.LORADS_PREC_MIXED])
+def test_resume_with_the_direct_subsolver(cuda, prec):
+    """The row-block direct solve keeps delta_U between iterations; a resume recomputes it
+    from the checkpoint, and at k a multiple of 32 the continuation is exact."""
+    inst = I.maxcut_torus(40, 40, seed=2)
+    kw = dict(precision=prec, subsolver=L.LORADS_SUB_ROW_DIRECT)
+    p = L.Problem(inst)
+    full = p.solve(**kw)
+    p.solve(max_admm_iter=256, **kw)
+    st = p.get_state()
+    p.close()
+    q = L.Problem(inst)
+    q.set_state(st)
+    res = q.solve(phase1=0, **kw)
+    q.close()
+    assert full["status"] == 0 and res["status"] == 0
+    assert res["objective"] == full["objective"] and res["admm_iters"] == full["admm_iters"]
+
+
 def test_resume_after_phase2_rank_growth(cuda):
     """The 770-vertex batch graph grows its rank 10 -> 15 in Phase II; a checkpoint taken
     near the end of the solve carries rank 15 and the growth count."""

@@ -166,3 +166,68 @@ def test_matrix_completion_grid_scope_both_forms(cuda):
     assert r64["status"] == 0 and r32["status"] == 0
     assert abs(r64["objective"] - r32["objective"]) <= 1e-5 * abs(r64["objective"])
     assert again["objective"] == r64["objective"] and again["admm_iters"] == r64["admm_iters"]
+
+
+@pytest.mark.parametrize("prec", [L.LORADS_PREC_FP64, L.LORADS_PREC_MIXED])
+def test_row_direct_against_oracle(cuda, prec):
+    """The exact row-block subproblem solve (subsolver 1) on ER n = 500 against the oracle's
+    own row_direct solve: both pass the final test; the FP64 form follows the oracle's
+    trajectory (same iteration count within 2, objective to 1e-9)."""
+    inst = I.workload_er500()
+    sdp = SDP.from_instance(inst)
+    ref = solve(sdp, Params(subsolver="row_direct"))
+    res, sol = gpu_solve(inst, precision=prec, subsolver=L.LORADS_SUB_ROW_DIRECT)
+    assert ref["converged"] and ref["cg_iters"] == 0
+    assert res["status"] == 0, L.lorads_status_string(res["status"])
+    assert res["cg_iters"] == 0
+    assert res["r_P"] <= 1e-6 and abs(res["gap"]) <= 1e-6 and res["d_infeas"] <= 1e-6
+    if prec == L.LORADS_PREC_FP64:
+        assert abs(res["admm_iters"] - ref["admm_iters"]) <= 2
+        assert abs(res["objective"] - ref["objective"]) <= 1e-9 * abs(ref["objective"])
+    else:
+        assert abs(res["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+    lmin = min_eig_dual_slack(sdp, sol["y"])
+    assert max(0.0, -lmin) / (1.0 + sdp.c_one) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [L.LORADS_PREC_FP64, L.LORADS_PREC_MIXED])
+def test_row_direct_closed_forms(cuda, prec):
+    n = 12
+    res, _ = gpu_solve(I.maxcut_complete(n), precision=prec, tol=1e-9, max_admm_iter=3000,
+                       subsolver=L.LORADS_SUB_ROW_DIRECT)
+    assert abs(res["objective"] + n * n / 4) <= 1e-7 * n * n / 4
+    a, b = 6, 8
+    res, _ = gpu_solve(I.maxcut_torus(a, b, seed=None), precision=prec, tol=1e-9,
+                       max_admm_iter=3000, subsolver=L.LORADS_SUB_ROW_DIRECT)
+    want = a * b * (lam_max_cycle(a) + lam_max_cycle(b)) / 4
+    assert abs(-res["objective"] - want) <= 1e-7 * want
+
+
+def test_row_direct_grid_scope_against_oracle(cuda):
+    """40 x 40 signed torus (grid scope, 152 CTAs): FP64 direct solve against the oracle's."""
+    inst = I.maxcut_torus(40, 40, seed=2)
+    sdp = SDP.from_instance(inst)
+    ref = solve(sdp, Params(subsolver="row_direct"))
+    res, _ = gpu_solve(inst, precision=L.LORADS_PREC_FP64, subsolver=L.LORADS_SUB_ROW_DIRECT)
+    assert ref["converged"] and res["status"] == 0
+    assert abs(res["admm_iters"] - ref["admm_iters"]) <= 2
+    assert abs(res["objective"] - ref["objective"]) <= 1e-9 * abs(ref["objective"])
+
+
+def test_row_direct_statuses(cuda):
+    # not row-separable: matrix completion's off-diagonal constraints
+    res, _ = gpu_solve(I.matrix_completion(10, 10, 2, 40, seed=1),
+                       subsolver=L.LORADS_SUB_ROW_DIRECT)
+    assert res["status"] == L.LORADS_ERR_UNSUPPORTED
+    res, _ = gpu_solve(I.maxcut_er(50, 4.0, seed=1), subsolver=2)
+    assert res["status"] == L.LORADS_ERR_ARG
+    # batches take it too: every problem row-separable
+    insts = [I.maxcut_er(n, 6.0, seed=90 + n) for n in (80, 200, 330)]
+    hs = [L.Problem(x) for x in insts]
+    prm = hs[0].params(subsolver=L.LORADS_SUB_ROW_DIRECT, threads=256, team_mult=1)
+    out, _, _ = L.lorads_solve_batch([h.handle for h in hs], prm)
+    for h, x, r in zip(hs, insts, out):
+        one = h.solve(subsolver=L.LORADS_SUB_ROW_DIRECT, grid=1, threads=256)
+        assert r["status"] == 0 and r["cg_iters"] == 0
+        assert r["objective"] == one["objective"] and r["admm_iters"] == one["admm_iters"]
+        h.close()
