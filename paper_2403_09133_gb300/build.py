@@ -1,8 +1,8 @@
 """Builds liblorads.so (the C ABI of include/lorads.h) in-tree with nvcc for sm_103a.
 
-Four translation units compile in parallel (FP64 kernels, FP32 kernels, host runtime, the
-learned warm start) and
-link into one shared library next to this file.  Usage: python -m paper_2403_09133_gb300.build
+Six translation units compile in parallel (the FP64 and FP32 solver kernels with CG, the
+same with the exact row-block subproblem solve, the host runtime, the learned warm start)
+and link into one shared library next to this file.  Usage: python -m paper_2403_09133_gb300.build
 """
 from __future__ import annotations
 
@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblorads.so")
-SOURCES = ["lorads_f64.cu", "lorads_f32.cu", "lorads_capi.cu", "lorads_gnn.cu"]
+SOURCES = ["lorads_f64.cu", "lorads_f32.cu", "lorads_f64_direct.cu", "lorads_f32_direct.cu",
+           "lorads_capi.cu", "lorads_gnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

@@ -620,7 +620,7 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   if (threads % 32 != 0 || threads > BLOCK_THREADS_MAX) return LORADS_ERR_ARG;
   cudaError_t le;
   if (grid == 1) {
-    le = Launch<T>::solve_block(dargs, 1, p->dqueue, 1, threads, s);
+    le = Launch<T>::solve_block(dv.subsolver, dargs, 1, p->dqueue, 1, threads, s);
   } else {
     // CTA size: enough teams for one row each at the initial rank, within [128, 320]
     int gthreads = prm->threads > 0 ? prm->threads : 0;
@@ -632,11 +632,12 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
     }
     if (gthreads % 32 != 0 || gthreads > GRID_THREADS_MAX) return LORADS_ERR_ARG;
     int per_sm = 0;
-    CU(Launch<T>::grid_capacity(gthreads, &per_sm));
+    CU(Launch<T>::grid_capacity(dv.subsolver, gthreads, &per_sm));
     const int maxg = std::max(1, per_sm) * dev_sms;
     grid = std::min(std::min(grid, maxg), dev_sms * 8);
     const long long spin = 50LL * 1000 * 1000;   // ~ a few seconds of polling
-    le = Launch<T>::solve_grid(dargs, p->dctl, p->dpartials, spin, grid, gthreads, s);
+    le = Launch<T>::solve_grid(dv.subsolver, dargs, p->dctl, p->dpartials, spin, grid, gthreads,
+                               s);
   }
   CU(le);
   SolveOut out{};
@@ -661,6 +662,7 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   std::vector<std::pair<double, int>> order(count);
   lorads_params q = *prm;
   q.team_mult = team_mult;
+  const int sub = prm->subsolver;
   const DevAlloc al = DevAlloc::from(prm, s);
   for (int i = 0; i < count; ++i) {
     lorads_problem* p = ps[i];
@@ -681,8 +683,8 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   for (int k = 0; k < count; ++k) sorted[k] = hs[order[k].second];
   int dev_sms = 0, per_sm = 0;
   CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device));
-  if (group > 1) CU(Launch<T>::group_capacity(threads, &per_sm));
-  else CU(Launch<T>::block_capacity(threads, &per_sm));
+  if (group > 1) CU(Launch<T>::group_capacity(sub, threads, &per_sm));
+  else CU(Launch<T>::block_capacity(sub, threads, &per_sm));
   // one CTA per problem, or groups of `group` CTAs per problem (never more than resident)
   int grid = std::max(1, std::min(count, std::max(1, per_sm) * dev_sms));
   int groups = 0;
@@ -722,9 +724,9 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
     cudaError_t c1 = cudaMemsetAsync(dqueue, 0, 16, cap);
     if (c1 == cudaSuccess && group > 1) c1 = cudaMemsetAsync(dctls, 0, c_bytes, cap);
     const cudaError_t c2 =
-        group > 1 ? Launch<T>::solve_group(dargs, count, dqueue, dctls, dparts, dslots, group,
+        group > 1 ? Launch<T>::solve_group(sub, dargs, count, dqueue, dctls, dparts, dslots, group,
                                            50LL * 1000 * 1000, grid, threads, cap)
-                  : Launch<T>::solve_block(dargs, count, dqueue, grid, threads, cap);
+                  : Launch<T>::solve_block(sub, dargs, count, dqueue, grid, threads, cap);
     const cudaError_t c3 = cudaStreamEndCapture(cap, &graph);
     if ((st = check_cuda(c1 != cudaSuccess ? c1 : (c2 != cudaSuccess ? c2 : c3))) != LORADS_OK)
       break;
@@ -1319,12 +1321,13 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   if (grid <= 0) grid = (n < 512) ? 1 : dev_sms;
   cudaError_t le;
   if (grid == 1) {
-    le = Launch<T>::solve_block(dargs, 1, dqueue, 1, SOLVER_THREADS, s);
+    le = Launch<T>::solve_block(dv.subsolver, dargs, 1, dqueue, 1, SOLVER_THREADS, s);
   } else {
     int per_sm = 0;
-    CU(Launch<T>::grid_capacity(SOLVER_THREADS, &per_sm));
+    CU(Launch<T>::grid_capacity(dv.subsolver, SOLVER_THREADS, &per_sm));
     grid = std::min(std::min(grid, std::max(1, per_sm) * dev_sms), dev_sms * 8);
-    le = Launch<T>::solve_grid(dargs, dctl, dpartials, 50LL * 1000 * 1000, grid, SOLVER_THREADS,
+    le = Launch<T>::solve_grid(dv.subsolver, dargs, dctl, dpartials, 50LL * 1000 * 1000, grid,
+                               SOLVER_THREADS,
                                s);
   }
   CU(le);

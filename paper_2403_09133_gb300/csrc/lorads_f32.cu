@@ -2,4 +2,5 @@
 #include "lorads_kernels.cuh"
 namespace lorads {
 LORADS_DEFINE_LAUNCH(float)
+LORADS_DEFINE_SOLVE_LAUNCH(float, 0)
 }

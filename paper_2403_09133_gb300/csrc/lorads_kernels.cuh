@@ -10,7 +10,7 @@ constexpr int BLOCK_THREADS_MAX = 384;    // ... and the largest (batches autotu
 constexpr int GRID_THREADS_MAX = 320;     // grid solver: CTA size chosen per problem
 
 // one CTA per problem; CTAs take problems from a queue (batches), or a single problem
-template <typename T>
+template <typename T, int SUB>
 __global__ void __launch_bounds__(BLOCK_THREADS_MAX, 1)
 solve_block_kernel(const SolverArgs<T>* args, int count, int* queue) {
   __shared__ double red[34 * MAXRED];
@@ -24,13 +24,13 @@ solve_block_kernel(const SolverArgs<T>* args, int count, int* queue) {
     if (threadIdx.x == 0) sa = args[i];
     __syncthreads();
     BlockScope sc{red};
-    run_solver<T>(sa, sc);
+    run_solver<T, SUB>(sa, sc);
     __syncthreads();
   }
 }
 
 // one problem over the whole grid (cooperative launch: all CTAs co-resident)
-template <typename T>
+template <typename T, int SUB>
 __global__ void __launch_bounds__(GRID_THREADS_MAX, 1)
 solve_grid_kernel(const SolverArgs<T>* args, GridCtl* ctl, double* partials, long long spin) {
   __shared__ double red[34 * MAXRED];
@@ -38,7 +38,7 @@ solve_grid_kernel(const SolverArgs<T>* args, GridCtl* ctl, double* partials, lon
   if (threadIdx.x == 0) sa = *args;
   __syncthreads();
   GridScope sc{red, ctl, partials, spin, 0, (int)gridDim.x};
-  run_solver<T>(sa, sc);
+  run_solver<T, SUB>(sa, sc);
 }
 
 // batches with several CTAs per problem: CTAs [g * group, (g + 1) * group) form group g,
@@ -46,7 +46,7 @@ solve_grid_kernel(const SolverArgs<T>* args, GridCtl* ctl, double* partials, lon
 // the group (ctls[g] is its barrier, slots[g] the index its leader fetched).  The launch is
 // cooperative, so every CTA of a group is resident and the group's bounded barriers never
 // wait on a CTA that has not started.
-template <typename T>
+template <typename T, int SUB>
 __global__ void __launch_bounds__(BLOCK_THREADS_MAX, 1)
 solve_group_kernel(const SolverArgs<T>* args, int count, int* queue, GridCtl* ctls,
                    double* partials, int* slots, int group, long long spin) {
@@ -61,7 +61,7 @@ solve_group_kernel(const SolverArgs<T>* args, int count, int* queue, GridCtl* ct
     if (i >= count) return;
     if (threadIdx.x == 0) sa = args[i];
     __syncthreads();
-    run_solver<T>(sa, sc);
+    run_solver<T, SUB>(sa, sc);
     __syncthreads();
   }
 }
@@ -120,9 +120,11 @@ __global__ void op_hessian_kernel(DevProblem P, int ld, T rho, T gamma, const T*
   }
 }
 
-// host-side launchers (defined in the per-type translation units)
-template <typename T>
-struct Launch {
+// host-side launchers of the solver kernels, per element type and subproblem solver
+// (defined in lorads_f64.cu / lorads_f32.cu for SUB 0 and lorads_f64_direct.cu /
+// lorads_f32_direct.cu for SUB 1, compiled in parallel)
+template <typename T, int SUB>
+struct SolveLaunch {
   static cudaError_t solve_block(const SolverArgs<T>* args, int count, int* queue, int grid,
                                  int threads, cudaStream_t s);
   static cudaError_t block_capacity(int threads, int* blocks_per_sm);
@@ -133,6 +135,104 @@ struct Launch {
                                  double* partials, int* slots, int group, long long spin,
                                  int grid, int threads, cudaStream_t s);
   static cudaError_t group_capacity(int threads, int* blocks_per_sm);
+};
+
+#define LORADS_DECLARE_SOLVE_LAUNCH(T, SUB)                                                    \
+  template <> cudaError_t SolveLaunch<T, SUB>::solve_block(const SolverArgs<T>*, int, int*,    \
+                                                           int, int, cudaStream_t);            \
+  template <> cudaError_t SolveLaunch<T, SUB>::block_capacity(int, int*);                      \
+  template <> cudaError_t SolveLaunch<T, SUB>::solve_grid(const SolverArgs<T>*, GridCtl*,      \
+                                                          double*, long long, int, int,        \
+                                                          cudaStream_t);                       \
+  template <> cudaError_t SolveLaunch<T, SUB>::grid_capacity(int, int*);                       \
+  template <> cudaError_t SolveLaunch<T, SUB>::solve_group(const SolverArgs<T>*, int, int*,    \
+                                                           GridCtl*, double*, int*, int,       \
+                                                           long long, int, int, cudaStream_t); \
+  template <> cudaError_t SolveLaunch<T, SUB>::group_capacity(int, int*);
+LORADS_DECLARE_SOLVE_LAUNCH(double, 0)
+LORADS_DECLARE_SOLVE_LAUNCH(float, 0)
+LORADS_DECLARE_SOLVE_LAUNCH(double, 1)
+LORADS_DECLARE_SOLVE_LAUNCH(float, 1)
+
+#define LORADS_DEFINE_SOLVE_LAUNCH(T, SUB)                                                     \
+  template <>                                                                                  \
+  cudaError_t SolveLaunch<T, SUB>::solve_block(const SolverArgs<T>* args, int count,           \
+                                               int* queue, int grid, int threads,              \
+                                               cudaStream_t s) {                               \
+    solve_block_kernel<T, SUB><<<grid, threads, 0, s>>>(args, count, queue);                   \
+    return cudaGetLastError();                                                                 \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t SolveLaunch<T, SUB>::block_capacity(int threads, int* blocks_per_sm) {           \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,                        \
+                                                         solve_block_kernel<T, SUB>, threads,  \
+                                                         0);                                   \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t SolveLaunch<T, SUB>::solve_grid(const SolverArgs<T>* args, GridCtl* ctl,         \
+                                              double* partials, long long spin, int grid,      \
+                                              int threads, cudaStream_t s) {                   \
+    void* kargs[] = {(void*)&args, (void*)&ctl, (void*)&partials, (void*)&spin};               \
+    return cudaLaunchCooperativeKernel((const void*)solve_grid_kernel<T, SUB>, dim3(grid),     \
+                                       dim3(threads), kargs, 0, s);                            \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t SolveLaunch<T, SUB>::grid_capacity(int threads, int* blocks_per_sm) {            \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,                        \
+                                                         solve_grid_kernel<T, SUB>, threads,   \
+                                                         0);                                   \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t SolveLaunch<T, SUB>::solve_group(const SolverArgs<T>* args, int count,           \
+                                               int* queue, GridCtl* ctls, double* partials,    \
+                                               int* slots, int group, long long spin,          \
+                                               int grid, int threads, cudaStream_t s) {        \
+    void* kargs[] = {(void*)&args,     (void*)&count, (void*)&queue, (void*)&ctls,             \
+                     (void*)&partials, (void*)&slots, (void*)&group, (void*)&spin};            \
+    return cudaLaunchCooperativeKernel((const void*)solve_group_kernel<T, SUB>, dim3(grid),    \
+                                       dim3(threads), kargs, 0, s);                            \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t SolveLaunch<T, SUB>::group_capacity(int threads, int* blocks_per_sm) {           \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,                        \
+                                                         solve_group_kernel<T, SUB>, threads,  \
+                                                         0);                                   \
+  }
+
+// the solver launchers by run-time subproblem solver, and the operator launchers
+template <typename T>
+struct Launch {
+  static cudaError_t solve_block(int sub, const SolverArgs<T>* args, int count, int* queue,
+                                 int grid, int threads, cudaStream_t s) {
+    return sub ? SolveLaunch<T, 1>::solve_block(args, count, queue, grid, threads, s)
+               : SolveLaunch<T, 0>::solve_block(args, count, queue, grid, threads, s);
+  }
+  static cudaError_t block_capacity(int sub, int threads, int* blocks_per_sm) {
+    return sub ? SolveLaunch<T, 1>::block_capacity(threads, blocks_per_sm)
+               : SolveLaunch<T, 0>::block_capacity(threads, blocks_per_sm);
+  }
+  static cudaError_t solve_grid(int sub, const SolverArgs<T>* args, GridCtl* ctl,
+                                double* partials, long long spin, int grid, int threads,
+                                cudaStream_t s) {
+    return sub ? SolveLaunch<T, 1>::solve_grid(args, ctl, partials, spin, grid, threads, s)
+               : SolveLaunch<T, 0>::solve_grid(args, ctl, partials, spin, grid, threads, s);
+  }
+  static cudaError_t grid_capacity(int sub, int threads, int* blocks_per_sm) {
+    return sub ? SolveLaunch<T, 1>::grid_capacity(threads, blocks_per_sm)
+               : SolveLaunch<T, 0>::grid_capacity(threads, blocks_per_sm);
+  }
+  static cudaError_t solve_group(int sub, const SolverArgs<T>* args, int count, int* queue,
+                                 GridCtl* ctls, double* partials, int* slots, int group,
+                                 long long spin, int grid, int threads, cudaStream_t s) {
+    return sub ? SolveLaunch<T, 1>::solve_group(args, count, queue, ctls, partials, slots,
+                                                group, spin, grid, threads, s)
+               : SolveLaunch<T, 0>::solve_group(args, count, queue, ctls, partials, slots,
+                                                group, spin, grid, threads, s);
+  }
+  static cudaError_t group_capacity(int sub, int threads, int* blocks_per_sm) {
+    return sub ? SolveLaunch<T, 1>::group_capacity(threads, blocks_per_sm)
+               : SolveLaunch<T, 0>::group_capacity(threads, blocks_per_sm);
+  }
   static cudaError_t op_sddmm(const DevProblem& P, int ld, const T* U, const T* V, double* q,
                               int grid, cudaStream_t s);
   static cudaError_t op_spmm(const DevProblem& P, int ld, const double* w, double gamma,
@@ -142,16 +242,6 @@ struct Launch {
 };
 
 #define LORADS_DECLARE_LAUNCH(T)                                                               \
-  template <> cudaError_t Launch<T>::solve_block(const SolverArgs<T>*, int, int*, int, int,     \
-                                                 cudaStream_t);                                 \
-  template <> cudaError_t Launch<T>::block_capacity(int, int*);                                 \
-  template <> cudaError_t Launch<T>::solve_grid(const SolverArgs<T>*, GridCtl*, double*,        \
-                                                long long, int, int, cudaStream_t);             \
-  template <> cudaError_t Launch<T>::grid_capacity(int, int*);                                  \
-  template <> cudaError_t Launch<T>::solve_group(const SolverArgs<T>*, int, int*, GridCtl*,     \
-                                                 double*, int*, int, long long, int, int,       \
-                                                 cudaStream_t);                                 \
-  template <> cudaError_t Launch<T>::group_capacity(int, int*);                                 \
   template <> cudaError_t Launch<T>::op_sddmm(const DevProblem&, int, const T*, const T*,      \
                                               double*, int, cudaStream_t);                      \
   template <> cudaError_t Launch<T>::op_spmm(const DevProblem&, int, const double*, double,    \
@@ -162,43 +252,6 @@ LORADS_DECLARE_LAUNCH(double)
 LORADS_DECLARE_LAUNCH(float)
 
 #define LORADS_DEFINE_LAUNCH(T)                                                                \
-  template <>                                                                                  \
-  cudaError_t Launch<T>::solve_block(const SolverArgs<T>* args, int count, int* queue, int grid,\
-                                     int threads, cudaStream_t s) {                            \
-    solve_block_kernel<T><<<grid, threads, 0, s>>>(args, count, queue);                        \
-    return cudaGetLastError();                                                                 \
-  }                                                                                            \
-  template <>                                                                                  \
-  cudaError_t Launch<T>::block_capacity(int threads, int* blocks_per_sm) {                     \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_block_kernel<T>, \
-                                                         threads, 0);                          \
-  }                                                                                            \
-  template <>                                                                                  \
-  cudaError_t Launch<T>::solve_grid(const SolverArgs<T>* args, GridCtl* ctl, double* partials, \
-                                    long long spin, int grid, int threads, cudaStream_t s) {   \
-    void* kargs[] = {(void*)&args, (void*)&ctl, (void*)&partials, (void*)&spin};               \
-    return cudaLaunchCooperativeKernel((const void*)solve_grid_kernel<T>, dim3(grid),          \
-                                       dim3(threads), kargs, 0, s);                            \
-  }                                                                                            \
-  template <>                                                                                  \
-  cudaError_t Launch<T>::grid_capacity(int threads, int* blocks_per_sm) {                      \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_grid_kernel<T>,  \
-                                                         threads, 0);                          \
-  }                                                                                            \
-  template <>                                                                                  \
-  cudaError_t Launch<T>::solve_group(const SolverArgs<T>* args, int count, int* queue,         \
-                                     GridCtl* ctls, double* partials, int* slots, int group,   \
-                                     long long spin, int grid, int threads, cudaStream_t s) {  \
-    void* kargs[] = {(void*)&args,     (void*)&count, (void*)&queue, (void*)&ctls,             \
-                     (void*)&partials, (void*)&slots, (void*)&group, (void*)&spin};            \
-    return cudaLaunchCooperativeKernel((const void*)solve_group_kernel<T>, dim3(grid),         \
-                                       dim3(threads), kargs, 0, s);                            \
-  }                                                                                            \
-  template <>                                                                                  \
-  cudaError_t Launch<T>::group_capacity(int threads, int* blocks_per_sm) {                     \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_group_kernel<T>, \
-                                                         threads, 0);                          \
-  }                                                                                            \
   template <>                                                                                  \
   cudaError_t Launch<T>::op_sddmm(const DevProblem& P, int ld, const T* U, const T* V,         \
                                   double* q, int grid, cudaStream_t s) {                       \

@@ -39,7 +39,7 @@ struct DevParams {
   int lanczos_steps;
   int dinf_every;
   double escape_scale;   // Phase II rank growth along the lambda_min eigenvector (0: off)
-  int subsolver;         // 0: CG on eq. linU / linV; 1: exact row-block solve (row-local form)
+  int subsolver;         // 0: CG on eq. linU / linV; 1: exact row-block solve (the kernel's SUB)
   // continuation of a checkpointed Phase II (resume = 1): V is given apart from U, and the
   // iteration counter, the final-test schedule and the reported counters go on from here
   int resume;
@@ -159,7 +159,10 @@ __device__ inline double quartic_step(double a1, double a2, double a3, double a4
   return best;
 }
 
-template <typename T, class Scope>
+// SUB selects the Phase II subproblem solver at compile time: 0 = CG (every constraint
+// structure), 1 = the exact row-block solve (row-local problems only), so that neither
+// kernel carries the other's code
+template <typename T, class Scope, int SUB = 0>
 struct Solver {
   const SolverArgs<T>& A;
   Scope& sc;
@@ -852,8 +855,17 @@ struct Solver {
   }
 
   __device__ bool phase2(double rho, double& rho_out) {
-    if (P.a_diag_only)
-      return prm.subsolver == 1 ? phase2_local_direct(rho, rho_out) : phase2_local(rho, rho_out);
+    if constexpr (SUB == 1) {
+      // launched by the host for row-local problems only
+      if (!P.a_diag_only) return false;
+      return phase2_local_direct(rho, rho_out);
+    } else {
+      return phase2_cg(rho, rho_out);
+    }
+  }
+
+  __device__ bool phase2_cg(double rho, double& rho_out) {
+    if (P.a_diag_only) return phase2_local(rho, rho_out);
     const double gamma = prm.gamma;
     for (int k = admm_iters; k < prm.max_admm_iter; ++k) {
       double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -1862,9 +1874,9 @@ struct Solver {
   }
 };
 
-template <typename T, class Scope>
+template <typename T, int SUB, class Scope>
 __device__ void run_solver(const SolverArgs<T>& a, Scope& sc) {
-  Solver<T, Scope> s(a, sc);
+  Solver<T, Scope, SUB> s(a, sc);
   s.run();
 }
 
