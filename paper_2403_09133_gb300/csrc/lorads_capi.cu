@@ -697,7 +697,7 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   const size_t a_bytes = (sizeof(SolverArgs<T>) * count + 255) / 256 * 256;
   const size_t c_bytes = (sizeof(GridCtl) * groups + 255) / 256 * 256;
   const size_t s_bytes = (sizeof(int) * groups + 255) / 256 * 256;
-  const size_t p_bytes = sizeof(double) * (size_t)grid * MAXRED * (group > 1 ? 1 : 0);
+  const size_t p_bytes = sizeof(double) * (size_t)grid * MAXRED * (group > 1 ? 2 : 0);
   const size_t base_bytes = a_bytes + 256 + c_bytes + s_bytes + p_bytes;
   char* base = static_cast<char*>(al.get(base_bytes));
   if (!base) return LORADS_ERR_NOMEM;

@@ -371,7 +371,7 @@ struct BlockScope {
 struct GridScope {
   double* red;             // shared memory (34 rows of MAXRED, see BlockScope)
   GridCtl* ctl;            // zeroed before launch
-  double* partials;        // gridDim.x * MAXRED
+  double* partials;        // 2 * gridDim.x * MAXRED (two rounds, by barrier generation)
   long long spin_limit;    // polls before a barrier gives up
   int first = 0;           // the scope spans CTAs [first, first + nb) of a cooperative launch
   int nb = 0;              // (0: the whole grid)
@@ -388,13 +388,22 @@ struct GridScope {
   // the generation with acquire loads (bounded).  Every CTA then loads all partials -- the
   // loads of one lane are issued together, eight CTAs at a time, so their L2 round trips
   // overlap -- and adds them in the same fixed order.
+  // The partials of consecutive barriers go to two buffers chosen by the generation's
+  // parity: a CTA released early may reach the next reduction and store its next partial
+  // while a later CTA still loads this round's, so one buffer would let the later CTA add a
+  // value of the wrong round.  Two rounds suffice, since no CTA passes the next barrier before
+  // every CTA has arrived there, that is, has finished reading this round.
   __device__ bool barrier(int k) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       int ok = 1;
+      unsigned parity = 0;
       if (lane == 0) {
-        for (int i = 0; i < k; ++i) partials[blockIdx.x * MAXRED + i] = red[32 * MAXRED + i];
+        // the generation of this barrier: every CTA of the scope reads the same value here
         const unsigned my_gen = ld_acquire_u32(&ctl->gen);
+        parity = my_gen & 1u;
+        double* mine = partials + (size_t)(my_gen & 1u) * gridDim.x * MAXRED;
+        for (int i = 0; i < k; ++i) mine[blockIdx.x * MAXRED + i] = red[32 * MAXRED + i];
         const unsigned arrived = atom_add_acq_rel_u32(&ctl->count, 1u);
         if (arrived == (unsigned)count() - 1) {
           ctl->count = 0;
@@ -418,9 +427,10 @@ struct GridScope {
       }
       // lane 0's acquire orders the other lanes' loads through __syncwarp
       __syncwarp();
+      parity = __shfl_sync(0xffffffffu, parity, 0);
       if (k > 0) {
         const int c = count();
-        const double* pp = partials + (size_t)first * MAXRED;
+        const double* pp = partials + ((size_t)parity * gridDim.x + first) * MAXRED;
         if (k <= 1) grid_partials_k<1>(pp, k, c, red);
         else if (k <= 2) grid_partials_k<2>(pp, k, c, red);
         else if (k <= 4) grid_partials_k<4>(pp, k, c, red);
