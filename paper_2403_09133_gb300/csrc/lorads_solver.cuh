@@ -915,6 +915,22 @@ struct Solver {
   // and re-rounded from the FP64 masters at the same exact steps.  Same iterates as the
   // unpipelined form up to rounding.
   // ----------------------------------------------------------------------------------
+  // row j's constraint (the row-local form has at most one per row): its index (-1: none),
+  // a, b and lambda, loaded before a pass stores anything (loads after a store to memory
+  // that might alias wait behind it)
+  struct RowCon {
+    int i;
+    double a, b, lam;
+  };
+  __device__ __forceinline__ RowCon row_con_of(int j) const {
+    RowCon c;
+    c.i = P.row_con[j];
+    c.a = P.row_a[j];
+    c.b = c.i >= 0 ? P.b[c.i] : 0.0;
+    c.lam = c.i >= 0 ? A.lam[c.i] : 0.0;
+    return c;
+  }
+
   // R_0 and w_0 = H r_0 of the local subproblem with fixed factor W on row j, given
   // mCWj = -(C W)_j:  R_0j = -(C W)_j + a (rho b_i - lambda_i - rho q_i) W_j, q_i = a W_j.W_j;
   // ||G||^2 with G_j = R_0j + (a rho q_i + gamma) W_j (only its norm is used) in T
@@ -925,21 +941,20 @@ struct Solver {
   // delta_j = (R_0j - c (W_j.R_0j) W_j) / gamma, c = rho a_j^2 / (gamma + rho a_j^2 ||W_j||^2)
   // (a_j = 0 without a constraint), in T with the shadow of W like the CG it replaces.
   __device__ __forceinline__ double local_r0_row(int j, const Frag<double>& Wj, const Frag<T>& Wjt,
-                                                 const Frag<double>& mCWj, double lam_i, double rho,
-                                                 double gamma, double* g3, T* dout = nullptr) {
+                                                 const Frag<double>& mCWj, const RowCon& c,
+                                                 double lam_i, double rho, double gamma,
+                                                 double* g3, T* dout = nullptr) {
     Frag<double> accR = mCWj;
     double cg = gamma, qi = 0.0;
-    const int i = P.row_con[j];
-    if (i >= 0) {
-      const double a = P.row_a[j];
-      qi = a * frag_dot(Wj, Wj, tm);
-      frag_axpy(accR, a * (rho * P.b[i] - lam_i - rho * qi), Wj);
-      cg += a * rho * qi;
+    if (c.i >= 0) {
+      qi = c.a * frag_dot(Wj, Wj, tm);
+      frag_axpy(accR, c.a * (rho * c.b - lam_i - rho * qi), Wj);
+      cg += c.a * rho * qi;
     }
     Frag<T> rt, wt, gt;
     frag_convert(rt, accR);
+    const T at = (T)c.a;                          // = rowa<T>(P)[j] (0 without a constraint)
     if (dout != nullptr) {
-      const T at = rowa<T>(P)[j];
       const T sa = (T)rho * at * at;
       const T c = sa / ((T)gamma + sa * frag_dot(Wjt, Wjt, tm));
       const T cw = -c * frag_dot(Wjt, rt, tm);
@@ -951,7 +966,7 @@ struct Solver {
       frag_store(wt, dout, j, ld, tm);
       return qi;
     }
-    local_h(rt, Wjt, rowa<T>(P)[j], (T)rho, (T)gamma, wt);
+    local_h(rt, Wjt, at, (T)rho, (T)gamma, wt);
     frag_store(rt, A.R, j, ld, tm);
     frag_store(wt, A.HP, j, ld, tm);
     gt = rt;
@@ -1005,6 +1020,7 @@ struct Solver {
     g3[0] = g3[1] = g3[2] = 0.0;
     const bool shadow = (const void*)A.Vt != (const void*)A.V;
     for (int j = tm.id; j < n; j += tm.count) {
+      const RowCon c = row_con_of(j);
       Frag<double> Wj, mCW;
       Frag<T> Wjt;
       frag_load(Wj, A.V, j, ld, tm);
@@ -1012,8 +1028,7 @@ struct Solver {
       else frag_convert(Wjt, Wj);
       local_mcx_row(j, A.V, A.Dl, false, true, Wj, mCW);
       frag_store(mCW, A.CWn, j, ld, tm);
-      const int i = P.row_con[j];
-      local_r0_row(j, Wj, Wjt, mCW, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3, dout);
+      local_r0_row(j, Wj, Wjt, mCW, c, c.lam, rho, gamma, g3, dout);
     }
     if (!sc.reduce(g3, 3)) return false;
     ++hess;
@@ -1053,6 +1068,54 @@ struct Solver {
     T a_t = (T)shs[1], b_t = T(0);
     __syncthreads();
     it = 0;
+    if (tm.count >= n) {
+      // at most one row per team: its CG state stays in registers across the iterations
+      // (same arithmetic in the same order as below), and only delta is stored at the end
+      const int j = tm.id;
+      const bool have = j < n;
+      Frag<T> r, w, pp, ss, x, Wjt;
+      T aj = T(0);
+      frag_zero(pp);
+      frag_zero(ss);
+      frag_zero(x);
+      if (have) {
+        frag_load(r, A.R, j, ld, tm);
+        frag_load(w, A.HP, j, ld, tm);
+        frag_load(Wjt, Wt, j, ld, tm);
+        aj = ra[j];
+      } else {
+        frag_zero(r);
+        frag_zero(w);
+        frag_zero(Wjt);
+      }
+      while (go && it < prm.cg_max_iter) {
+        double z[2] = {0.0, 0.0};
+        if (have) {
+#pragma unroll
+          for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+            for (int e = 0; e < CHUNK; ++e) {
+              pp.v[k][e] = fma(b_t, pp.v[k][e], r.v[k][e]);
+              ss.v[k][e] = fma(b_t, ss.v[k][e], w.v[k][e]);
+              x.v[k][e] = fma(a_t, pp.v[k][e], x.v[k][e]);
+              r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
+            }
+          local_h(r, Wjt, aj, rho_t, gamma_t, w);
+          const T d1 = frag_dot(r, r, tm), d2 = frag_dot(w, r, tm);
+          if (tm.lane == 0) {
+            z[0] += (double)d1;
+            z[1] += (double)d2;
+          }
+        }
+        if (!sc.reduce(z, 2)) return false;
+        ++hess;
+        ++it;
+        if (!cg_scalars(lead, shs, z, target2, gam, ga, go, a_t, b_t)) break;
+      }
+      if (have && it > 0) frag_store(x, A.Dl, j, ld, tm);
+      cg_iters += it;
+      return true;
+    }
     while (go && it < prm.cg_max_iter) {
       double z[2] = {0.0, 0.0};
       for (int j = tm.id; j < n; j += tm.count) {
@@ -1093,43 +1156,50 @@ struct Solver {
       if (!sc.reduce(z, 2)) return false;
       ++hess;
       ++it;
-      if (lead) {
-        int state = 0;                 // 0: go on, 1: stop, 2: NaN
-        const double gam_new = z[0], del_new = z[1];
-        double alpha = 0.0, beta = 0.0;
-        if (!(gam_new == gam_new) || !(del_new == del_new)) {
-          state = 2;
-        } else if (gam_new <= target2) {
-          state = 1;
-        } else {
-          const double D = del_new * ga - gam_new * gam_new;
-          if (D > 0.0) {
-            const double inv = 1.0 / (gam * D);
-            beta = gam_new * D * inv;
-            alpha = gam_new * ga * gam * inv;
-            ga = gam_new * alpha;
-            gam = gam_new;
-          } else {
-            state = 1;                     // rounding made the denominator non-positive
-          }
-        }
-        shs[0] = (double)state;
-        shs[1] = alpha;
-        shs[2] = beta;
-      }
-      __syncthreads();
-      const int state = (int)shs[0];
-      a_t = (T)shs[1];
-      b_t = (T)shs[2];
-      __syncthreads();
-      if (state == 2) {
-        status = ST_NAN;
-        break;
-      }
-      if (state == 1) break;
+      if (!cg_scalars(lead, shs, z, target2, gam, ga, go, a_t, b_t)) break;
     }
     cg_iters += it;
     return true;
+  }
+
+  // the Chronopoulos-Gear scalars after a reduction z = (r.r, w.r): thread 0 of the CTA
+  // evaluates them (one division) and shares them through shared memory; false when the
+  // CG stops (converged, a non-positive denominator, or NaN, which sets the status)
+  __device__ __forceinline__ bool cg_scalars(bool lead, double* shs, const double* z,
+                                             double target2, double& gam, double& ga, int& go,
+                                             T& a_t, T& b_t) {
+    if (lead) {
+      int state = 0;                 // 0: go on, 1: stop, 2: NaN
+      const double gam_new = z[0], del_new = z[1];
+      double alpha = 0.0, beta = 0.0;
+      if (!(gam_new == gam_new) || !(del_new == del_new)) {
+        state = 2;
+      } else if (gam_new <= target2) {
+        state = 1;
+      } else {
+        const double D = del_new * ga - gam_new * gam_new;
+        if (D > 0.0) {
+          const double inv = 1.0 / (gam * D);
+          beta = gam_new * D * inv;
+          alpha = gam_new * ga * gam * inv;
+          ga = gam_new * alpha;
+          gam = gam_new;
+        } else {
+          state = 1;                     // rounding made the denominator non-positive
+        }
+      }
+      shs[0] = (double)state;
+      shs[1] = alpha;
+      shs[2] = beta;
+    }
+    __syncthreads();
+    const int state = (int)shs[0];
+    a_t = (T)shs[1];
+    b_t = (T)shs[2];
+    __syncthreads();
+    if (state == 2) status = ST_NAN;
+    go = state == 0;
+    return state == 0;
   }
 
   __device__ bool phase2_local(double rho, double& rho_out) {
@@ -1147,6 +1217,7 @@ struct Solver {
       // U^{k+1} = V^k + delta, -(C U^{k+1}), and the V-step's R_0 (W = U^{k+1})
       g3[0] = g3[1] = g3[2] = 0.0;
       for (int j = tm.id; j < n; j += tm.count) {
+        const RowCon c = row_con_of(j);
         Frag<double> Wj, Xj, mCW, mCX;
         Frag<T> Xt;
         frag_load(Wj, A.V, j, ld, tm);
@@ -1166,9 +1237,8 @@ struct Solver {
         frag_store(Xj, A.U, j, ld, tm);
         if (shadow) frag_store(Xt, A.Ut, j, ld, tm);
         frag_store(mCX, A.CWn, j, ld, tm);
-        const int i = P.row_con[j];
-        const double qU = local_r0_row(j, Xj, Xt, mCX, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3);
-        if (i >= 0 && tm.lane == 0) A.e[i] = qU;  // a ||U_j^{k+1}||^2 for the output residual
+        const double qU = local_r0_row(j, Xj, Xt, mCX, c, c.lam, rho, gamma, g3);
+        if (c.i >= 0 && tm.lane == 0) A.e[c.i] = qU;  // a ||U_j^{k+1}||^2 for the output residual
       }
       if (!sc.reduce(g3, 3)) return false;
       ++hess;
@@ -1180,6 +1250,8 @@ struct Solver {
           ((k + 1) % prm.rho_every == 0) ? fmin(rho * prm.rho_growth, prm.rho_max) : rho;
       double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       for (int j = tm.id; j < n; j += tm.count) {
+        const RowCon c = row_con_of(j);
+        const double qU = c.i >= 0 ? A.e[c.i] : 0.0;   // a ||U_j^{k+1}||^2 from pass A
         Frag<double> Wj, Xj, mCW, mCX;
         Frag<T> x, Wt, Vot;
         frag_load(Wj, A.U, j, ld, tm);
@@ -1203,23 +1275,22 @@ struct Solver {
         const double d2 = (double)frag_dot(dV, dV, tm), o2 = (double)frag_dot(Vot, Vot, tm);
         if (exact) frag_convert(Xt, Xj);          // re-rounded from the master every 32
         // dual step lambda_i += rho (a U_j.V_j - b_i)
-        const int i = P.row_con[j];
         double e = 0.0, lam_new = 0.0;
-        if (i >= 0) {
-          e = P.row_a[j] * frag_dot(Wj, Xj, tm) - P.b[i];
-          lam_new = A.lam[i] + rho * e;     // every lane of the team holds the same value
+        if (c.i >= 0) {
+          e = c.a * frag_dot(Wj, Xj, tm) - c.b;
+          lam_new = c.lam + rho * e;        // every lane of the team holds the same value
         }
         local_mcx_row(j, A.U, A.Dl, it > 0, exact, mCW, mCX);
         frag_store(Xj, A.V, j, ld, tm);
         if (shadow) frag_store(Xt, A.Vt, j, ld, tm);
         frag_store(mCX, A.CWn, j, ld, tm);
-        const double qV = local_r0_row(j, Xj, Xt, mCX, lam_new, rho_next, gamma, v + 5);
+        const double qV = local_r0_row(j, Xj, Xt, mCX, c, lam_new, rho_next, gamma, v + 5);
         // the output's row residual a ||(U_j + V_j)/2||^2 - b_i from a||U_j||^2 (pass A),
         // a U_j.V_j = e + b_i and a||V_j||^2
         double eh = 0.0;
-        if (i >= 0) eh = 0.25 * (A.e[i] + 2.0 * (e + P.b[i]) + qV) - P.b[i];
+        if (c.i >= 0) eh = 0.25 * (qU + 2.0 * (e + c.b) + qV) - c.b;
         if (tm.lane == 0) {
-          if (i >= 0) A.lam[i] = lam_new;
+          if (c.i >= 0) A.lam[c.i] = lam_new;
           v[0] += e * e;
           v[1] += eh * eh;
           v[2] += d2;
@@ -1285,6 +1356,7 @@ struct Solver {
       const bool exact = (k + 1) % 32 == 0;
       // pass A: U-step finish and the V-step's solution
       for (int j = tm.id; j < n; j += tm.count) {
+        const RowCon c = row_con_of(j);
         Frag<double> Wj, Xj, mCW, mCX, xd;
         Frag<T> Xt, x;
         frag_load(Wj, A.V, j, ld, tm);
@@ -1300,10 +1372,8 @@ struct Solver {
         frag_store(Xj, A.U, j, ld, tm);
         if (shadow) frag_store(Xt, A.Ut, j, ld, tm);
         frag_store(mCX, A.CWn, j, ld, tm);
-        const int i = P.row_con[j];
-        const double qU =
-            local_r0_row(j, Xj, Xt, mCX, i >= 0 ? A.lam[i] : 0.0, rho, gamma, g3, dV);
-        if (i >= 0 && tm.lane == 0) A.e[i] = qU;  // a ||U_j^{k+1}||^2 for the output residual
+        const double qU = local_r0_row(j, Xj, Xt, mCX, c, c.lam, rho, gamma, g3, dV);
+        if (c.i >= 0 && tm.lane == 0) A.e[c.i] = qU;  // a ||U_j^{k+1}||^2 for the output residual
       }
       if (!sc.sync()) return false;
       ++hess;
@@ -1312,6 +1382,8 @@ struct Solver {
           ((k + 1) % prm.rho_every == 0) ? fmin(rho * prm.rho_growth, prm.rho_max) : rho;
       double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
       for (int j = tm.id; j < n; j += tm.count) {
+        const RowCon c = row_con_of(j);
+        const double qU = c.i >= 0 ? A.e[c.i] : 0.0;   // a ||U_j^{k+1}||^2 from pass A
         Frag<double> Wj, Xj, mCW, mCX, xd;
         Frag<T> x, Wt, Vot;
         frag_load(Wj, A.U, j, ld, tm);
@@ -1330,23 +1402,22 @@ struct Solver {
         const double d2 = (double)frag_dot(dVk, dVk, tm), o2 = (double)frag_dot(Vot, Vot, tm);
         if (exact) frag_convert(Xt, Xj);          // re-rounded from the master every 32
         // dual step lambda_i += rho (a U_j.V_j - b_i)
-        const int i = P.row_con[j];
         double e = 0.0, lam_new = 0.0;
-        if (i >= 0) {
-          e = P.row_a[j] * frag_dot(Wj, Xj, tm) - P.b[i];
-          lam_new = A.lam[i] + rho * e;     // every lane of the team holds the same value
+        if (c.i >= 0) {
+          e = c.a * frag_dot(Wj, Xj, tm) - c.b;
+          lam_new = c.lam + rho * e;        // every lane of the team holds the same value
         }
         local_mcx_row(j, A.U, dV, true, exact, mCW, mCX);
         frag_store(Xj, A.V, j, ld, tm);
         if (shadow) frag_store(Xt, A.Vt, j, ld, tm);
         frag_store(mCX, A.CWn, j, ld, tm);
-        const double qV = local_r0_row(j, Xj, Xt, mCX, lam_new, rho_next, gamma, g3, dU);
+        const double qV = local_r0_row(j, Xj, Xt, mCX, c, lam_new, rho_next, gamma, g3, dU);
         // the output's row residual a ||(U_j + V_j)/2||^2 - b_i from a||U_j||^2 (pass A),
         // a U_j.V_j = e + b_i and a||V_j||^2
         double eh = 0.0;
-        if (i >= 0) eh = 0.25 * (A.e[i] + 2.0 * (e + P.b[i]) + qV) - P.b[i];
+        if (c.i >= 0) eh = 0.25 * (qU + 2.0 * (e + c.b) + qV) - c.b;
         if (tm.lane == 0) {
-          if (i >= 0) A.lam[i] = lam_new;
+          if (c.i >= 0) A.lam[c.i] = lam_new;
           v[0] += e * e;
           v[1] += eh * eh;
           v[2] += d2;
