@@ -375,6 +375,7 @@ struct GridScope {
   long long spin_limit;    // polls before a barrier gives up
   int first = 0;           // the scope spans CTAs [first, first + nb) of a cooperative launch
   int nb = 0;              // (0: the whole grid)
+  unsigned gen_next = 0;   // thread 0: the generation of its next barrier (ctl->gen starts at 0)
 
   __device__ int count() const { return nb > 0 ? nb : (int)gridDim.x; }
   __device__ double* scratch() const { return red + 33 * MAXRED; }
@@ -388,22 +389,29 @@ struct GridScope {
   // the generation with acquire loads (bounded).  Every CTA then loads all partials -- the
   // loads of one lane are issued together, eight CTAs at a time, so their L2 round trips
   // overlap -- and adds them in the same fixed order.
-  // The partials of consecutive barriers go to two buffers chosen by the generation's
-  // parity: a CTA released early may reach the next reduction and store its next partial
-  // while a later CTA still loads this round's, so one buffer would let the later CTA add a
-  // value of the wrong round.  Two rounds suffice, since no CTA passes the next barrier before
-  // every CTA has arrived there, that is, has finished reading this round.
+  // The partials of consecutive barriers go to two buffers chosen by the parity of the
+  // barrier's generation: a CTA released early may reach the next reduction and store its
+  // next partial while a later CTA still loads this round's, so one buffer would let the later
+  // CTA add a value of the wrong round.  Two rounds suffice, since no CTA passes the next
+  // barrier before every CTA has arrived there, that is, has finished reading this round.
+  // Thread 0 knows the generation in advance (the one it saw released, plus one), so the store
+  // needs no load before it; the generation load the wait needs anyway checks it, and a
+  // mismatch is reported as a failed barrier rather than summed.
   __device__ bool barrier(int k) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       int ok = 1;
       unsigned parity = 0;
       if (lane == 0) {
-        // the generation of this barrier: every CTA of the scope reads the same value here
-        const unsigned my_gen = ld_acquire_u32(&ctl->gen);
-        parity = my_gen & 1u;
-        double* mine = partials + (size_t)(my_gen & 1u) * gridDim.x * MAXRED;
+        parity = gen_next & 1u;
+        double* mine = partials + (size_t)parity * gridDim.x * MAXRED;
         for (int i = 0; i < k; ++i) mine[blockIdx.x * MAXRED + i] = red[32 * MAXRED + i];
+        const unsigned my_gen = ld_acquire_u32(&ctl->gen);
+        if (my_gen != gen_next) {
+          atomicExch(&ctl->error, 1);
+          ok = 0;
+        }
+        gen_next = my_gen + 1u;
         const unsigned arrived = atom_add_acq_rel_u32(&ctl->count, 1u);
         if (arrived == (unsigned)count() - 1) {
           ctl->count = 0;
