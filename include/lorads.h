@@ -138,6 +138,9 @@ typedef struct lorads_params {
                            /*    (the matrix is then block diagonal, gamma I + rho a_j^2 W_j  */
                            /*    W_j^T per row, inverted by Sherman-Morrison; Section 1 admits */
                            /*    direct methods): LORADS_ERR_UNSUPPORTED otherwise (0)        */
+  int64_t barrier_polls;   /* polls a grid-wide (or CTA-group) barrier makes before it gives */
+                           /*    up; the solve then ends with LORADS_ERR_DEVICE and the CUDA  */
+                           /*    context stays usable (0 = 50,000,000, a few seconds)          */
   lorads_alloc_fn dev_alloc; /* device allocator (NULL with dev_free: cudaMalloc / cudaFree) */
   lorads_free_fn dev_free;
   void *alloc_ctx;         /* passed to dev_alloc and dev_free                               */

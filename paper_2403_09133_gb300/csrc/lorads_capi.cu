@@ -152,6 +152,12 @@ struct lorads_problem {
 // ---------------------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------------------
+// polls a grid or group barrier makes before it gives up and fails the solve
+// (LORADS_ERR_DEVICE): the caller's limit, else about a few seconds of polling
+static long long barrier_polls(const lorads_params* prm) {
+  return prm->barrier_polls > 0 ? (long long)prm->barrier_polls : 50LL * 1000 * 1000;
+}
+
 static bool is_finite_value(double x) { return std::isfinite(x); }
 
 static int check_cuda(cudaError_t e) {
@@ -635,7 +641,7 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
     CU(Launch<T>::grid_capacity(dv.subsolver, gthreads, &per_sm));
     const int maxg = std::max(1, per_sm) * dev_sms;
     grid = std::min(std::min(grid, maxg), dev_sms * 8);
-    const long long spin = 50LL * 1000 * 1000;   // ~ a few seconds of polling
+    const long long spin = barrier_polls(prm);
     le = Launch<T>::solve_grid(dv.subsolver, dargs, p->dctl, p->dpartials, spin, grid, gthreads,
                                s);
   }
@@ -725,7 +731,7 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
     if (c1 == cudaSuccess && group > 1) c1 = cudaMemsetAsync(dctls, 0, c_bytes, cap);
     const cudaError_t c2 =
         group > 1 ? Launch<T>::solve_group(sub, dargs, count, dqueue, dctls, dparts, dslots, group,
-                                           50LL * 1000 * 1000, grid, threads, cap)
+                                           barrier_polls(prm), grid, threads, cap)
                   : Launch<T>::solve_block(sub, dargs, count, dqueue, grid, threads, cap);
     const cudaError_t c3 = cudaStreamEndCapture(cap, &graph);
     if ((st = check_cuda(c1 != cudaSuccess ? c1 : (c2 != cudaSuccess ? c2 : c3))) != LORADS_OK)
@@ -1326,7 +1332,7 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
     int per_sm = 0;
     CU(Launch<T>::grid_capacity(dv.subsolver, SOLVER_THREADS, &per_sm));
     grid = std::min(std::min(grid, std::max(1, per_sm) * dev_sms), dev_sms * 8);
-    le = Launch<T>::solve_grid(dv.subsolver, dargs, dctl, dpartials, 50LL * 1000 * 1000, grid,
+    le = Launch<T>::solve_grid(dv.subsolver, dargs, dctl, dpartials, barrier_polls(prm), grid,
                                SOLVER_THREADS,
                                s);
   }

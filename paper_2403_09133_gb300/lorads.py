@@ -53,7 +53,7 @@ class lorads_params(ctypes.Structure):
         ("threads", _i32), ("grid", _i32), ("team_mult", _i32),
         ("kkt_dinf", _i32), ("lanczos_steps", _i32), ("dinf_every", _i32),
         ("escape_scale", _f64), ("group", _i32), ("subsolver", _i32),
-        ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+        ("barrier_polls", _i64), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 
 

@@ -61,6 +61,7 @@ def test_default_params_match_oracle_readings(lib):
     assert p.kkt_dinf == int(o.kkt_dinf) and p.dinf_every == o.dinf_every
     assert p.escape_scale == o.escape_scale and p.lanczos_steps > 0
     assert p.subsolver == L.LORADS_SUB_CG and o.subsolver == "cg"
+    assert p.barrier_polls == 0          # library default: about a few seconds of polling
 
 
 def test_status_strings(lib):
