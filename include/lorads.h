@@ -161,8 +161,10 @@ typedef struct lorads_result {
   double gamma;            /* gamma used in Phase II                                         */
   double sigma;            /* final Phase I penalty                                          */
   int32_t admm_iters;      /* Phase II iterations                                            */
-  int32_t cg_iters;        /* CG iterations summed over all subproblems                     */
-  int32_t hessian_applies; /* Hessian-vector products (CG iterations + warm-start residuals) */
+  int32_t cg_iters;        /* CG iterations summed over all subproblems (0 with             */
+                           /*    LORADS_SUB_ROW_DIRECT)                                       */
+  int32_t hessian_applies; /* Hessian-vector products (CG iterations + warm-start residuals; */
+                           /*    with LORADS_SUB_ROW_DIRECT the passes that form R_0 and solve) */
   int32_t alm_outer;       /* Phase I outer iterations                                       */
   int32_t lbfgs_iters;     /* Phase I L-BFGS iterations                                      */
   int32_t rank_growths;    /* rank increases (Phase I and Phase II)                          */
