@@ -7,15 +7,16 @@ ends when the output passes the final test at 1e-6: the paper's primal infeasibi
 the Appendix B gap and dual infeasibility (lambda_min(C - A^T y) by Lanczos on the device), so
 the time of a converged step is the time to KKT <= 1e-6 in those measures.
 
-Prints one JSON line (see README of the repository for the keys):
+Prints one JSON line; its main keys:
   value       solves per second over all ranks (device-resident inputs, CUDA events)
   e2e         the same metric through the C ABI from host buffers (upload + solve + download)
   roofline    the solver kernel's algorithmic bytes / its CUDA-event time vs measured HBM peak
   cpu_baseline  the FP64 CPU oracle timed on a bounded sample of the same workload
 
 `--impl reference` times the CPU oracle alone (the reference arm for this workload).
-Multi-GPU (torchrun): every rank solves its own copy (replicas, weak scaling); rank 0
-prints max-over-ranks timing.
+Multi-GPU (torchrun): every rank solves its own copy of the headline workload (replicas,
+weak scaling) and its share of the batch (no data exchange); rank 0 prints max-over-ranks
+timing.
 """
 from __future__ import annotations
 
@@ -165,8 +166,7 @@ def oracle_sample(inst, seconds, admm_iters_gpu):
 
 # --------------------------------------------------------------------------------- GPU arm
 def algorithmic_bytes(res, n, s, ld):
-    """Algorithmic HBM bytes of one solve's CG operators (roofline section):
-    per CG iteration the Hessian apply reads P and W and writes HP, the update reads delta,
+    """Algorithmic HBM bytes of one solve's CG operators: per CG iteration the Hessian apply reads P and W and writes HP, the update reads delta,
     P, R, HP and writes delta and R, the direction step reads R, P and writes P:
     12 n ld s bytes; each warm-start residual pass reads W (FP64) and writes R, P, delta."""
     cg = res["cg_iters"]

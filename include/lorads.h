@@ -44,7 +44,7 @@ enum {
   LORADS_ERR_MAXITER = -5,      /* iteration cap reached before the tolerance             */
   LORADS_ERR_TIMEOUT = -6,      /* time limit reached before the tolerance                */
   LORADS_ERR_NAN = -7,          /* a NaN or Inf appeared in the iterates or the input     */
-  LORADS_ERR_UNSUPPORTED = -8,  /* constraint structure this build does not handle        */
+  LORADS_ERR_UNSUPPORTED = -8,  /* constraint structure the device solver does not handle  */
   LORADS_ERR_DEVICE = -9,       /* a device-side wait gave up (bounded grid barrier)      */
   LORADS_ERR_TOO_LARGE = -10    /* lorads_solve_static: problem exceeds its fixed scratch */
 };
@@ -194,7 +194,7 @@ int lorads_add_A_sparse(lorads_problem *p, int64_t nnz, const int32_t *con, cons
 
 /* Adds a rank-one term A_con += scale * a a^T with a given by nnz (idx, a) pairs (the
  * sensor-localisation constraints of Section 2.3).  Accepted and kept; the device solver
- * of this build returns LORADS_ERR_UNSUPPORTED for problems that use it. */
+ * returns LORADS_ERR_UNSUPPORTED for problems that use it. */
 int lorads_add_A_rank1(lorads_problem *p, int32_t con, int64_t nnz, const int32_t *idx,
                        const double *a, double scale);
 

@@ -1,5 +1,6 @@
-"""Matrix completion at the full spec size: n = 40,000 (n1 = n2 = 20,000), rank-5
-M = P Q^T, 15,694,167 observed entries, r = 24 (Section 5.4's SDP; the paper's MC_40000).
+"""Matrix completion at the size of the paper's largest MC instance: n = 40,000
+(n1 = n2 = 20,000), rank-5 M = P Q^T, 15,694,167 observed entries, r = 24 (Section 5.4's
+SDP; the paper's MC_40000).
 
 Parity: the FP32 Hessian apply against the oracle on every row; the solve against what the
 problem fixes (exact recovery: objective 2 ||M||_*, and Z = M on entries never observed)."""
