@@ -16,6 +16,11 @@ notation, one function per step, with no fusion or reordering:
     then lambda += rho (A(U V^T) - b); rho *= 1.2 every 5 iterations up to 5000
     (Section 5.1, "The control of penalty factor").
   * Output: U_hat = (U + V)/2, X = U_hat U_hat^T, y = -lambda.
+  * Option (Section 1 admits direct solvers for the subproblems): when every constraint is
+    one diagonal entry, ``Params(subsolver="row_direct")`` solves eq. linU / eq. linV exactly,
+    row block by row block (``row_block_solve``, Sherman-Morrison), instead of by CG.
+  * Checkpoint/resume: ``AdmmState`` holds all Algorithm 1 carries between iterations
+    (U, V, lambda, rho, k, the final-test schedule); ``lradmm_resume`` continues from it.
 
 Readings of points the paper leaves open are parameters of ``Params`` (their defaults
 are the readings the CUDA library uses as well):
