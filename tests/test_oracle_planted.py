@@ -1,0 +1,114 @@
+"""The pins catch plausible mistakes: each test plants one mistake in the oracle (on the CPU,
+through monkeypatch) and checks that the pin that guards that step then fails, while it
+passes on the oracle as written.  Mistakes: a dropped symmetric term in A(U V^T), a dropped
+gamma term in the Hessian, a instead of a^2 in the row-block solve, the sign of lambda in the
+subproblem right-hand side, and y = +lambda in the output."""
+import math
+
+import numpy as np
+
+from oracle import SDP, Params, solve
+import oracle.lorads as L
+from oracle import sdp as S
+from paper_2403_09133_gb300 import instances as I
+from tests.helpers_sdp import random_general_sdp
+
+
+def _A_of_error(sdp, rng):
+    U = rng.standard_normal((sdp.n, 3))
+    V = rng.standard_normal((sdp.n, 3))
+    want = np.array([np.trace(sdp.dense_A(i).T @ (U @ V.T)) for i in range(sdp.m)])
+    return np.abs(sdp.A_of(U, V) - want).max()
+
+
+def test_dropped_symmetric_term_in_A_of(rng, monkeypatch):
+    sdp = SDP.from_instance(random_general_sdp(n=9, m=7, nnz_per_con=3, rng=rng))
+    assert _A_of_error(sdp, rng) <= 1e-12
+
+    def planted(self, U, V):                       # U_r.V_c only, also off the diagonal
+        term = np.einsum("ij,ij->i", U[self.A_row], V[self.A_col])
+        return np.bincount(self.A_con, weights=self.A_val * term, minlength=self.m)
+
+    monkeypatch.setattr(S.SDP, "A_of", planted)
+    assert _A_of_error(sdp, rng) > 1e-3
+
+
+def _hessian_error(sdp, rng, rho=2.5, gamma=0.8, r=3):
+    W = rng.standard_normal((sdp.n, r))
+    P = rng.standard_normal((sdp.n, r))
+    # the matrix of eq. linU from the definition: rho sum_i vec(A_i W) vec(A_i W)^T + gamma I
+    H = gamma * np.eye(sdp.n * r)
+    for i in range(sdp.m):
+        a = (sdp.dense_A(i) @ W).ravel()
+        H += rho * np.outer(a, a)
+    return np.abs(L.hessian_apply(sdp, W, P, rho, gamma).ravel() - H @ P.ravel()).max()
+
+
+def test_dropped_gamma_in_hessian(rng, monkeypatch):
+    sdp = SDP.from_instance(random_general_sdp(n=8, m=5, nnz_per_con=3, rng=rng))
+    assert _hessian_error(sdp, rng) <= 1e-10
+    monkeypatch.setattr(L, "hessian_apply",
+                        lambda sdp, W, P, rho, gamma: rho * sdp.At_times(sdp.A_of(P, W), W))
+    assert _hessian_error(sdp, rng) > 1e-2
+
+
+def _row_solve_error(sdp, rng):
+    r, rho, gamma = 3, 6.0, 0.7
+    W = rng.standard_normal((sdp.n, r))
+    G = rng.standard_normal((sdp.n, r))
+    X = L.row_block_solve(sdp, W, G, rho, gamma)
+    return np.abs(L.hessian_apply(sdp, W, X, rho, gamma) - G).max()
+
+
+def test_a_instead_of_a_squared_in_row_block_solve(rng, monkeypatch):
+    rows = np.array([0, 1, 2, 4, 6])
+    sdp = SDP(7, 5, [0, 1], [1, 2], [1.0, -1.0], np.arange(5), rows, rows,
+              np.array([1.0, 2.0, 0.5, 3.0, 1.0]), np.ones(5))
+    assert _row_solve_error(sdp, rng) <= 1e-12
+
+    def planted(sdp, W, G, rho, gamma):
+        s = np.bincount(sdp.A_row, weights=sdp.A_val, minlength=sdp.n)   # a, not a^2
+        w2 = np.einsum("ij,ij->i", W, W)
+        wg = np.einsum("ij,ij->i", W, G)
+        c = rho * s / (gamma + rho * s * w2)
+        return (G - (c * wg)[:, None] * W) / gamma
+
+    monkeypatch.setattr(L, "row_block_solve", planted)
+    assert _row_solve_error(sdp, rng) > 1e-3
+
+
+def _optv_residual(sdp, rng):
+    """eq. optv_revise after one ADMM iteration (the KKT identity pinned in test_oracle_admm)."""
+    p = Params(cg_rel_tol=1e-14, cg_abs_floor=1e-15, cg_max_iter=5000)
+    U0 = rng.standard_normal((sdp.n, 3))
+    st = L.AdmmState(U=U0.copy(), V=U0.copy(), lam=0.3 * rng.standard_normal(sdp.m), rho=3.0)
+    info = L.admm_iteration(sdp, st, p)
+    U1, V1, lam1 = st.U, st.V, st.lam
+    res = sdp.C_times(U1) - info["gamma"] * (U1 - V1) + sdp.At_times(lam1, U1)
+    return np.linalg.norm(res) / (1 + np.linalg.norm(sdp.C_times(U1)))
+
+
+def test_lambda_sign_in_rhs(rng, monkeypatch):
+    sdp = SDP.from_instance(I.maxcut_er(40, 5.0, seed=8))
+    assert _optv_residual(sdp, np.random.default_rng(1)) <= 1e-8
+    monkeypatch.setattr(L, "subproblem_rhs", lambda sdp, W, lam, rho, gamma:
+                        sdp.At_times(rho * sdp.b + lam, W) - sdp.C_times(W) + gamma * W)
+    assert _optv_residual(sdp, np.random.default_rng(1)) > 1e-3
+
+
+def test_dual_sign_in_output(monkeypatch):
+    """K_n: the dual is y = -(n/4) 1 (closed form); y = +lambda fails it."""
+    n = 8
+    sdp = SDP.from_instance(I.maxcut_complete(n))
+    good = solve(sdp, Params(tol=1e-9, max_admm_iter=4000))
+    assert np.abs(good["y"] + n / 4).max() <= 1e-4 * n
+    real = L.kkt_report
+
+    def planted(sdp, Uh, y, min_eig=None):
+        return real(sdp, Uh, -y, min_eig)
+
+    monkeypatch.setattr(L, "kkt_report", planted)
+    bad = solve(sdp, Params(tol=1e-9, max_admm_iter=4000))
+    # the report built from the wrong sign no longer closes the gap at the K_n optimum
+    assert abs(bad["gap"]) > 1e-3 and abs(good["gap"]) <= 1e-6
+    assert math.isclose(bad["objective"], good["objective"], rel_tol=1e-9)
