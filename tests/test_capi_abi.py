@@ -74,3 +74,32 @@ def test_null_arguments_rejected(lib):
     assert lib.lorads_set_b(None, None) == L.LORADS_ERR_ARG
     assert lib.lorads_solve(None, None, None, None) == L.LORADS_ERR_ARG
     assert lib.lorads_create(0, 5, None) == L.LORADS_ERR_ARG
+
+
+def test_field_offsets_match_header(tmp_path):
+    """Every field of the binding's three structs sits where include/lorads.h puts it
+    (offsetof from a C program compiled against the header), not only the sizes."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    structs = [("lorads_params", L.lorads_params), ("lorads_result", L.lorads_result),
+               ("lorads_state", L.lorads_state)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lorads.h"',
+             "int main(void) {"]
+    for cname, py in structs:
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "offsets.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "offsets"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for cname, py in structs:
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
