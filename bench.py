@@ -52,10 +52,11 @@ def solver_traffic():
         return SOLVER_TRAFFIC["bytes_per_launch"]
     return None
 WORKLOAD = "maxcut_torus_141x141_pm1"
-# Phase II iterations of the FP64 oracle's own full solve of this workload (default
-# parameters, final test at 1e-6; 181 s on one x86 host core): the reference arm and the CPU
-# baseline time a bounded sample and scale it to a whole solve with this count.
-ORACLE_ADMM_ITERS = {WORKLOAD: 1960}
+# The FP64 oracle's own full solve of this workload (default parameters, the final test at
+# 1e-6; tests/golden/make_torus141.py, 603 s on one x86 host core): 1,960 Phase II iterations,
+# then Phase III with 129 Newton steps and 44,780 CG iterations (rank 15 -> 23).  The CPU
+# baseline and the reference arm time a bounded sample of each phase and scale it to these.
+ORACLE_COUNTS = {WORKLOAD: {"admm_iters": 1960, "newton_steps": 129, "newton_cg": 44780}}
 
 
 def parse():
@@ -135,15 +136,31 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------------- CPU oracle
-def oracle_sample(inst, seconds, admm_iters_gpu):
-    """Times the FP64 CPU oracle on a bounded sample: Phase I in full, then Phase II
-    iterations until `seconds` elapse; scales to one solve of `admm_iters_gpu` iterations
-    (the oracle's own count for this workload).  The final test's eigenvalue checks are not
-    in the sample (one dense/ARPACK check at the last iteration of the full solve)."""
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def oracle_sample_here(workload, seconds, counts):
+    """The FP64 CPU oracle on a bounded sample of one solve (this process): Phase I in full,
+    Phase II iterations for half the budget, then Phase III's Newton-CG iterations (each a
+    Hessian-vector product on the product of spheres) at the Phase II point for the other half;
+    the per-iteration times are scaled to `counts` (a projection, not a full solve)."""
     from oracle import SDP, Params
     import oracle.lorads as OL
+    inst = make_instance(workload)
     sdp = SDP.from_instance(inst)
-    p = Params()
+    p = OL.resolve_auto(sdp, Params())
     t0 = time.perf_counter()
     r = OL.initial_rank(sdp.m, sdp.n, p)
     ph1 = OL.lralm(sdp, OL.initial_factor(sdp, r, p.seed), p)
@@ -151,27 +168,59 @@ def oracle_sample(inst, seconds, admm_iters_gpu):
     st = OL.AdmmState(U=ph1["U"].copy(), V=ph1["U"].copy(), lam=ph1["lam"].copy(),
                       rho=min(p.h * ph1["sigma"], p.rho_max), rp=ph1["rp"])
     k = 0
-    while time.perf_counter() - t1 < seconds and k < admm_iters_gpu:
+    while time.perf_counter() - t1 < 0.5 * seconds and k < counts["admm_iters"]:
         OL.admm_iteration(sdp, st, p)
         k += 1
     t2 = time.perf_counter()
-    per_iter = (t2 - t1) / max(k, 1)
-    solve_s = (t1 - t0) + per_iter * admm_iters_gpu
-    cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
-    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"Phase I in full ({t1 - t0:.2f} s) + {k} Phase II iterations "
-                      f"({per_iter * 1e3:.2f} ms each), scaled to {admm_iters_gpu} iterations",
+    rad, con, a = OL.sphere_structure(sdp)
+    U = OL.retract(0.5 * (st.U + st.V), rad)
+    _, mu, CU = OL.manifold_multiplier(sdp, U, con, a)
+    g = 2.0 * (CU - mu[:, None] * U)
+    j = 0
+    while time.perf_counter() - t2 < 0.5 * seconds and j < counts["newton_cg"]:
+        OL.truncated_cg(lambda Z: OL.riemannian_hessian(sdp, U, mu, Z), g, 1)
+        j += 1
+    t3 = time.perf_counter()
+    per_admm = (t2 - t1) / max(k, 1)
+    per_cg = (t3 - t2) / max(j, 1)
+    solve_s = (t1 - t0) + per_admm * counts["admm_iters"] + per_cg * counts["newton_cg"]
+    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": f"projection: Phase I in full ({t1 - t0:.2f} s), {k} Phase II iterations "
+                      f"({per_admm * 1e3:.2f} ms each) and {j} Phase III CG iterations "
+                      f"({per_cg * 1e3:.2f} ms each) timed on one thread, scaled to "
+                      f"{counts['admm_iters']} and {counts['newton_cg']} (the oracle's own "
+                      f"full solve of this workload)",
             "seconds_per_solve": solve_s}
 
 
+def oracle_sample(workload, seconds, counts):
+    """oracle_sample_here in a child process pinned to one BLAS / OpenMP thread, so that the
+    baseline's thread count is known (the oracle is numpy/scipy code)."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+              "BLIS_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample_here(%r, %r, %r)))"
+            % (ROOT, workload, float(seconds), dict(counts)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=30 * 60)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 # --------------------------------------------------------------------------------- GPU arm
-def algorithmic_bytes(res, n, s, ld):
-    """Algorithmic HBM bytes of one solve's CG operators: per CG iteration the Hessian apply reads P and W and writes HP, the update reads delta,
-    P, R, HP and writes delta and R, the direction step reads R, P and writes P:
-    12 n ld s bytes; each warm-start residual pass reads W (FP64) and writes R, P, delta."""
-    cg = res["cg_iters"]
-    r0 = res["hessian_applies"] - cg
-    return cg * 12 * n * ld * s + r0 * n * ld * (8 + 3 * s)
+def algorithmic_bytes(res, n, s):
+    """Algorithmic bytes of one solve's Hessian applies, 3 n ld s per apply (read P and the fixed
+    factor W, write H P; ld = 4 ceil(r / 4), s the element size): Phase II's applies (CG
+    iterations and warm-start residuals, in the form's element type, at the initial rank's ld)
+    plus Phase III's Newton-CG applies (FP64, at the final rank's ld)."""
+    r0 = res.get("rank0", res["rank"])
+    ld0 = (r0 + 3) // 4 * 4
+    ld1 = (res["rank"] + 3) // 4 * 4
+    return res["hessian_applies"] * 3 * n * ld0 * s + res["newton_cg_iters"] * 3 * n * ld1 * 8
 
 
 def run_gpu(args):
@@ -267,9 +316,13 @@ def run_gpu(args):
             dist.destroy_process_group()
         return None
     rm, rf = results["mixed"]["res"], results["fp64"]["res"]
-    ld = (rm["rank"] + 3) // 4 * 4
-    bytes_mixed = algorithmic_bytes(rm, inst.n, 4, ld)
-    bytes_fp64 = algorithmic_bytes(rf, inst.n, 8, (rf["rank"] + 3) // 4 * 4)
+    r0 = int(np.ceil(np.log2(max(inst.m, 2))))
+    rm["rank0"] = rf["rank0"] = r0
+    bytes_mixed = algorithmic_bytes(rm, inst.n, 4)
+    bytes_fp64 = algorithmic_bytes(rf, inst.n, 8)
+    tol = 1e-6
+    kkt_ok = lambda r: (r["status"] == 0 and r["r_P"] <= tol and r["r_D"] <= tol
+                        and abs(r["gap"]) <= tol and r["dual_psd"] <= tol)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -294,17 +347,24 @@ def run_gpu(args):
                    "r0": rm["rank"], "form": "mixed", "parallelism": "replicas",
                    "l2": "256 MB buffer written between timed solves"},
         "solve": {k: rm[k] for k in ("status", "objective", "dual_objective", "r_P", "r_P_split",
-                                    "r_stop", "r_D", "gap", "p_infeas", "d_infeas", "lambda_min",
-                                    "admm_iters", "cg_iters", "hessian_applies", "alm_outer",
-                                    "lbfgs_iters", "rank", "rank_growths", "gamma",
-                                    "time_phase1_s", "time_phase2_s")},
-        "kkt": {"tol": 1e-6, "reached": rm["status"] == 0,
-                "primal_r_P_binf": rm["r_P"], "appendix_b_p_infeas": rm["p_infeas"],
-                "appendix_b_d_infeas": rm["d_infeas"], "appendix_b_gap": rm["gap"]},
+                                    "r_stop", "r_D", "gap", "p_infeas", "d_infeas", "dual_psd",
+                                    "lambda_min", "admm_iters", "cg_iters", "hessian_applies",
+                                    "alm_outer", "lbfgs_iters", "rank", "rank_growths", "gamma",
+                                    "polished", "newton_steps", "newton_cg_iters",
+                                    "time_phase1_s", "time_phase2_s", "time_phase3_s")},
+        # the final test: max(r_P, r_D) <= 1e-6 with r_D = ||(C - A^T y) U_hat||_F/(1+||C||_F),
+        # the Appendix B gap, and lambda_min(C - A^T y) >= -1e-6 (1 + ||C||_inf) (Lanczos)
+        "kkt": {"tol": tol, "reached": kkt_ok(rm), "r_P": rm["r_P"], "r_D": rm["r_D"],
+                "gap": rm["gap"], "lambda_min": rm["lambda_min"], "dual_psd": rm["dual_psd"],
+                "appendix_b_p_infeas": rm["p_infeas"], "appendix_b_d_infeas": rm["d_infeas"]},
         "plain_fp64": {"ms_per_solve": t_fp64 * 1e3, "status": rf["status"],
+                       "kkt_reached": kkt_ok(rf),
                        "time_phase1_s": rf["time_phase1_s"], "time_phase2_s": rf["time_phase2_s"],
+                       "time_phase3_s": rf["time_phase3_s"],
                        "objective": rf["objective"], "admm_iters": rf["admm_iters"],
-                       "cg_iters": rf["cg_iters"], "d_infeas": rf["d_infeas"], "gap": rf["gap"],
+                       "cg_iters": rf["cg_iters"], "newton_steps": rf["newton_steps"],
+                       "newton_cg_iters": rf["newton_cg_iters"], "rank": rf["rank"],
+                       "r_D": rf["r_D"], "dual_psd": rf["dual_psd"], "gap": rf["gap"],
                        "objective_rel_diff_vs_mixed":
                            abs(rf["objective"] - rm["objective"]) / abs(rf["objective"]),
                        "cg_operator_gbs": bytes_fp64 / t_fp64 / 1e9},
@@ -316,15 +376,20 @@ def run_gpu(args):
                    "cg_iters": r["cg_iters"], "objective": r["objective"],
                    "objective_rel_diff_vs_cg_mixed":
                        abs(r["objective"] - rm["objective"]) / abs(rm["objective"]),
-                   "r_P": r["r_P"], "gap": r["gap"], "d_infeas": r["d_infeas"],
-                   "speedup_vs_cg_mixed": t_mixed / t}
+                   "r_P": r["r_P"], "r_D": r["r_D"], "gap": r["gap"], "dual_psd": r["dual_psd"],
+                   "kkt_reached": kkt_ok(r), "speedup_vs_cg_mixed": t_mixed / t}
             for form, r, t in (("mixed", results["mixed_row_direct"]["res"], t_mixed_d),
                                ("fp64", results["fp64_row_direct"]["res"], t_fp64_d))},
         "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "traffic": solver_traffic(),
-                     "kernel": "lorads::solve_grid_kernel<float>",
+                     "kernel": "lorads::solve_grid_kernel<float, 0>",
+                     "unit_bytes": "3 n ld s per Hessian apply (Phase II, FP32) plus 3 n ld 8 "
+                                   "per Phase III Newton-CG apply (FP64)",
+                     "bytes_per_launch": bytes_mixed,
+                     "l2_resident": True,
+                     "working_set_bytes": 3 * inst.n * ((rm["rank"] + 3) // 4 * 4) * 8,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
         "gpu_launches": args.steps,
         "clocks": clocks,
@@ -336,8 +401,10 @@ def run_gpu(args):
     if not args.no_learned:
         line["learned_warm_start"] = learned_bench(args)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(
-            inst, args.oracle_seconds, ORACLE_ADMM_ITERS.get(args.workload, rm["admm_iters"]))
+        counts = ORACLE_COUNTS.get(args.workload, {"admm_iters": rf["admm_iters"],
+                                                     "newton_steps": rf["newton_steps"],
+                                                     "newton_cg": rf["newton_cg_iters"]})
+        line["cpu_baseline"] = oracle_sample(args.workload, args.oracle_seconds, counts)
     if world > 1:
         dist.destroy_process_group()
     return line
@@ -481,12 +548,13 @@ def run_reference(args):
     if rank != 0:
         return None
     inst = make_instance(args.workload)
-    iters = ORACLE_ADMM_ITERS.get(args.workload, 5000)
+    counts = ORACLE_COUNTS.get(args.workload,
+                               {"admm_iters": 5000, "newton_steps": 0, "newton_cg": 0})
     vals = []
     last = None
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        last = oracle_sample(inst, args.oracle_seconds / max(1, args.steps), iters)
+        last = oracle_sample(args.workload, args.oracle_seconds / max(1, args.steps), counts)
         t1 = time.perf_counter()
         if it >= args.warmup:
             vals.append(last["value"])
@@ -498,7 +566,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": inst.n, "m": inst.m, "form": "oracle"},
         "cpu_baseline": {"value": v, "unit": "solves/s", "cores": last["cores"],
-                         "kind": "oracle", "sample": last["sample"]},
+                         "kind": "oracle", "cpu": last["cpu"], "sample": last["sample"]},
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

@@ -118,10 +118,14 @@ typedef struct lorads_params {
   int32_t grid;            /* solver CTAs (0 = library choice; 1 forces one-CTA scope)       */
   int32_t team_mult;       /* lanes per factor row = team_mult x the minimum for the rank    */
                            /* (1, 2, 4, 8; 0 = 1, or autotuned by lorads_solve_batch)         */
-  int32_t kkt_dinf;        /* 1: the final test includes the Appendix B dual infeasibility   */
-                           /*    (needs lanczos_steps > 0); 0: primal test and gap only (1)   */
-  int32_t lanczos_steps;   /* Lanczos steps of each lambda_min(C - A^T y) estimate, <= 512;  */
-                           /*    0 = no estimate (kkt_dinf must be 0) (128)                   */
+  int32_t kkt_dinf;        /* 1: the final test includes the dual measure                    */
+                           /*    max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf) (needs      */
+                           /*    lanczos_steps > 0); 0: r_P, gap and r_D only (1)             */
+  int32_t lanczos_steps;   /* Lanczos steps of each lambda_min(C - A^T y) estimate, at most, */
+                           /*    <= 2048; the recurrence stops earlier once the estimate moved */
+                           /*    by at most 0.05 tol (1 + ||C||_inf) over its last doubling of */
+                           /*    steps (checked at 128, 256, ...); 0 = no estimate (kkt_dinf   */
+                           /*    must be 0) (2048)                                            */
   int32_t dinf_every;      /* after a failed dual-infeasibility test at iteration k, the next */
                            /*    waits max(dinf_every, k / 10) iterations (10)                */
   double escape_scale;     /* when a dual-infeasibility test fails less than 10% below the   */
@@ -138,6 +142,15 @@ typedef struct lorads_params {
                            /*    (the matrix is then block diagonal, gamma I + rho a_j^2 W_j  */
                            /*    W_j^T per row, inverted by Sherman-Morrison; Section 1 admits */
                            /*    direct methods): LORADS_ERR_UNSUPPORTED otherwise (0)        */
+  int32_t polish;          /* Phase III, a refinement of eq. prob:BM's stationarity (not in  */
+                           /*    the paper), entered when Phase II's output passes the primal */
+                           /*    test and the gap but not r_D: Newton's method on the product */
+                           /*    of spheres when every row carries exactly one diagonal       */
+                           /*    constraint a X_jj = b, b/a > 0 (MaxCut with n = m), else     */
+                           /*    Phase I's augmented Lagrangian method continued from Phase  */
+                           /*    II's output; 1 = on, 0 = Phase II alone (1)                  */
+  int32_t newton_max;      /* Phase III Newton steps, at most (200)                          */
+  int32_t newton_cg_max;   /* CG iterations of one Newton step, at most (1000)               */
   int64_t barrier_polls;   /* polls a grid-wide (or CTA-group) barrier makes before it gives */
                            /*    up; the solve then ends with LORADS_ERR_DEVICE and the CUDA  */
                            /*    context stays usable (0 = 50,000,000, a few seconds)          */
@@ -169,10 +182,21 @@ typedef struct lorads_result {
   int32_t lbfgs_iters;     /* Phase I L-BFGS iterations                                      */
   int32_t rank_growths;    /* rank increases (Phase I and Phase II)                          */
   double time_phase1_s;    /* device time of Phase I                                         */
-  double time_phase2_s;    /* device time of Phase II and the output step                    */
+  double time_phase2_s;    /* device time of Phase II (and the output step without Phase III) */
   double p_infeas;         /* ||A(X) - b||_2 / (1 + ||b||_1)                    (Appendix B)  */
   double d_infeas;         /* max(0, -lambda_min) / (1 + ||vec(C)||_1)          (Appendix B)  */
   double lambda_min;       /* Lanczos estimate of lambda_min(C - A^T y) (NaN: not computed)  */
+  double dual_psd;         /* max(0, -lambda_min) / (1 + ||C||_inf): the final test's dual   */
+                           /*    measure (||C||_inf = max_j sum_k |C_jk|; it does not grow    */
+                           /*    with n the way ||vec(C)||_1 does)                            */
+  double time_phase3_s;    /* device time of Phase III and the output step (0: no Phase III) */
+  int32_t polished;        /* Phase III: 0 none, 1 Newton on the product of spheres, 2 the   */
+                           /*    augmented Lagrangian method of Phase I continued            */
+  int32_t newton_steps;    /* Phase III Newton steps                                         */
+  int32_t newton_cg_iters; /* Phase III CG iterations, summed over the Newton steps          */
+  int32_t refine_outer;    /* Phase III augmented-Lagrangian outer iterations                */
+  int32_t refine_lbfgs_iters; /* Phase III L-BFGS iterations                                 */
+  int32_t reserved;        /* 0                                                              */
 } lorads_result;
 
 typedef struct lorads_problem lorads_problem;
@@ -214,12 +238,16 @@ int lorads_set_start(lorads_problem *p, int32_t r, const double *U0, const doubl
 
 /* Algorithm 2 on the device.  stream is a cudaStream_t (NULL = the legacy default stream);
  * the call returns when the solve has finished.  res may be NULL.  The return value is
- * the solve status (also res->status).  Phase II ends (LORADS_OK) when the output
- * X = U_hat U_hat^T, y = -lambda passes, in this order: the paper's termination
- * ||A(X) - b||_2 / (1 + ||b||_inf) <= tol (Section 5.2), the Appendix B gap |gap| <= tol, and,
- * with kkt_dinf, the Appendix B dual infeasibility <= tol (lambda_min by Lanczos, tested at
- * most once per max(dinf_every, k/10) iterations after a failure); otherwise after
- * max_admm_iter iterations with LORADS_ERR_MAXITER. */
+ * the solve status (also res->status).  The solve ends (LORADS_OK) when the output
+ * X = U_hat U_hat^T, y = -lambda passes the final test: the paper's termination
+ * r_P = ||A(X) - b||_2 / (1 + ||b||_inf) <= tol (Section 5.2), the Appendix B gap |gap| <= tol,
+ * the stationarity r_D = ||(C - A^T y) U_hat||_F / (1 + ||C||_F) <= tol (eq. def:eKKT), and,
+ * with kkt_dinf, the dual measure max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf) <= tol
+ * (lambda_min by Lanczos, tested at most once per max(dinf_every, k/10) iterations after a
+ * test that did not end the solve).  With polish = 1 the first Phase II output that passes
+ * r_P and the gap is handed to Phase III, which ends the solve when r_P, r_D and the dual
+ * measure pass.  Otherwise the solve ends with LORADS_ERR_MAXITER after max_admm_iter Phase II
+ * iterations, newton_max Newton steps or max_outer augmented-Lagrangian iterations. */
 int lorads_solve(lorads_problem *p, const lorads_params *prm, void *stream, lorads_result *res);
 
 /* Solves count independent problems (same device) in one persistent launch: one CTA (or a
@@ -312,13 +340,19 @@ int lorads_set_state(lorads_problem *p, const lorads_state *st, const double *U,
  *
  * Outputs go to caller DEVICE buffers: U_hat as n x ldu row-major doubles (ldu >= the final
  * rank, which is at most the rank cap; columns beyond the final rank are left unchanged),
- * y (length m, y = -lambda); either may be NULL.  res (host) receives the report.
+ * y (length m, y = -lambda); either may be NULL.  res (host) receives the report.  The
+ * problem's own solution from its last lorads_solve (what lorads_get_solution and
+ * lorads_get_state return) is left as it was.
  *
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every call shares
- * the one array and leaves the last call's contents in it; the call clears what must start
- * at zero.  Calls that overlap on the GPU (several streams or host threads at once) race on
- * the array: serialize them.  The call returns when the solve has finished on stream. */
+ * The call that assembles the problem also prepares this one: with the problem's device
+ * current it loads the library's device code (CUDA loads modules lazily by default, and
+ * loading a module allocates device memory, this array included) and looks up the array's
+ * device address with cudaGetSymbolAddress.  The solve launches with the geometry
+ * lorads_solve picks for the same parameters (grid, threads, team_mult), so the two give
+ * the same iterates.  Every call shares the one array and leaves the last call's contents
+ * in it; the call clears what must start at zero.  Calls that overlap on the GPU (several
+ * streams or host threads at once) race on the array: serialize them.  The call blocks until
+ * the solve has finished on stream. */
 #define LORADS_STATIC_SCRATCH_BYTES (32ull << 20)
 int lorads_solve_static(lorads_problem *p, const lorads_params *prm, void *stream,
                         double *U_hat, int64_t ldu, double *y, lorads_result *res);

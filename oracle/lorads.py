@@ -24,7 +24,10 @@ notation, one function per step, with no fusion or reordering:
 
 Readings of points the paper leaves open are parameters of ``Params`` (their defaults
 are the readings the CUDA library uses as well):
-  * gamma is never given a value; gamma = ||C||_inf (largest absolute row sum of C);
+  * gamma is never given a value; gamma = s ||C||_inf (largest absolute row sum of C), with
+    s = 1 for the MaxCut class (every constraint one diagonal entry on its own row, b/a > 0)
+    and s = 2 otherwise; the phase-switch tolerance and the heuristic factor h follow the same
+    class (1e-2 and 10 for MaxCut, Section 5.1; 1e-3 and 1 otherwise): ``resolve_auto``;
   * the multiplier enters eq. ALF with a plus sign, so the SDP dual is y = -lambda;
   * with phi's multiplier normalised as in eq. ALF, the switch takes lambda_0 = lambda_hat
     (the paper's 1/2 factor belongs to the normalisation of eq. def:eKKT);
@@ -76,12 +79,13 @@ class Params:
     rank_max: int = 0             # 0 -> min(floor(sqrt(2 m)), n, 256)
     rank_factor: float = 1.5      # Section 4.3 / 5.1
     tol: float = 1e-6             # final tolerance
-    switch_tol: float = 1e-2      # Section 5.1: 1e-2 for MaxCut, 1e-3 otherwise
-    h: float = 10.0               # Section 5.1: heuristic factor (10 for MaxCut)
+    switch_tol: Optional[float] = None   # Section 5.1: None = by problem class (resolve_auto)
+    h: Optional[float] = None     # Section 5.1: heuristic factor; None = by problem class
     rho_max: float = 5000.0       # Section 5.1
     rho_growth: float = 1.2       # Section 5.1
     rho_every: int = 5            # Section 5.1
-    gamma_scale: float = 1.0      # gamma = gamma_scale * ||C||_inf (paper silent) ...
+    gamma_scale: Optional[float] = None  # gamma = gamma_scale * ||C||_inf (paper silent);
+                                  # None = by problem class (resolve_auto) ...
     gamma_fixed: float = 0.0      # ... unless gamma_fixed > 0
     max_admm_iter: int = 5000     # Section 5.2
     cg_max_iter: int = 1000
@@ -103,6 +107,13 @@ class Params:
     escape_scale: float = 0.3     # Phase II rank growth along the lambda_min eigenvector
     subsolver: str = "cg"         # eq. linU / linV: "cg" (Section 4.4) or "row_direct"
                                   # (exact block solve; every constraint one diagonal entry)
+    polish: str = "auto"          # Phase III, a refinement of eq. prob:BM's stationarity once
+                                  # Phase II's output passes r_P and the gap: "auto" = Newton
+                                  # on the product of spheres where every row carries one
+                                  # diagonal constraint, else the Phase I method continued;
+                                  # "off" = Phase II alone
+    newton_max: int = 200         # Phase III Newton steps, at most
+    newton_cg_max: int = 1000     # CG iterations of one Newton step, at most
 
 
 # ======================================================================================
@@ -204,6 +215,14 @@ def dual_infeasibility(sdp: SDP, y) -> float:
     return max(0.0, -min_eig_dual_slack(sdp, y)) / (1.0 + sdp.c_one)
 
 
+def dual_psd_measure(sdp: SDP, y) -> float:
+    """Size-independent dual infeasibility max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf).
+    Appendix B divides the same eigenvalue by 1 + ||vec C||_1, which grows with n (about
+    4 10^4 on the 141 x 141 torus) and so lets lambda_min = -2 10^-4 pass at 10^-6; the row-sum
+    norm ||C||_inf bounds ||C||_2 and does not grow with n."""
+    return max(0.0, -min_eig_dual_slack(sdp, y)) / (1.0 + sdp.C_rowsum_max)
+
+
 def dual_stationarity(sdp: SDP, Uh, lam) -> float:
     """||(C + A^T(lambda)) U_hat||_F / (1 + ||C||_F): first line of eq. def:eKKT with
     f = <C, .> and multiplier 2 lambda (Theorem 1), i.e. y = -lambda."""
@@ -283,6 +302,29 @@ def row_block_solve(sdp: SDP, W, G, rho, gamma):
     return (G - (c * wg)[:, None] * W) / gamma
 
 
+def maxcut_class(sdp: SDP) -> bool:
+    """Every constraint is a single diagonal entry on a row of its own with b_i / a_i > 0 (the
+    MaxCut SDP of Section 5.3, X_jj = 1): the class for which Section 5.1 states a phase-switch
+    tolerance of 1e-2."""
+    return diagonal_row_scaling(sdp) is not None
+
+
+def resolve_auto(sdp: SDP, p: Params) -> Params:
+    """Fills the parameters left at None by the problem class (Section 5.1 states 1e-2 as the
+    switch tolerance for MaxCut and 1e-3 for other problems, and h = 10 for MaxCut; h and gamma
+    otherwise are readings): MaxCut class -> switch_tol 1e-2, h 10, gamma_scale 1; any other
+    problem -> switch_tol 1e-3, h 1, gamma_scale 2.  Explicit values are kept."""
+    mc = maxcut_class(sdp)
+    q = Params(**{**asdict(p)})
+    if q.switch_tol is None:
+        q.switch_tol = 1e-2 if mc else 1e-3
+    if q.h is None:
+        q.h = 10.0 if mc else 1.0
+    if q.gamma_scale is None:
+        q.gamma_scale = 1.0 if mc else 2.0
+    return q
+
+
 def penalty_gamma(sdp: SDP, p: Params) -> float:
     """gamma of eq. prob:penalty.  The paper fixes no value; the U-step moves U along
     -(C + A^T lambda) V / gamma, so gamma is tied to the scale of C through the row-sum
@@ -290,7 +332,8 @@ def penalty_gamma(sdp: SDP, p: Params) -> float:
     if p.gamma_fixed > 0:
         return p.gamma_fixed
     cinf = sdp.C_rowsum_max
-    return p.gamma_scale * (cinf if cinf > 0 else 1.0)
+    scale = p.gamma_scale if p.gamma_scale is not None else resolve_auto(sdp, p).gamma_scale
+    return scale * (cinf if cinf > 0 else 1.0)
 
 
 @dataclass
@@ -307,6 +350,8 @@ class AdmmState:
     # the dual infeasibility of the latest failed test since the last rank growth
     next_dual_test: int = 0
     prev_dinf: Optional[float] = None
+    # set when Phase II hands over to Phase III (primal test and gap passed, r_D not yet)
+    polish: bool = False
 
 
 def admm_iteration(sdp: SDP, st: AdmmState, p: Params) -> dict:
@@ -370,44 +415,196 @@ def lradmm_resume(sdp: SDP, state: AdmmState, p: Params, trace: Optional[list] =
     return _lradmm_loop(sdp, st, p, trace)
 
 
+def polish_applies(sdp: SDP, p: Params) -> bool:
+    """Phase III takes its Newton form when every row carries exactly one diagonal constraint
+    a_i U_j.U_j = b_i with b_i / a_i > 0 (MaxCut, Section 5.3, with n = m): the feasible set of
+    eq. prob:BM is then a product of spheres of radius sqrt(b_i / a_i), on which the projection
+    is a row scaling.  Other problems take the augmented-Lagrangian form (alm_refine)."""
+    return p.polish == "auto" and sdp.n == sdp.m and maxcut_class(sdp)
+
+
 def _lradmm_loop(sdp: SDP, st: AdmmState, p: Params, trace: Optional[list]):
+    """Algorithm 1 with the final test on the output X = U_hat U_hat^T, y = -lambda:
+    r_P(X) <= tol (Section 5.2), |gap| <= tol (Appendix B), the stationarity of eq. def:eKKT
+    r_D = ||(C - A^T y) U_hat||_F / (1 + ||C||_F) <= tol and the dual measure
+    max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf) <= tol (tested at most once per
+    max(dinf_every, k // 10) iterations after a test that did not end the solve).  Where Phase III
+    applies, the first iterate that passes the primal test and the gap while r_D > tol is handed
+    over to it (st.polish)."""
     converged = False
     cap = rank_cap(sdp.m, sdp.n, p)
+    polish = p.polish == "auto"
     while st.k < p.max_admm_iter:
         info = admm_iteration(sdp, st, p)
         if info["rp_hat"] <= p.tol:
             Uh = 0.5 * (st.U + st.V)
             y = -st.lam
             info["gap"] = pd_gap(sdp, Uh, y)
+            info["r_D"] = dual_stationarity(sdp, Uh, st.lam)
             if abs(info["gap"]) <= p.tol:
-                if not p.kkt_dinf:
-                    converged = True
+                if polish and info["r_D"] > p.tol:
+                    st.polish = True
+                elif not p.kkt_dinf:
+                    converged = info["r_D"] <= p.tol
                 elif st.k >= st.next_dual_test:
-                    info["d_inf"] = dual_infeasibility(sdp, y)
-                    if info["d_inf"] <= p.tol:
+                    info["d_psd"] = dual_psd_measure(sdp, y)
+                    if info["d_psd"] <= p.tol and info["r_D"] <= p.tol:
                         converged = True
                     else:
                         st.next_dual_test = st.k + max(p.dinf_every, st.k // 10)
                         r = st.U.shape[1]
-                        if (st.prev_dinf is not None and info["d_inf"] > 0.9 * st.prev_dinf
+                        if info["d_psd"] <= p.tol:
+                            pass
+                        elif (st.prev_dinf is not None and info["d_psd"] > 0.9 * st.prev_dinf
                                 and p.escape_scale > 0 and r < cap):
-                            _, z = min_eig_pair_dual_slack(sdp, y)
                             r_new = max(next_rank(r, cap, p), r + 1)
-                            tau = p.escape_scale * float(np.linalg.norm(Uh)) / math.sqrt(r)
-                            add = np.zeros((sdp.n, r_new - r))
-                            add[:, 0] = tau * z
-                            st.U = np.concatenate([st.U, add], axis=1)
-                            st.V = np.concatenate([st.V, add], axis=1)
+                            st.U = escape_columns(sdp, st.U, Uh, y, r_new, p)
+                            st.V = escape_columns(sdp, st.V, Uh, y, r_new, p)
                             st.growths += 1
                             info["grow_to"] = r_new
                             st.prev_dinf = None
                         else:
-                            st.prev_dinf = info["d_inf"]
+                            st.prev_dinf = info["d_psd"]
         if trace is not None:
             trace.append(info)
-        if converged:
+        if converged or st.polish:
             break
     return st, converged
+
+
+def escape_columns(sdp: SDP, W, Uh, y, r_new: int, p: Params):
+    """W with r_new - r columns appended: tau z, then zeros, where z is the unit eigenvector of
+    lambda_min(C - A^T y) and tau = escape_scale ||U_hat||_F / sqrt(r) (the size of an average
+    column): a descent direction of eq. prob:BM's objective when lambda_min < 0."""
+    _, z = min_eig_pair_dual_slack(sdp, y)
+    r = W.shape[1]
+    tau = p.escape_scale * float(np.linalg.norm(Uh)) / math.sqrt(r)
+    add = np.zeros((sdp.n, r_new - r))
+    add[:, 0] = tau * z
+    return np.concatenate([W, add], axis=1)
+
+
+# ======================================================================================
+# Phase III (not in the paper): Newton refinement of eq. prob:BM's stationarity
+# ======================================================================================
+# Algorithm 1's dual stationarity falls only like 1/k on degenerate instances (the +-1 torus:
+# r_D = 4.8e-4 after 10^3 iterations, 1.7e-5 after 3.2 10^4), while r_D <= 1e-6 asks for a
+# relative gap of about 1e-13 there.  When every row carries one diagonal constraint the
+# feasible set of eq. prob:BM is a product of spheres, and Newton's method on that manifold
+# (Absil, Mahony and Sepulchre, "Optimization Algorithms on Matrix Manifolds", 2008, Ch. 6;
+# the Burer-Monteiro MaxCut setting of Boumal, Voroninski and Bandeira, 2016) converges
+# quadratically from the point Phase II reaches.  Each Newton step solves its system by
+# truncated CG (Nocedal and Wright, "Numerical Optimization", Algorithm 7.1) with Hessian-vector
+# products built from the same C-times-dense product as the ADMM subproblems.
+def sphere_structure(sdp: SDP):
+    """Per row j: the sphere radius sqrt(b_i / a_i) of its constraint i, i, and a_i."""
+    rows, target = diagonal_row_scaling(sdp)
+    rad = np.zeros(sdp.n)
+    rad[rows] = target
+    con = np.full(sdp.n, -1, dtype=np.int64)
+    con[sdp.A_row] = sdp.A_con
+    a = np.zeros(sdp.n)
+    a[sdp.A_row] = sdp.A_val
+    return rad, con, a
+
+
+def retract(U, rad):
+    """Projection onto the product of spheres: row j scaled to length rad_j."""
+    return U * (rad / np.linalg.norm(U, axis=1))[:, None]
+
+
+def tangent_project(U, Z):
+    """Row j of Z minus its component along U_j (the tangent space of the sphere at U_j)."""
+    return Z - (np.einsum("ij,ij->i", Z, U) / np.einsum("ij,ij->i", U, U))[:, None] * U
+
+
+def manifold_multiplier(sdp: SDP, U, con, a):
+    """On the product of spheres, the multiplier minimising ||(C + A^T lambda) U||_F: row j
+    gives (C U)_j + a_i lambda_i U_j, so a_i lambda_i = -(C U)_j.U_j / ||U_j||^2 =: -mu_j.
+    Returns lambda (indexed by constraint), mu and C U."""
+    CU = sdp.C_times(U)
+    mu = np.einsum("ij,ij->i", CU, U) / np.einsum("ij,ij->i", U, U)
+    lam = np.zeros(sdp.m)
+    lam[con] = -mu / a
+    return lam, mu, CU
+
+
+def riemannian_hessian(sdp: SDP, U, mu, Z):
+    """Hessian of <C, U U^T> on the product of spheres applied to a tangent Z:
+    2 P_U(C Z - mu Z) (the Euclidean Hessian 2 C Z projected, plus the curvature term of the
+    spheres -2 mu_j Z_j)."""
+    return 2.0 * tangent_project(U, sdp.C_times(Z) - mu[:, None] * Z)
+
+
+def truncated_cg(hess: Callable, g, max_iter: int):
+    """Newton direction d ~ -Hess^{-1} g by CG from d = 0 (Nocedal and Wright, Algorithm 7.1):
+    stops at ||Hess d + g|| <= eta ||g||, eta = min(0.5, sqrt(||g||)), or at a direction of
+    non-positive curvature (then the steepest-descent direction -g if no step was taken yet)."""
+    gn = float(np.linalg.norm(g))
+    eta = min(0.5, math.sqrt(gn))
+    d = np.zeros_like(g)
+    res = -g
+    pdir = res.copy()
+    rr = float(np.vdot(res, res))
+    for j in range(max_iter):
+        Hp = hess(pdir)
+        pHp = float(np.vdot(pdir, Hp))
+        if pHp <= 0.0:
+            return (-g if j == 0 else d), j
+        alpha = rr / pHp
+        d = d + alpha * pdir
+        res = res - alpha * Hp
+        rr_new = float(np.vdot(res, res))
+        if math.sqrt(rr_new) <= eta * gn:
+            return d, j + 1
+        pdir = res + (rr_new / rr) * pdir
+        rr = rr_new
+    return d, max_iter
+
+
+def bm_newton_polish(sdp: SDP, U0, p: Params) -> dict:
+    """Phase III from U0 (Phase II's U_hat): Newton steps on the product of spheres, each
+    followed by an Armijo backtracking line search (sufficient decrease 1e-4, step halved)
+    along the retraction, until r_D(U, lambda(U)) <= tol; then the dual test
+    max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf) <= tol.  A failed dual test means the rank
+    is too small: the rank grows as in Phase II (a column tau z along the eigenvector of
+    lambda_min) and the Newton steps go on.  On the manifold A(U U^T) = b holds to rounding and
+    the gap with y = -lambda(U) vanishes identically (<C, U U^T> = sum_j mu_j ||U_j||^2 = b^T y)."""
+    rad, con, a = sphere_structure(sdp)
+    cap = rank_cap(sdp.m, sdp.n, p)
+    U = retract(U0, rad)
+    steps = cg_total = growths = 0
+    converged = False
+    lam = np.zeros(sdp.m)
+    while True:
+        lam, mu, CU = manifold_multiplier(sdp, U, con, a)
+        g = 2.0 * (CU - mu[:, None] * U)                 # the Riemannian gradient, 2 S U
+        r_D = float(np.linalg.norm(g)) / (2.0 * (1.0 + sdp.C_fro))
+        if r_D <= p.tol:
+            if not p.kkt_dinf or dual_psd_measure(sdp, -lam) <= p.tol:
+                converged = True
+                break
+            r = U.shape[1]
+            if r >= cap or p.escape_scale <= 0:
+                break
+            U = retract(escape_columns(sdp, U, U, -lam, max(next_rank(r, cap, p), r + 1), p),
+                        rad)
+            growths += 1
+            continue
+        if steps >= p.newton_max:
+            break
+        d, j = truncated_cg(lambda Z: riemannian_hessian(sdp, U, mu, Z), g, p.newton_cg_max)
+        cg_total += j
+        f0 = sdp.C_inner(U, U)
+        slope = float(np.vdot(g, d))
+        t = 1.0
+        Un = retract(U + d, rad)
+        while sdp.C_inner(Un, Un) > f0 + 1e-4 * t * slope and t > 2.0 ** -30:
+            t *= 0.5
+            Un = retract(U + t * d, rad)
+        U = Un
+        steps += 1
+    return dict(U=U, lam=lam, converged=converged, steps=steps, cg=cg_total, growths=growths)
 
 
 # ======================================================================================
@@ -505,14 +702,23 @@ def grow_rank(U, r_new: int, seed: int, growth_index: int, std: float):
     return np.concatenate([U, extra], axis=1)
 
 
-def lralm(sdp: SDP, U0, p: Params, trace: Optional[list] = None):
-    """Phase I: augmented Lagrangian on eq. prob:BM, L-BFGS inner solves, dynamic rank."""
+def lralm(sdp: SDP, U0, p: Params, trace: Optional[list] = None, lam0=None, sigma0=None,
+          refine: bool = False, growth0: int = 0):
+    """Phase I: augmented Lagrangian on eq. prob:BM, L-BFGS inner solves, dynamic rank.
+
+    With refine=True the same method continues from (U0, lam0, sigma0) -- Phase II's output --
+    until the multiplier-updated pair meets the primal test and the stationarity of
+    eq. def:eKKT: r_P <= tol and r_D = ||(C + A^T lambda) U||_F / (1 + ||C||_F) <= tol (after
+    an inner solve, (C + A^T(lambda + sigma e)) U is half the gradient of phi, so r_D is read
+    from it).  Rank growths draw from streams growth0 + 1, ..."""
+    p = resolve_auto(sdp, p)
     U = U0.copy()
-    lam = np.zeros(sdp.m)
-    sigma = 1.0 / (1.0 + sdp.b_inf)
+    lam = np.zeros(sdp.m) if lam0 is None else np.asarray(lam0, dtype=np.float64).copy()
+    sigma = 1.0 / (1.0 + sdp.b_inf) if sigma0 is None else float(sigma0)
     cap = rank_cap(sdp.m, sdp.n, p)
     rp_prev = math.inf
-    growths = 0
+    growths = growth0
+    done = False
     inner_total = 0
     rp = primal_infeasibility(sdp, U, U)
     outer = 0
@@ -557,8 +763,15 @@ def lralm(sdp: SDP, U0, p: Params, trace: Optional[list] = None):
         r = U.shape[1]
         if trace is not None:
             trace.append(dict(outer=outer, inner=it, rp=rp, sigma=sigma, rank=r, stalled=stalled))
-        if rp <= p.switch_tol:
+        if refine:
+            r_D = float(np.linalg.norm(g)) / (2.0 * (1.0 + sdp.C_fro))
+            if rp <= p.tol and r_D <= p.tol:
+                lam = lam + sigma * e
+                done = True
+                break
+        elif rp <= p.switch_tol:
             lam = lam + sigma * e
+            done = True
             break
         if stalled and r < cap:
             # Section 4.3: stop the subproblem, raise the rank, carry on
@@ -569,8 +782,38 @@ def lralm(sdp: SDP, U0, p: Params, trace: Optional[list] = None):
         if rp > p.sigma_decrease * rp_prev:
             sigma *= p.sigma_factor
         rp_prev = rp
-    return dict(U=U, lam=lam, sigma=sigma, outer=outer, inner=inner_total, growths=growths,
-                rp=rp)
+    return dict(U=U, lam=lam, sigma=sigma, outer=outer, inner=inner_total,
+                growths=growths - growth0, rp=rp, done=done)
+
+
+def alm_refine(sdp: SDP, U0, lam0, sigma0: float, p: Params, growth0: int) -> dict:
+    """Phase III for problems outside the product-of-spheres class: the augmented Lagrangian
+    method of Phase I continued from Phase II's output (U_hat, lambda) with Phase I's last
+    penalty sigma, until r_P <= tol and r_D <= tol, then the dual test
+    max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf) <= tol; a failed dual test grows the rank
+    along the eigenvector of lambda_min (as in Phase II) and the method goes on."""
+    cap = rank_cap(sdp.m, sdp.n, p)
+    U, lam, sigma = U0.copy(), np.asarray(lam0, dtype=np.float64).copy(), float(sigma0)
+    outer = inner = growths = 0
+    converged = False
+    while True:
+        ph = lralm(sdp, U, p, lam0=lam, sigma0=sigma, refine=True, growth0=growth0 + growths)
+        U, lam, sigma = ph["U"], ph["lam"], ph["sigma"]
+        outer += ph["outer"]
+        inner += ph["inner"]
+        growths += ph["growths"]
+        if not ph["done"]:
+            break
+        if not p.kkt_dinf or dual_psd_measure(sdp, -lam) <= p.tol:
+            converged = True
+            break
+        r = U.shape[1]
+        if r >= cap or p.escape_scale <= 0:
+            break
+        U = escape_columns(sdp, U, U, -lam, max(next_rank(r, cap, p), r + 1), p)
+        growths += 1
+    return dict(U=U, lam=lam, sigma=sigma, converged=converged, outer=outer, inner=inner,
+                growths=growths)
 
 
 # ======================================================================================
@@ -590,12 +833,14 @@ def kkt_report(sdp: SDP, Uh, y, min_eig: Optional[float] = None) -> dict:
     if min_eig is not None:
         rep["lambda_min"] = min_eig
         rep["d_infeas"] = max(0.0, -min_eig) / (1.0 + sdp.c_one)
+        rep["dual_psd"] = max(0.0, -min_eig) / (1.0 + sdp.C_rowsum_max)
     return rep
 
 
 def lorads(sdp: SDP, p: Params = Params(), U0=None, lam0=None, rho0=None,
            trace: Optional[dict] = None) -> dict:
     """Algorithm 2.  Returns U, V, U_hat, lambda, y and the KKT report."""
+    p = resolve_auto(sdp, p)
     t0 = time.perf_counter()
     tr1: list = []
     tr2: list = []
@@ -605,14 +850,27 @@ def lorads(sdp: SDP, p: Params = Params(), U0=None, lam0=None, rho0=None,
         ph1 = lralm(sdp, U_init, p, tr1)
         U_bm, lam_bm, sigma = ph1["U"], ph1["lam"], ph1["sigma"]
         rho = min(p.h * sigma, p.rho_max)
+        sigma_last = sigma
     else:
         ph1 = dict(outer=0, inner=0, growths=0, rp=math.nan)
         U_bm = U0
         lam_bm = np.zeros(sdp.m) if lam0 is None else lam0
         rho = 100.0 if rho0 is None else rho0
+        sigma_last = 1.0 / (1.0 + sdp.b_inf)
     t1 = time.perf_counter()
     st, converged = lradmm(sdp, U_bm, U_bm, lam_bm, rho, p, tr2)
     t2 = time.perf_counter()
+    ph3 = dict(steps=0, cg=0, growths=0, outer=0, inner=0)
+    if st.polish:
+        Uh = 0.5 * (st.U + st.V)
+        if polish_applies(sdp, p):
+            ph3 = {**ph3, **bm_newton_polish(sdp, Uh, p)}
+        else:
+            ph3 = {**ph3, **alm_refine(sdp, Uh, st.lam, sigma_last, p,
+                                       ph1["growths"] + st.growths)}
+        st.U, st.V, st.lam = ph3["U"], ph3["U"].copy(), ph3["lam"]
+        converged = ph3["converged"]
+    t3 = time.perf_counter()
     Uh = 0.5 * (st.U + st.V)
     y = -st.lam
     rep = kkt_report(sdp, Uh, y, min_eig_dual_slack(sdp, y))
@@ -621,5 +879,8 @@ def lorads(sdp: SDP, p: Params = Params(), U0=None, lam0=None, rho0=None,
         trace["phase2"] = tr2
     return dict(U=st.U, V=st.V, U_hat=Uh, lam=st.lam, y=y, rank=Uh.shape[1],
                 converged=converged, admm_iters=st.k, cg_iters=st.cg_iters, rho=st.rho,
-                alm_outer=ph1["outer"], lbfgs_iters=ph1["inner"], growths=ph1["growths"] + st.growths,
-                t_phase1=t1 - t0, t_phase2=t2 - t1, **rep)
+                alm_outer=ph1["outer"], lbfgs_iters=ph1["inner"],
+                growths=ph1["growths"] + st.growths + ph3["growths"],
+                polished=st.polish, newton_steps=ph3["steps"], newton_cg=ph3["cg"],
+                refine_outer=ph3["outer"], refine_lbfgs=ph3["inner"],
+                t_phase1=t1 - t0, t_phase2=t2 - t1, t_phase3=t3 - t2, **rep)

@@ -1,7 +1,8 @@
 """Builds liblorads.so (the C ABI of include/lorads.h) in-tree with nvcc for sm_103a.
 
-Six translation units compile in parallel (the FP64 and FP32 solver kernels with CG, the
-same with the exact row-block subproblem solve, the host runtime, the learned warm start)
+Seven translation units compile in parallel (the FP64 and FP32 solver kernels with CG, the
+FP64 one-CTA kernel apart, the same with the exact row-block subproblem solve, the host
+runtime, the learned warm start)
 and link into one shared library next to this file.  Usage: python -m paper_2403_09133_gb300.build
 """
 from __future__ import annotations
@@ -15,10 +16,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblorads.so")
-SOURCES = ["lorads_f64.cu", "lorads_f32.cu", "lorads_f64_direct.cu", "lorads_f32_direct.cu",
-           "lorads_capi.cu", "lorads_gnn.cu"]
+SOURCES = ["lorads_f64.cu", "lorads_f64_block.cu", "lorads_f32.cu", "lorads_f64_direct.cu",
+           "lorads_f32_direct.cu", "lorads_capi.cu", "lorads_gnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+# per-unit ptxas flags: the one-CTA FP64 solver kernel is built at ptxas -O1 (see that file)
+UNIT_FLAGS = {"lorads_f64_block.cu": ["-Xptxas", "-O1"]}
 
 
 def nvcc() -> str:
@@ -44,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([nvcc(), *ARCH, *FLAGS, *UNIT_FLAGS.get(src, []), "-c", s, "-o", o])
 
     def run(cmd):
         if verbose:

@@ -202,6 +202,8 @@ static void build_sym_csr(int64_t n, std::vector<SymEntry>& ent, std::vector<int
   }
 }
 
+static void static_path_setup(int device);
+
 // assemble the device form of (C, A, b)
 static int assemble(lorads_problem* p, const DevAlloc& al) {
   if (p->assembled) return p->assemble_status;
@@ -374,6 +376,7 @@ static int assemble(lorads_problem* p, const DevAlloc& al) {
     row_a[con_r[i]] = con_a[i];
   }
   dp.a_diag_only = diag_only ? 1 : 0;
+  dp.polish_ok = (diag_only && dsep && n == m) ? 1 : 0;
   if (diag_only) {
     std::vector<float> row_af(row_a.begin(), row_a.end());
     int* d_row_con = a.take<int>(n);
@@ -389,6 +392,7 @@ static int assemble(lorads_problem* p, const DevAlloc& al) {
   p->dp = dp;
   p->assembled = true;
   p->assemble_status = LORADS_OK;
+  static_path_setup(p->device);
   return LORADS_OK;
 }
 
@@ -463,6 +467,11 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   dv.escape_scale = prm->escape_scale;
   if (!(prm->escape_scale >= 0.0)) return LORADS_ERR_ARG;
   dv.subsolver = prm->subsolver;
+  if (prm->polish != 0 && prm->polish != 1) return LORADS_ERR_ARG;
+  if (prm->newton_max < 0 || prm->newton_cg_max < 1) return LORADS_ERR_ARG;
+  dv.polish = prm->polish;
+  dv.newton_max = prm->newton_max;
+  dv.newton_cg_max = prm->newton_cg_max;
   if (prm->subsolver != 0 && prm->subsolver != 1) return LORADS_ERR_ARG;
   if (prm->subsolver == 1 && !p->dp.a_diag_only) return LORADS_ERR_UNSUPPORTED;
   if (prm->lanczos_steps < 0 || prm->lanczos_steps > LANCZOS_MAX) return LORADS_ERR_ARG;
@@ -597,6 +606,13 @@ static void to_result(const SolveOut& out, lorads_result& r) {
   r.p_infeas = out.p_infeas;
   r.d_infeas = out.d_infeas;
   r.lambda_min = out.lambda_min;
+  r.dual_psd = out.dual_psd;
+  r.time_phase3_s = out.t_phase3_ns * 1e-9;
+  r.polished = out.polished;
+  r.newton_steps = out.newton_steps;
+  r.newton_cg_iters = out.newton_cg;
+  r.refine_outer = out.refine_outer;
+  r.refine_lbfgs_iters = out.refine_lbfgs;
 }
 
 static void record_solution(lorads_problem* p, const SolveOut& out, const lorads_result& r) {
@@ -607,43 +623,64 @@ static void record_solution(lorads_problem* p, const SolveOut& out, const lorads
   p->has_solution = out.ld > 0;
 }
 
+// Launch geometry of a single-problem solve: one CTA for small problems (n < 512), the whole
+// GPU from a few hundred rows up.  One-CTA solves take prm->threads (default SOLVER_THREADS);
+// whole-GPU solves take prm->threads or, by default, enough teams for one row each at the
+// initial rank, within [128, 320] threads, and at most as many CTAs as are co-resident.
+// lorads_solve and lorads_solve_static both launch with it, so that the same parameters
+// give the same reduction order and iterates on either path.
+template <typename T>
+static int solve_geometry(const lorads_problem* p, const lorads_params* prm,
+                          const DevParams& dv, int dev_sms, bool* whole_gpu, int* grid_out,
+                          int* threads_out) {
+  int grid = prm->grid;
+  if (grid <= 0) grid = (p->n < 512) ? 1 : dev_sms;
+  *whole_gpu = grid != 1;
+  if (grid == 1) {
+    const int threads = prm->threads > 0 ? prm->threads : SOLVER_THREADS;
+    if (threads % 32 != 0 || threads > BLOCK_THREADS_MAX) return LORADS_ERR_ARG;
+    *grid_out = 1;
+    *threads_out = threads;
+    return LORADS_OK;
+  }
+  int gthreads = prm->threads > 0 ? prm->threads : 0;
+  if (gthreads == 0) {
+    const int G = team_size_for(round4(dv.phase1 ? dv.r0 : p->start_r)) * dv.team_mult;
+    const long long lanes = (long long)p->n * std::min(G, 32);
+    const int per = (int)((lanes + grid - 1) / grid);
+    gthreads = std::min(GRID_THREADS_MAX, std::max(128, ((per + 31) / 32) * 32));
+  }
+  if (gthreads % 32 != 0 || gthreads > GRID_THREADS_MAX) return LORADS_ERR_ARG;
+  int per_sm = 0;
+  CU(Launch<T>::grid_capacity(dv.subsolver, gthreads, &per_sm));
+  const int maxg = std::max(1, per_sm) * dev_sms;
+  *grid_out = std::min(std::min(grid, maxg), dev_sms * 8);
+  *threads_out = gthreads;
+  return LORADS_OK;
+}
+
 template <typename T>
 static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s,
                      lorads_result* res) {
   DevParams dv;
   int st = fill_params(p, prm, dv);
   if (st != LORADS_OK) return st;
+  int dev_sms = 0;
+  CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
+  bool whole = false;
+  int grid = 1, threads = SOLVER_THREADS;
+  st = solve_geometry<T>(p, prm, dv, dev_sms, &whole, &grid, &threads);
+  if (st != LORADS_OK) return st;
   SolverArgs<T> h;
   SolverArgs<T>* dargs = nullptr;
   st = prepare_state<T>(p, dv, s, DevAlloc::from(prm, s), h, &dargs);
   if (st != LORADS_OK) return st;
-  int dev_sms = 0;
-  CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
-  // scope: one CTA for small problems, the whole GPU from a few hundred rows up
-  int grid = prm->grid;
-  if (grid <= 0) grid = (p->n < 512) ? 1 : dev_sms;
-  const int threads = (grid == 1 && prm->threads > 0) ? prm->threads : SOLVER_THREADS;
-  if (threads % 32 != 0 || threads > BLOCK_THREADS_MAX) return LORADS_ERR_ARG;
   cudaError_t le;
-  if (grid == 1) {
+  if (!whole) {
     le = Launch<T>::solve_block(dv.subsolver, dargs, 1, p->dqueue, 1, threads, s);
   } else {
-    // CTA size: enough teams for one row each at the initial rank, within [128, 320]
-    int gthreads = prm->threads > 0 ? prm->threads : 0;
-    if (gthreads == 0) {
-      const int G = team_size_for(round4(dv.phase1 ? dv.r0 : p->start_r)) * dv.team_mult;
-      const long long lanes = (long long)p->n * std::min(G, 32);
-      const int per = (int)((lanes + grid - 1) / grid);
-      gthreads = std::min(GRID_THREADS_MAX, std::max(128, ((per + 31) / 32) * 32));
-    }
-    if (gthreads % 32 != 0 || gthreads > GRID_THREADS_MAX) return LORADS_ERR_ARG;
-    int per_sm = 0;
-    CU(Launch<T>::grid_capacity(dv.subsolver, gthreads, &per_sm));
-    const int maxg = std::max(1, per_sm) * dev_sms;
-    grid = std::min(std::min(grid, maxg), dev_sms * 8);
-    const long long spin = barrier_polls(prm);
-    le = Launch<T>::solve_grid(dv.subsolver, dargs, p->dctl, p->dpartials, spin, grid, gthreads,
-                               s);
+    le = Launch<T>::solve_grid(dv.subsolver, dargs, p->dctl, p->dpartials, barrier_polls(prm),
+                               grid, threads, s);
   }
   CU(le);
   SolveOut out{};
@@ -902,10 +939,13 @@ void lorads_default_params(lorads_params* prm) {
   prm->grid = 0;
   prm->team_mult = 0;
   prm->kkt_dinf = 1;
-  prm->lanczos_steps = 128;
+  prm->lanczos_steps = 2048;
   prm->dinf_every = 10;
   prm->escape_scale = 0.3;
   prm->group = 0;
+  prm->polish = 1;
+  prm->newton_max = 200;
+  prm->newton_cg_max = 1000;
 }
 
 int lorads_set_start(lorads_problem* p, int32_t r, const double* U0, const double* lambda0,
@@ -1248,17 +1288,35 @@ struct DeviceGuard {
 
 }  // namespace
 
+// Set-up of lorads_solve_static on `device` (current), done when a problem is assembled:
+// loads the modules of the solver kernels and of this file (CUDA loads modules lazily by
+// default, and loading one allocates device memory for its code and its __device__ data,
+// g_static_scratch included) and resolves the array's address.  Failures are left for the
+// static call itself to report.
+static void static_path_setup(int device) {
+  unsigned char* base = nullptr;
+  int per_sm = 0;
+  for (int sub = 0; sub < 2; ++sub) {
+    Launch<float>::block_capacity(sub, SOLVER_THREADS, &per_sm);
+    Launch<float>::grid_capacity(sub, SOLVER_THREADS, &per_sm);
+    Launch<double>::block_capacity(sub, SOLVER_THREADS, &per_sm);
+    Launch<double>::grid_capacity(sub, SOLVER_THREADS, &per_sm);
+  }
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, static_negate_kernel);
+  cudaGetLastError();
+  static_scratch_address(device, &base);
+}
+
 template <typename T>
 static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStream_t s,
                             double* U_hat, int64_t ldu, double* y, lorads_result* res) {
   const int64_t n = p->n, m = p->m;
-  // the solve's state lives in the shared scratch array: an earlier solve's state in p's
-  // arena no longer belongs to the latest solve
-  p->has_solution = false;
+  // The solve's state lives in the shared scratch array; p's own arena (and with it the
+  // last lorads_solve's solution and checkpoint, which lorads_get_solution / get_state
+  // read) is left as it is.
   DevParams dv;
-  lorads_params q = *prm;
-  q.team_mult = 1;
-  const int pst = fill_params(p, &q, dv);
+  const int pst = fill_params(p, prm, dv);
   if (pst != LORADS_OK) return pst;
   const int cap = dv.rank_cap;
   if (!dv.phase1 && (!p->has_start || p->start_r > 256)) return LORADS_ERR_STATE;
@@ -1270,8 +1328,12 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   const bool mixed = sizeof(T) == 4;
   int dev_sms = 0;
   CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
+  bool whole = false;
+  int grid = 1, threads = SOLVER_THREADS;
+  int st = solve_geometry<T>(p, prm, dv, dev_sms, &whole, &grid, &threads);
+  if (st != LORADS_OK) return st;
   unsigned char* base = nullptr;
-  int st = static_scratch_address(p->device, &base);
+  st = static_scratch_address(p->device, &base);
   if (st != LORADS_OK) return st;
   StaticCarve a{base, (size_t)LORADS_STATIC_SCRATCH_BYTES, 0};
   SolverArgs<T> h{};
@@ -1323,18 +1385,12 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   CU(cudaMemsetAsync(dctl, 0, sizeof(GridCtl), s));
   CU(cudaMemsetAsync(dpartials, 0xFF, sizeof(double) * (size_t)dev_sms * 8 * MAXRED * 3, s));
   CU(cudaMemsetAsync(dqueue, 0, 16, s));
-  int grid = prm->grid;
-  if (grid <= 0) grid = (n < 512) ? 1 : dev_sms;
   cudaError_t le;
-  if (grid == 1) {
-    le = Launch<T>::solve_block(dv.subsolver, dargs, 1, dqueue, 1, SOLVER_THREADS, s);
+  if (!whole) {
+    le = Launch<T>::solve_block(dv.subsolver, dargs, 1, dqueue, 1, threads, s);
   } else {
-    int per_sm = 0;
-    CU(Launch<T>::grid_capacity(dv.subsolver, SOLVER_THREADS, &per_sm));
-    grid = std::min(std::min(grid, std::max(1, per_sm) * dev_sms), dev_sms * 8);
     le = Launch<T>::solve_grid(dv.subsolver, dargs, dctl, dpartials, barrier_polls(prm), grid,
-                               SOLVER_THREADS,
-                               s);
+                               threads, s);
   }
   CU(le);
   SolveOut out{};

@@ -55,6 +55,9 @@ struct DevProblem {
   const int* row_con;
   const double* row_a;
   const float* row_af;
+  // every row carries exactly one diagonal constraint with b/a > 0 (n = m, row_norm set): the
+  // feasible set of the Burer-Monteiro problem is a product of spheres (Phase III applies)
+  int polish_ok;
 };
 
 template <typename T> __device__ __forceinline__ const T* cval(const DevProblem& P);

@@ -154,7 +154,7 @@ LORADS_DECLARE_SOLVE_LAUNCH(float, 0)
 LORADS_DECLARE_SOLVE_LAUNCH(double, 1)
 LORADS_DECLARE_SOLVE_LAUNCH(float, 1)
 
-#define LORADS_DEFINE_SOLVE_LAUNCH(T, SUB)                                                     \
+#define LORADS_DEFINE_SOLVE_LAUNCH_BLOCK(T, SUB)                                               \
   template <>                                                                                  \
   cudaError_t SolveLaunch<T, SUB>::solve_block(const SolverArgs<T>* args, int count,           \
                                                int* queue, int grid, int threads,              \
@@ -167,7 +167,9 @@ LORADS_DECLARE_SOLVE_LAUNCH(float, 1)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,                        \
                                                          solve_block_kernel<T, SUB>, threads,  \
                                                          0);                                   \
-  }                                                                                            \
+  }
+
+#define LORADS_DEFINE_SOLVE_LAUNCH_MULTI(T, SUB)                                               \
   template <>                                                                                  \
   cudaError_t SolveLaunch<T, SUB>::solve_grid(const SolverArgs<T>* args, GridCtl* ctl,         \
                                               double* partials, long long spin, int grid,      \
@@ -198,6 +200,10 @@ LORADS_DECLARE_SOLVE_LAUNCH(float, 1)
                                                          solve_group_kernel<T, SUB>, threads,  \
                                                          0);                                   \
   }
+
+#define LORADS_DEFINE_SOLVE_LAUNCH(T, SUB) \
+  LORADS_DEFINE_SOLVE_LAUNCH_BLOCK(T, SUB) \
+  LORADS_DEFINE_SOLVE_LAUNCH_MULTI(T, SUB)
 
 // the solver launchers by run-time subproblem solver, and the operator launchers
 template <typename T>

@@ -40,6 +40,8 @@ struct DevParams {
   int dinf_every;
   double escape_scale;   // Phase II rank growth along the lambda_min eigenvector (0: off)
   int subsolver;         // 0: CG on eq. linU / linV; 1: exact row-block solve (the kernel's SUB)
+  int polish;            // Phase III (Newton on the product of spheres) where it applies
+  int newton_max, newton_cg_max;
   // continuation of a checkpointed Phase II (resume = 1): V is given apart from U, and the
   // iteration counter, the final-test schedule and the reported counters go on from here
   int resume;
@@ -47,7 +49,7 @@ struct DevParams {
   double prev_dinf0, sigma0;
 };
 
-constexpr int LANCZOS_MAX = 512;   // Lanczos steps of one lambda_min estimate, at most
+constexpr int LANCZOS_MAX = 2048;  // Lanczos steps of one lambda_min estimate, at most
 
 struct SolveOut {
   int status, rank, ld, admm_iters, cg_iters, hess_applies, alm_outer, lbfgs_iters, growths;
@@ -56,8 +58,9 @@ struct SolveOut {
   int pad;
   double prev_dinf;
   double objective, dual_objective, r_P, r_P_split, r_stop, r_D, gap, rho, gamma, sigma;
-  double p_infeas, d_infeas, lambda_min;
-  long long t_phase1_ns, t_phase2_ns;
+  double p_infeas, d_infeas, lambda_min, dual_psd;
+  long long t_phase1_ns, t_phase2_ns, t_phase3_ns;
+  int polished, newton_steps, newton_cg, refine_outer, refine_lbfgs, pad2;
 };
 
 // status values written to SolveOut (mirror the public codes)
@@ -181,13 +184,21 @@ struct Solver {
   double uh_norm2;    // ||U_hat||_F^2 from the latest gap test
   double rs_num, rs_den;   // ||V^{k+1} - V^k||^2, ||V^k||^2 of the row-local loop (< 0: unused)
   int ndt;            // first Phase II iteration at which the dual-infeasibility test may run
-  double pdinf;       // dual infeasibility of the latest failed test since the last growth
+  double pdinf;       // dual measure of the latest failed test since the last growth
+  double last_rd2;    // ||(C + A^T lambda) U_hat||_F^2 from the latest final test
+  bool to_polish;     // Phase II handed its output to Phase III
+  bool fp64_bulk;     // Phase I's bulk products read the FP64 masters (Phase III refinement)
+  bool alm_done;      // the augmented Lagrangian loop met its stopping rule
+  int refine_outer, refine_lbfgs;
+  int newton_steps, newton_cg;
+  long long t_p3;     // start of Phase III (0: none)
 
   __device__ Solver(const SolverArgs<T>& a, Scope& s)
       : A(a), sc(s), P(a.P), prm(a.prm), n(a.P.n), m(a.P.m), r(0), ld(0), status(ST_OK),
         cg_iters(0), hess(0), admm_iters(0), alm_outer(0), lbfgs_iters(0), growths(0),
         last_rs(0.0), last_lmin(NAN), lmin_at(-1), uh_norm2(0.0), rs_num(-1.0), rs_den(0.0),
-        ndt(0), pdinf(NAN) {}
+        ndt(0), pdinf(NAN), last_rd2(0.0), to_polish(false), fp64_bulk(false), alm_done(false),
+        refine_outer(0), refine_lbfgs(0), newton_steps(0), newton_cg(0), t_p3(0) {}
 
   __device__ void set_rank(int rr) {
     r = rr;
@@ -238,10 +249,11 @@ struct Solver {
   }
 
   // e = A(U U^T) - b (stored), returns ||e||^2
-  __device__ bool eval_residual_UU(double& e2) {
+  template <typename E>
+  __device__ bool eval_residual_UU_e(const E* Ub, double& e2) {
     double v[1] = {0.0};
     for (int i = tmc.id; i < m; i += tmc.count) {
-      const double q = sddmm_con<T>(P, A.Ut, A.Ut, ld, i, tmc);
+      const double q = sddmm_con<E>(P, Ub, Ub, ld, i, tmc);
       const double ei = q - P.b[i];
       if (tmc.lane == 0) {
         A.e[i] = ei;
@@ -253,14 +265,19 @@ struct Solver {
     return true;
   }
 
+  __device__ bool eval_residual_UU(double& e2) {
+    return fp64_bulk ? eval_residual_UU_e<double>(A.U, e2) : eval_residual_UU_e<T>(A.Ut, e2);
+  }
+
   // grad = 2 (C + A^T(lambda + sigma e)) U, returns ||grad||_F^2
-  __device__ bool eval_grad(double sigma, double& g2) {
+  template <typename E>
+  __device__ bool eval_grad_e(const E* Ub, double sigma, double& g2) {
     double v[1] = {0.0};
     if (P.a_diag_only) {
       for (int j = tm.id; j < n; j += tm.count) {
-        Frag<T> ot;
+        Frag<E> ot;
         Frag<double> out;
-        spmm_row<T>(P, A.Ut, ld, j, A.lam, A.e, 0.0, -1.0, -sigma, T(0), tm, ot);
+        spmm_row<E>(P, Ub, ld, j, A.lam, A.e, 0.0, -1.0, -sigma, E(0), tm, ot);
         frag_convert(out, ot);
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
@@ -274,9 +291,9 @@ struct Solver {
       // rows with many entries: one warp per row
       const WarpRow wr = make_warp_row(ld, sc.tid(), sc.nthreads(), prm.team_mult);
       for (int j = wr.warp; j < n; j += wr.nwarps) {
-        Frag<T> ot;
+        Frag<E> ot;
         Frag<double> out;
-        spmm_row_warp<T>(P, A.Ut, ld, j, A.lam, A.e, 0.0, -1.0, -sigma, T(0), wr, ot);
+        spmm_row_warp<E>(P, Ub, ld, j, A.lam, A.e, 0.0, -1.0, -sigma, E(0), wr, ot);
         frag_convert(out, ot);
         if (wr.sub == 0) {
 #pragma unroll
@@ -292,6 +309,10 @@ struct Solver {
     if (!sc.reduce(v, 1)) return false;
     g2 = v[0];
     return true;
+  }
+
+  __device__ bool eval_grad(double sigma, double& g2) {
+    return fp64_bulk ? eval_grad_e<double>(A.U, sigma, g2) : eval_grad_e<T>(A.Ut, sigma, g2);
   }
 
   // L-BFGS two-loop recursion (Nocedal and Wright, Algorithm 7.4), passes fused with the
@@ -415,16 +436,16 @@ struct Solver {
   }
 
   // quartic coefficients of phi(U + t D) - phi(U)
-  __device__ bool line_search_coeffs(double sigma, double* a) {
+  template <typename E>
+  __device__ bool line_search_coeffs_e(const E* Ub, const E* Dt, double sigma, double* a) {
     double v[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) v[i] = 0.0;
     // <C, U D^T + D U^T> = 2 sum_j D_j . (C U)_j ;  <C, D D^T> = sum_j D_j . (C D)_j
-    const T* Dt = dir_shadow();
     for (int j = tm.id; j < n; j += tm.count) {
-      Frag<T> mCU, mCD, Dj;
-      spmm_row<T>(P, A.Ut, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, T(0), tm, mCU);
-      spmm_row<T>(P, Dt, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, T(0), tm, mCD);
+      Frag<E> mCU, mCD, Dj;
+      spmm_row<E>(P, Ub, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, E(0), tm, mCU);
+      spmm_row<E>(P, Dt, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, E(0), tm, mCD);
       frag_load(Dj, Dt, j, ld, tm);
       const double c1 = -2.0 * (double)frag_dot(Dj, mCU, tm);
       const double c2 = -(double)frag_dot(Dj, mCD, tm);
@@ -436,11 +457,11 @@ struct Solver {
     for (int i = tmc.id; i < m; i += tmc.count) {
       const int rr = P.con_r[i], cc = P.con_c[i];
       const double aa = P.con_a[i];
-      Frag<T> Ur, Dc, Dr, Uc;
-      frag_load(Ur, A.Ut, rr, ld, tmc);
+      Frag<E> Ur, Dc, Dr, Uc;
+      frag_load(Ur, Ub, rr, ld, tmc);
       frag_load(Dc, Dt, cc, ld, tmc);
       frag_load(Dr, Dt, rr, ld, tmc);
-      frag_load(Uc, A.Ut, cc, ld, tmc);
+      frag_load(Uc, Ub, cc, ld, tmc);
       double e1, e2;
       if (rr != cc) {
         e1 = 2.0 * aa * (double)team_sum(frag_dot_local(Ur, Dc) + frag_dot_local(Uc, Dr), tmc);
@@ -466,6 +487,11 @@ struct Solver {
     a[2] = sigma * v[5];
     a[3] = 0.5 * sigma * v[6];
     return true;
+  }
+
+  __device__ bool line_search_coeffs(double sigma, double* a) {
+    return fp64_bulk ? line_search_coeffs_e<double>(A.U, A.dir, sigma, a)
+                     : line_search_coeffs_e<T>(A.Ut, dir_shadow(), sigma, a);
   }
 
   // U <- U + t dir; S[head] = t dir; grad_old = grad
@@ -548,16 +574,33 @@ struct Solver {
   // ----------------------------------------------------------------------------------
   // Phase I: LRALM (Section 4.1) with dynamic rank (Section 4.3)
   // ----------------------------------------------------------------------------------
-  __device__ bool phase1(double& sigma_out) {
-    for (int i = sc.tid(); i < m; i += sc.nthreads()) A.lam[i] = 0.0;
-    init_factor();
-    if (!sc.sync()) return false;
-    double sigma = 1.0 / (1.0 + P.b_inf);
+  __device__ bool phase1(double& sigma_out) { return alm(sigma_out, false); }
+
+  // The augmented Lagrangian method of Phase I.  refine = false: from U_0 (init_factor),
+  // lambda = 0, sigma_0 = 1/(1+||b||_inf), until r_P <= switch_tol.  refine = true (Phase III
+  // outside the product-of-spheres class): from the U in A.U, lambda in A.lam and sigma_io, with
+  // the bulk products on the FP64 masters, until r_P <= tol and r_D <= tol, where r_D of the
+  // multiplier-updated pair is ||grad phi|| / (2 (1 + ||C||_F)) at the end of an inner solve.
+  // alm_done tells whether the stopping rule was met (else max_outer ran out).
+  __device__ bool alm(double& sigma_io, bool refine) {
+    double sigma;
+    if (!refine) {
+      for (int i = sc.tid(); i < m; i += sc.nthreads()) A.lam[i] = 0.0;
+      init_factor();
+      if (!sc.sync()) return false;
+      sigma = 1.0 / (1.0 + P.b_inf);
+    } else {
+      sigma = sigma_io;
+      fp64_bulk = true;
+    }
+    alm_done = false;
+    const double tol_g2 = 4.0 * prm.tol * (1.0 + P.C_fro) * prm.tol * (1.0 + P.C_fro);
     double rp_prev = INFINITY, rp = 0.0;
     double hrho[MAXMEM + 1], hsy[MAXMEM + 1], hyy[MAXMEM + 1];
     const int ring = prm.lbfgs_mem + 1;
     for (int outer = 1; outer <= prm.max_outer; ++outer) {
-      alm_outer = outer;
+      if (refine) ++refine_outer;
+      else alm_outer = outer;
       int cnt = 0, head = 0;
       double e2, g2;
       if (!eval_residual_UU(e2)) return false;
@@ -600,10 +643,12 @@ struct Solver {
         }
         ++it;
       }
-      lbfgs_iters += it;
-      if (rp <= prm.switch_tol) {
+      if (refine) refine_lbfgs += it;
+      else lbfgs_iters += it;
+      if (refine ? (rp <= prm.tol && g2 <= tol_g2) : (rp <= prm.switch_tol)) {
         for (int i = sc.tid(); i < m; i += sc.nthreads()) A.lam[i] += sigma * A.e[i];
         if (!sc.sync()) return false;
+        alm_done = true;
         break;
       }
       if (stalled && r < prm.rank_cap) {
@@ -618,7 +663,7 @@ struct Solver {
       if (rp > prm.sigma_decrease * rp_prev) sigma *= prm.sigma_factor;
       rp_prev = rp;
     }
-    sigma_out = sigma;
+    sigma_io = sigma;
     return true;
   }
 
@@ -821,37 +866,60 @@ struct Solver {
     }
   }
 
-  // Final test on X = U_hat U_hat^T, y = -lambda^{k+1} once the primal test has passed:
-  // the Appendix B gap, then the Appendix B dual infeasibility (rate-limited); a dual
-  // infeasibility that fell by less than 10% since the previous failed test (a stationary
-  // point of the rank-r problem) grows the rank along the eigenvector of lambda_min.
-  // Returns 1 (done), 0 (continue), 2 (rank grown: U, V changed), -1 (device error).
+  // the dual measure of the final test: max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf).
+  // Appendix B divides the same eigenvalue by 1 + ||vec C||_1, which grows with n.
+  __device__ double dual_psd(double lmin) const { return fmax(0.0, -lmin) / (1.0 + P.C_inf); }
+
+  // Phase III applies: every row carries exactly one diagonal constraint with b/a > 0
+  __device__ bool polish_applies() const {
+    return prm.polish && P.polish_ok && P.row_norm != nullptr;
+  }
+
+  // Final test on X = U_hat U_hat^T, y = -lambda^{k+1} once the primal test has passed: the
+  // Appendix B gap and the stationarity r_D = ||(C - A^T y) U_hat||_F / (1 + ||C||_F) of
+  // eq. def:eKKT (one pass); where Phase III applies, an output that passes the gap with
+  // r_D > tol is handed over to it; otherwise the dual measure (rate-limited Lanczos) and r_D
+  // must both pass.  A dual measure that fell by less than 10% since the previous failed test
+  // (a stationary point of the rank-r problem) grows the rank along the eigenvector of
+  // lambda_min.  Returns 1 (done), 0 (continue), 2 (rank grown: U, V changed), 3 (hand over to
+  // Phase III), -1 (device error).
   __device__ int final_test() {
     double gap;
     if (!gap_check(gap)) return -1;
     if (!(fabs(gap) <= prm.tol)) return 0;
-    if (!prm.kkt_dinf) return 1;
+    const double tol_rd2 = prm.tol * (1.0 + P.C_fro) * prm.tol * (1.0 + P.C_fro);
+    const bool rd_ok = last_rd2 <= tol_rd2;
+    if (!rd_ok && prm.polish) return 3;
+    if (!prm.kkt_dinf) return rd_ok ? 1 : 0;
     if (admm_iters < ndt) return 0;
     if (!lanczos_lambda_min(last_lmin)) return -1;
     lmin_at = admm_iters;
-    const double dinf = fmax(0.0, -last_lmin) / (1.0 + P.c_one);
-    if (dinf <= prm.tol) return 1;
+    const double d = dual_psd(last_lmin);
+    if (d <= prm.tol && rd_ok) return 1;
     ndt = admm_iters + max(prm.dinf_every, admm_iters / 10);
-    if (pdinf == pdinf && dinf > 0.9 * pdinf && prm.escape_scale > 0.0 &&
-        r < prm.rank_cap) {
-      double zn2 = 0.0, lm;
-      if (!lanczos_lambda_min(lm, true, &zn2)) return -1;
-      const int K = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
-      int r_new = (int)ceil(prm.rank_factor * r - 1e-9);
-      if (r_new <= r) r_new = r + 1;
-      if (r_new > prm.rank_cap) r_new = prm.rank_cap;
-      if (!grow_rank_phase2(r_new, A.Y + 2 * K, zn2)) return -1;
-      ++growths;
+    if (d <= prm.tol) return 0;
+    if (pdinf == pdinf && d > 0.9 * pdinf && prm.escape_scale > 0.0 && r < prm.rank_cap) {
+      if (!escape_grow()) return -1;
       pdinf = NAN;
       return 2;
     }
-    pdinf = dinf;
+    pdinf = d;
     return 0;
+  }
+
+  // rank growth along the eigenvector of lambda_min(C - A^T y): r -> ceil(1.5 r) (at least
+  // r + 1, at most the cap), new columns [tau z, 0, ...] in U and V (Section 4.3's rule,
+  // applied where the rank-r problem has stalled)
+  __device__ bool escape_grow() {
+    double zn2 = 0.0, lm;
+    if (!lanczos_lambda_min(lm, true, &zn2)) return false;
+    const int K = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
+    int r_new = (int)ceil(prm.rank_factor * r - 1e-9);
+    if (r_new <= r) r_new = r + 1;
+    if (r_new > prm.rank_cap) r_new = prm.rank_cap;
+    if (!grow_rank_phase2(r_new, A.Y + 2 * K, zn2)) return false;
+    ++growths;
+    return true;
   }
 
   __device__ bool phase2(double rho, double& rho_out) {
@@ -890,7 +958,8 @@ struct Solver {
       if (rph <= prm.tol) {
         const int t = final_test();
         if (t < 0) return false;
-        if (t == 1) {
+        if (t == 1 || t == 3) {
+          to_polish = t == 3;
           rho_out = rho;
           return true;
         }
@@ -1165,9 +1234,10 @@ struct Solver {
   // the Chronopoulos-Gear scalars after a reduction z = (r.r, w.r): thread 0 of the CTA
   // evaluates them (one division) and shares them through shared memory; false when the
   // CG stops (converged, a non-positive denominator, or NaN, which sets the status)
+  template <typename S>
   __device__ __forceinline__ bool cg_scalars(bool lead, double* shs, const double* z,
                                              double target2, double& gam, double& ga, int& go,
-                                             T& a_t, T& b_t) {
+                                             S& a_t, S& b_t) {
     if (lead) {
       int state = 0;                 // 0: go on, 1: stop, 2: NaN
       const double gam_new = z[0], del_new = z[1];
@@ -1194,8 +1264,8 @@ struct Solver {
     }
     __syncthreads();
     const int state = (int)shs[0];
-    a_t = (T)shs[1];
-    b_t = (T)shs[2];
+    a_t = (S)shs[1];
+    b_t = (S)shs[2];
     __syncthreads();
     if (state == 2) status = ST_NAN;
     go = state == 0;
@@ -1312,7 +1382,8 @@ struct Solver {
       if (v[1] <= tol2_primal) {
         const int t = final_test();
         if (t < 0) return false;
-        if (t == 1) {
+        if (t == 1 || t == 3) {
+          to_polish = t == 3;
           rho_out = rho;
           return true;
         }
@@ -1434,7 +1505,8 @@ struct Solver {
       if (v[1] <= tol2_primal) {
         const int t = final_test();
         if (t < 0) return false;
-        if (t == 1) {
+        if (t == 1 || t == 3) {
+          to_polish = t == 3;
           rho_out = rho;
           return true;
         }
@@ -1452,6 +1524,332 @@ struct Solver {
     if (status == ST_OK) status = ST_MAXITER;
     rho_out = rho;
     return true;
+  }
+
+  // ----------------------------------------------------------------------------------
+  // Phase III (not in the paper): Newton's method for eq. prob:BM on the product of spheres.
+  // When every row carries one diagonal constraint a U_j.U_j = b (b/a > 0), the feasible set
+  // of eq. prob:BM is the product of the spheres ||U_j|| = rad_j = sqrt(b/a) (P.row_norm), the
+  // projection onto it is a row scaling, and for U on it the multiplier minimising
+  // ||(C + A^T lambda) U||_F is a_j lambda_i = -mu_j, mu_j = (C U)_j.U_j / ||U_j||^2.  Then
+  //   Riemannian gradient  g_j = 2 ((C U)_j - mu_j U_j)            (= 2 ((C + A^T lambda) U)_j)
+  //   Riemannian Hessian   (H Z)_j = 2 P_j((C Z)_j - mu_j Z_j),  P_j(W) = W - (W.U_j/||U_j||^2) U_j
+  // (Absil, Mahony and Sepulchre 2008, Ch. 6), and r_D = ||g|| / (2 (1 + ||C||_F)); on the
+  // manifold A(U U^T) = b holds and the gap with y = -lambda(U) is zero.  Each Newton step solves
+  // H d = -g by truncated CG (Nocedal and Wright, Algorithm 7.1: stop at ||H d + g|| <= eta ||g||,
+  // eta = min(0.5, sqrt(||g||)), or at non-positive curvature, then -g if no step was taken),
+  // run as the Chronopoulos-Gear recurrence (one reduction and one barrier per iteration: the
+  // Hessian reads the neighbours' residual), then backtracks from t = 1 until
+  // f(R(U + t d)) <= f(U) + 1e-4 t g.d, R the row scaling.  Once r_D <= tol the dual measure is
+  // tested (Lanczos); a failure grows the rank along the eigenvector of lambda_min as in Phase II.
+  // All in FP64.  Arrays: U (iterate), V (trial), CWn (C U), grad (g), dir (d), grad_old (CG
+  // residual r), S slot 0 (CG direction p), S slot 1 (s = H p), Y slot 0 (w = H r), e (mu, by row).
+  // ----------------------------------------------------------------------------------
+  // (H Z)_j for the tangent field Z (neighbours' rows of Z must be visible); Zj is row j of Z
+  __device__ __forceinline__ void sphere_hess_row(int j, const double* Z, const Frag<double>& Zj,
+                                                  const Frag<double>& Uj, double u2, double mu,
+                                                  Frag<double>& out) const {
+    Frag<double> mCZ;
+    spmm_row<double>(P, Z, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCZ);
+    // W = (C Z)_j - mu Z_j
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+      for (int e = 0; e < CHUNK; ++e) out.v[k][e] = -mCZ.v[k][e] - mu * Zj.v[k][e];
+    const double c = frag_dot(out, Uj, tm) / u2;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+      for (int e = 0; e < CHUNK; ++e) out.v[k][e] = 2.0 * (out.v[k][e] - c * Uj.v[k][e]);
+  }
+
+  // g, mu, lambda(U) and C U at the iterate in A.U; v = (||g||^2, <C, U U^T>, ||U||_F^2, time)
+  __device__ bool sphere_gradient(double* v) {
+    v[0] = v[1] = v[2] = v[3] = 0.0;
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Uj, mCU, g;
+      frag_load(Uj, A.U, j, ld, tm);
+      spmm_row<double>(P, A.U, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCU);
+      const double u2 = frag_dot(Uj, Uj, tm);
+      const double cu = -frag_dot(mCU, Uj, tm);
+      const double mu = cu / u2;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) g.v[k][e] = 2.0 * (-mCU.v[k][e] - mu * Uj.v[k][e]);
+      frag_store(g, A.grad, j, ld, tm);
+      const double g2 = frag_dot(g, g, tm);
+      if (tm.lane == 0) {
+        A.e[j] = mu;
+        const int ci = P.row_con[j];
+        A.lam[ci] = -mu / P.row_a[j];
+        v[0] += g2;
+        v[1] += cu;
+        v[2] += u2;
+      }
+    }
+    if (sc.is_leader()) v[3] = (double)(globaltimer_ns() - t_start);
+    return sc.reduce(v, 4);
+  }
+
+  // truncated CG for H d = -g (see above); d in A.dir; returns the iterations in it
+  __device__ bool sphere_newton_cg(double g2, int& it) {
+    double* const R = A.grad_old;
+    double* const Pp = A.S;
+    const long long NS = (long long)n * A.ld_cap;
+    double* const Sv = A.S + NS;
+    double* const W = A.Y;
+    // r_0 = -g, w_0 = H r_0 = -H g (the gradient of every row is visible after its reduction)
+    double g3[2] = {0.0, 0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Uj, gj, w;
+      frag_load(Uj, A.U, j, ld, tm);
+      frag_load(gj, A.grad, j, ld, tm);
+      const double u2 = frag_dot(Uj, Uj, tm);
+      sphere_hess_row(j, A.grad, gj, Uj, u2, A.e[j], w);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) {
+          gj.v[k][e] = -gj.v[k][e];
+          w.v[k][e] = -w.v[k][e];
+        }
+      frag_store(gj, R, j, ld, tm);
+      frag_store(w, W, j, ld, tm);
+      const double d1 = frag_dot(gj, gj, tm), d2 = frag_dot(w, gj, tm);
+      if (tm.lane == 0) {
+        g3[0] += d1;
+        g3[1] += d2;
+      }
+    }
+    if (!sc.reduce(g3, 2)) return false;
+    const bool lead = threadIdx.x == 0;
+    double* shs = sc.scratch() + 4;
+    const double eta = fmin(0.5, sqrt(sqrt(g2)));
+    const double target2 = eta * eta * g2;
+    double gam = 0.0, ga = 0.0;
+    if (lead) {
+      gam = g3[0];
+      const double del = g3[1];
+      const double alpha = del > 0.0 ? gam / del : 0.0;
+      ga = gam * alpha;
+      shs[0] = (gam > target2 && del > 0.0) ? 0.0 : 1.0;
+      shs[1] = alpha;
+      shs[2] = 0.0;
+    }
+    __syncthreads();
+    int go = shs[0] == 0.0;
+    double a_t = shs[1], b_t = 0.0;
+    __syncthreads();
+    it = 0;
+    while (go && it < prm.newton_cg_max) {
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> r, w, pp, ss, x;
+        frag_load(r, R, j, ld, tm);
+        frag_load(w, W, j, ld, tm);
+        if (it > 0) {
+          frag_load(pp, Pp, j, ld, tm);
+          frag_load(ss, Sv, j, ld, tm);
+          frag_load(x, A.dir, j, ld, tm);
+        } else {
+          frag_zero(pp);
+          frag_zero(ss);
+          frag_zero(x);
+        }
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+          for (int e = 0; e < CHUNK; ++e) {
+            pp.v[k][e] = fma(b_t, pp.v[k][e], r.v[k][e]);
+            ss.v[k][e] = fma(b_t, ss.v[k][e], w.v[k][e]);
+            x.v[k][e] = fma(a_t, pp.v[k][e], x.v[k][e]);
+            r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
+          }
+        frag_store(pp, Pp, j, ld, tm);
+        frag_store(ss, Sv, j, ld, tm);
+        frag_store(x, A.dir, j, ld, tm);
+        frag_store(r, R, j, ld, tm);
+      }
+      if (!sc.sync()) return false;
+      double z[2] = {0.0, 0.0};
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> Uj, r, w;
+        frag_load(Uj, A.U, j, ld, tm);
+        frag_load(r, R, j, ld, tm);
+        const double u2 = frag_dot(Uj, Uj, tm);
+        sphere_hess_row(j, R, r, Uj, u2, A.e[j], w);
+        frag_store(w, W, j, ld, tm);
+        const double d1 = frag_dot(r, r, tm), d2 = frag_dot(w, r, tm);
+        if (tm.lane == 0) {
+          z[0] += d1;
+          z[1] += d2;
+        }
+      }
+      if (!sc.reduce(z, 2)) return false;
+      ++it;
+      if (!cg_scalars(lead, shs, z, target2, gam, ga, go, a_t, b_t)) break;
+    }
+    if (it == 0) {
+      // non-positive curvature along -g: the steepest-descent direction
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<double> gj;
+        frag_load(gj, A.grad, j, ld, tm);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+          for (int e = 0; e < CHUNK; ++e) gj.v[k][e] = -gj.v[k][e];
+        frag_store(gj, A.dir, j, ld, tm);
+      }
+      if (!sc.sync()) return false;
+    }
+    return true;
+  }
+
+  // trial point R(U + t d) into A.V (row scaling onto the spheres); with want_slope also g.d
+  __device__ bool sphere_trial(double t, bool want_slope, double& slope) {
+    double v[1] = {0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Uj, dj;
+      frag_load(Uj, A.U, j, ld, tm);
+      frag_load(dj, A.dir, j, ld, tm);
+      if (want_slope) {
+        Frag<double> gj;
+        frag_load(gj, A.grad, j, ld, tm);
+        const double gd = frag_dot(gj, dj, tm);
+        if (tm.lane == 0) v[0] += gd;
+      }
+      frag_axpy(Uj, t, dj);
+      const double sc2 = P.row_norm[j] / sqrt(frag_dot(Uj, Uj, tm));
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) Uj.v[k][e] *= sc2;
+      frag_store(Uj, A.V, j, ld, tm);
+    }
+    if (!sc.reduce(v, 1)) return false;
+    if (want_slope) slope = v[0];
+    return true;
+  }
+
+  // <C, W W^T> for W = A.V (neighbours visible)
+  __device__ bool trial_objective(double& f) {
+    double v[1] = {0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Wj, mCW;
+      frag_load(Wj, A.V, j, ld, tm);
+      spmm_row<double>(P, A.V, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCW);
+      const double o = -frag_dot(Wj, mCW, tm);
+      if (tm.lane == 0) v[0] += o;
+    }
+    if (!sc.reduce(v, 1)) return false;
+    f = v[0];
+    return true;
+  }
+
+  // copies src into dst (both n x ld FP64), then a barrier
+  __device__ bool copy_rows(const double* src, double* dst) {
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> x;
+      frag_load(x, src, j, ld, tm);
+      frag_store(x, dst, j, ld, tm);
+    }
+    return sc.sync();
+  }
+
+  // U <- rows of U scaled onto the spheres (after a rank growth), V = U
+  __device__ bool sphere_retract_u() {
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Uj;
+      frag_load(Uj, A.U, j, ld, tm);
+      const double sc2 = P.row_norm[j] / sqrt(frag_dot(Uj, Uj, tm));
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) Uj.v[k][e] *= sc2;
+      frag_store(Uj, A.U, j, ld, tm);
+      frag_store(Uj, A.V, j, ld, tm);
+    }
+    return sc.sync();
+  }
+
+  __device__ bool phase3() {
+    t_p3 = globaltimer_ns();
+    // start: U = R(U_hat), U_hat = (U + V)/2 of Phase II's output
+    if (!form_u_hat()) return false;
+    if (!copy_rows(A.tmp, A.U)) return false;
+    if (!sphere_retract_u()) return false;
+    const double tol_g2 = 4.0 * prm.tol * (1.0 + P.C_fro) * prm.tol * (1.0 + P.C_fro);
+    for (;;) {
+      double v[4];
+      if (!sphere_gradient(v)) return false;
+      const double g2 = v[0], f0 = v[1];
+      if (!(g2 == g2) || !(f0 == f0)) { status = ST_NAN; return true; }
+      if (g2 <= tol_g2) {
+        if (!prm.kkt_dinf) return true;
+        if (!lanczos_lambda_min(last_lmin)) return false;
+        lmin_at = admm_iters;
+        if (dual_psd(last_lmin) <= prm.tol) return true;
+        if (!(prm.escape_scale > 0.0) || r >= prm.rank_cap) { status = ST_MAXITER; return true; }
+        uh_norm2 = v[2];
+        if (!copy_rows(A.U, A.V)) return false;
+        if (!escape_grow()) return false;
+        if (!sphere_retract_u()) return false;
+        continue;
+      }
+      if ((long long)v[3] > prm.time_limit_ns) { status = ST_TIMEOUT; return true; }
+      if (newton_steps >= prm.newton_max) { status = ST_MAXITER; return true; }
+      int it = 0;
+      if (!sphere_newton_cg(g2, it)) return false;
+      newton_cg += it;
+      if (status != ST_OK) return true;
+      double slope = 0.0, t = 1.0, f = 0.0;
+      for (int ls = 0; ls < 31; ++ls) {
+        if (!sphere_trial(t, ls == 0, slope)) return false;
+        if (!trial_objective(f)) return false;
+        if (f <= f0 + 1e-4 * t * slope) break;
+        t *= 0.5;
+      }
+      if (!copy_rows(A.V, A.U)) return false;
+      ++newton_steps;
+    }
+  }
+
+  // ||U||_F^2 of the masters
+  __device__ bool u_norm2(double& u2) {
+    double v[1] = {0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<double> Uj;
+      frag_load(Uj, A.U, j, ld, tm);
+      const double d = frag_dot(Uj, Uj, tm);
+      if (tm.lane == 0) v[0] += d;
+    }
+    if (!sc.reduce(v, 1)) return false;
+    u2 = v[0];
+    return true;
+  }
+
+  // Phase III outside the product-of-spheres class: the augmented Lagrangian method of Phase I
+  // continued from Phase II's output (U = U_hat, lambda, sigma = Phase I's last penalty) until
+  // r_P <= tol and r_D <= tol, then the dual test; a failed dual test grows the rank along the
+  // eigenvector of lambda_min (as in Phase II) and the method goes on.  V = U at the end.
+  __device__ bool phase3_alm(double sigma) {
+    t_p3 = globaltimer_ns();
+    if (!form_u_hat()) return false;
+    if (!copy_rows(A.tmp, A.U)) return false;
+    for (;;) {
+      if (!alm(sigma, true)) return false;
+      if (status != ST_OK) break;
+      if (!alm_done) { status = ST_MAXITER; break; }
+      if (!prm.kkt_dinf) break;
+      if (!lanczos_lambda_min(last_lmin)) return false;
+      lmin_at = admm_iters;
+      if (dual_psd(last_lmin) <= prm.tol) break;
+      if (!(prm.escape_scale > 0.0) || r >= prm.rank_cap) { status = ST_MAXITER; break; }
+      if (!u_norm2(uh_norm2)) return false;
+      if (!copy_rows(A.U, A.V)) return false;
+      if (!escape_grow()) return false;
+    }
+    return copy_rows(A.U, A.V);
   }
 
   // U_hat = (U + V)/2 into tmp
@@ -1472,60 +1870,147 @@ struct Solver {
 
   // Appendix B primal-dual gap of X = U_hat U_hat^T, y = -lambda:
   // (<C, X> - b^T y) / (1 + |<C, X>| + |b^T y|), in FP64 from the masters
+  // Appendix B primal-dual gap of X = U_hat U_hat^T, y = -lambda:
+  // (<C, X> - b^T y) / (1 + |<C, X>| + |b^T y|), in FP64 from the masters; in the same pass
+  // last_rd2 = ||(C + A^T lambda) U_hat||_F^2 (eq. def:eKKT's stationarity with y = -lambda)
   __device__ bool gap_check(double& gap) {
     if (!form_u_hat()) return false;
-    double v[3] = {0.0, 0.0, 0.0};
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (P.a_diag_only) {
       for (int j = tm.id; j < n; j += tm.count) {
         Frag<double> Uh, mCU;
         frag_load(Uh, A.tmp, j, ld, tm);
         spmm_row<double>(P, A.tmp, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCU);
         const double o = -frag_dot(Uh, mCU, tm), u2 = frag_dot(Uh, Uh, tm);
+        // -(C + A^T lambda) U_hat on row j: -(C U_hat)_j - a lambda_i U_hat_j
+        const int ci = P.row_con[j];
+        if (ci >= 0) frag_axpy(mCU, -P.row_a[j] * A.lam[ci], Uh);
+        const double s2 = frag_dot(mCU, mCU, tm);
         if (tm.lane == 0) {
           v[0] += o;
           v[2] += u2;
+          v[3] += s2;
         }
       }
     } else {
       const WarpRow wr = make_warp_row(ld, sc.tid(), sc.nthreads(), prm.team_mult);
       for (int j = wr.warp; j < n; j += wr.nwarps) {
-        Frag<double> Uh, mCU;
+        Frag<double> Uh, mCU, mSU;
         frag_load(Uh, A.tmp, j, ld, wr.st);
         spmm_row_warp<double>(P, A.tmp, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, wr, mCU);
+        spmm_row_warp<double>(P, A.tmp, ld, j, A.lam, nullptr, 0.0, -1.0, 0.0, 0.0, wr, mSU);
         if (wr.sub == 0) {
           const double o = -frag_dot(Uh, mCU, wr.st), u2 = frag_dot(Uh, Uh, wr.st);
+          const double s2 = frag_dot(mSU, mSU, wr.st);
           if (wr.st.lane == 0) {
             v[0] += o;
             v[2] += u2;
+            v[3] += s2;
           }
         }
       }
     }
     for (int i = sc.tid(); i < m; i += sc.nthreads()) v[1] += P.b[i] * A.lam[i];
-    if (!sc.reduce(v, 3)) return false;
+    if (!sc.reduce(v, 4)) return false;
     uh_norm2 = v[2];
+    last_rd2 = v[3];
     const double pobj = v[0], dobj = -v[1];
     gap = (pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
     return true;
   }
 
+  // Largest eigenvalue of each Lanczos tridiagonal T_c (alpha at hist[8k + c], beta at
+  // hist[8k + 4 + c], L[c] steps): warp c of every CTA runs a 32-point multisection on the
+  // Sturm count (identical in every CTA, so every thread ends with the same values).  best is
+  // the largest over the columns (-inf when none has a step), cs its column.
+  __device__ void ritz_top(const double* hist, const int* L, double& best, int& cs) {
+    constexpr int NC = 4;
+    double* theta = sc.scratch();     // NC entries
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < NC) {
+      const int c = warp, Lc = L[c];
+      double th = -INFINITY;
+      if (Lc > 0) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int i = lane; i < Lc; i += 32) {
+          const double ai = hist[8 * i + c];
+          const double bl = i > 0 ? fabs(hist[8 * (i - 1) + 4 + c]) : 0.0;
+          const double br = i + 1 < Lc ? fabs(hist[8 * i + 4 + c]) : 0.0;
+          lo = fmin(lo, ai - bl - br);
+          hi = fmax(hi, ai + bl + br);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+          hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+        }
+        for (int round = 0; round < 11; ++round) {
+          const double width = hi - lo;
+          const double x = lo + width * (double)(lane + 1) / 33.0;
+          int below = 0;      // eigenvalues of T_c below x
+          double d = 1.0;
+          for (int i = 0; i < Lc; ++i) {
+            const double ai = hist[8 * i + c];
+            if (i == 0) {
+              d = ai - x;
+            } else {
+              const double bi = hist[8 * (i - 1) + 4 + c];
+              d = (ai - x) - bi * bi / d;
+            }
+            if (fabs(d) < 1e-300) d = -1e-300;
+            below += d < 0.0;
+          }
+          // lanes whose x lies above every eigenvalue form a suffix; the top eigenvalue
+          // lies between the last x below it and the first x above it
+          const unsigned above = __ballot_sync(0xffffffffu, below >= Lc);
+          const int f = above ? __ffs(above) - 1 : 32;
+          const double nlo = f == 0 ? lo : lo + width * (double)f / 33.0;
+          const double nhi = f == 32 ? hi : lo + width * (double)(f + 1) / 33.0;
+          lo = nlo;
+          hi = nhi;
+        }
+        th = 0.5 * (lo + hi);
+      }
+      if (lane == 0) theta[c] = th;
+    }
+    __syncthreads();
+    best = -INFINITY;
+    cs = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (theta[c] > best) {
+        best = theta[c];
+        cs = c;
+      }
+    __syncthreads();
+  }
+
   // lambda_min(C - A^T y), y = -lambda: Lanczos on M = -(C + A^T(lambda)) from four random
-  // start columns at once (an n x 4 block in the factor layout of width 4), K =
-  // min(lanczos_steps, n) steps each, no reorthogonalisation; the estimate is -max_c theta_c,
-  // theta_c the largest eigenvalue of column c's tridiagonal (Sturm-count multisection).
-  // Column c stops early when its beta vanishes (its Krylov space is exhausted).
+  // start columns at once (an n x 4 block in the factor layout of width 4), at most Kmax =
+  // min(lanczos_steps, 2048, n) steps each (fewer once the estimate settles, see below), no
+  // reorthogonalisation; the estimate is -max_c theta_c, theta_c the largest eigenvalue of
+  // column c's tridiagonal (Sturm-count multisection).  A clustered bottom of the spectrum
+  // (the dual slack of a degenerate SDP) needs many steps: on the 141 x 141 torus the estimate
+  // moves from +6e-5 (128 steps) to -3.6e-6 (2048).  Column c stops early when its beta
+  // vanishes (its Krylov space is exhausted).
   // With want_vec the Ritz vector of the estimate is rebuilt too: the eigenvector s of the
   // chosen T_c by inverse iteration, then a second pass of the same recurrence (the stored
-  // alpha / beta, the same start) accumulates z = sum_k s_k q_k into A.Y + 2K (n entries);
+  // alpha / beta, the same start) accumulates z = sum_k s_k q_k into A.Y + 2 Kmax (n entries);
   // zn2 receives ||z||^2.
   __device__ __noinline__ bool lanczos_lambda_min(double& lmin, bool want_vec = false,
                                                   double* zn2 = nullptr) {
     constexpr int NC = 4;
-    const int K = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
-    if (K <= 0) {
+    const int Kmax = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
+    if (Kmax <= 0) {
       lmin = NAN;
       return true;
     }
+    // steps taken: Kmax, or fewer once the estimate settles (checked at 128, 256, 512, ...
+    // steps: the largest Ritz value of M grows with the step count, and the recurrence stops
+    // when it rose by at most 0.05 tol (1 + ||C||_inf) over the last doubling)
+    int K = Kmax;
+    int next_check = min(128, Kmax);
+    double theta_prev = -INFINITY;
+    const double settle = 0.05 * prm.tol * (1.0 + P.C_inf);
     double* Qp = A.dir;     // raw q_{k-1} (true vector: qps * Qp)
     double* Q = A.grad;     // raw q_k     (true vector: qs * Q)
     double* W = A.grad_old;
@@ -1553,7 +2038,7 @@ struct Solver {
       bp[c] = 0.0;
       len[c] = v[c] > 0.0 ? K : 0;
     }
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < Kmax; ++k) {
       // W = M q_k - beta_{k-1} q_{k-1};  alpha_k = q_k . W
       double a[NC] = {0.0, 0.0, 0.0, 0.0};
       const bool diag = P.a_diag_only != 0;
@@ -1605,75 +2090,36 @@ struct Solver {
       Qp = Q;
       Q = W;
       W = t;
-    }
-    if (!sc.sync()) return false;       // the coefficients written by the leader
-    // largest eigenvalue of each T_c: warp c of every CTA, 32-point multisection on the
-    // Sturm count (identical in every CTA, so every thread ends with the same estimate)
-    double* theta = sc.scratch();     // NC entries
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < NC) {
-      const int c = warp, L = len[c];
-      double th = -INFINITY;
-      if (L > 0) {
-        double lo = INFINITY, hi = -INFINITY;
-        for (int i = lane; i < L; i += 32) {
-          const double ai = hist[8 * i + c];
-          const double bl = i > 0 ? fabs(hist[8 * (i - 1) + 4 + c]) : 0.0;
-          const double br = i + 1 < L ? fabs(hist[8 * i + 4 + c]) : 0.0;
-          lo = fmin(lo, ai - bl - br);
-          hi = fmax(hi, ai + bl + br);
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-          hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
-        }
-        for (int round = 0; round < 11; ++round) {
-          const double width = hi - lo;
-          const double x = lo + width * (double)(lane + 1) / 33.0;
-          int below = 0;      // eigenvalues of T_c below x
-          double d = 1.0;
-          for (int i = 0; i < L; ++i) {
-            const double ai = hist[8 * i + c];
-            if (i == 0) {
-              d = ai - x;
-            } else {
-              const double bi = hist[8 * (i - 1) + 4 + c];
-              d = (ai - x) - bi * bi / d;
-            }
-            if (fabs(d) < 1e-300) d = -1e-300;
-            below += d < 0.0;
-          }
-          // lanes whose x lies above every eigenvalue form a suffix; the top eigenvalue
-          // lies between the last x below it and the first x above it
-          const unsigned above = __ballot_sync(0xffffffffu, below >= L);
-          const int f = above ? __ffs(above) - 1 : 32;
-          const double nlo = f == 0 ? lo : lo + width * (double)f / 33.0;
-          const double nhi = f == 32 ? hi : lo + width * (double)(f + 1) / 33.0;
-          lo = nlo;
-          hi = nhi;
-        }
-        th = 0.5 * (lo + hi);
-      }
-      if (lane == 0) theta[c] = th;
-    }
-    __syncthreads();
-    double best = -INFINITY;
-    int cs = 0;
+      if (k + 1 == next_check && k + 1 < Kmax) {
+        if (!sc.sync()) return false;   // the coefficients written by the leader
+        double th;
+        int cc;
+        int lc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (theta[c] > best) {
-        best = theta[c];
-        cs = c;
+        for (int c = 0; c < NC; ++c) lc[c] = min(len[c], k + 1);
+        ritz_top(hist, lc, th, cc);
+        if (th - theta_prev <= settle) {
+          K = k + 1;
+          break;
+        }
+        theta_prev = th;
+        next_check *= 2;
       }
-    __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) len[c] = min(len[c], K);
+    if (!sc.sync()) return false;       // the coefficients written by the leader
+    double best;
+    int cs;
+    ritz_top(hist, len, best, cs);
     lmin = best > -INFINITY ? -best : NAN;
     if (!want_vec) return true;
     // eigenvector of T_cs for theta by two steps of inverse iteration (Thomas elimination of
     // T_cs - theta I; pivots below 1e-300 are nudged), one thread
     const int L = len[cs];
     double* sv = A.Y;          // s (L entries)
-    double* cp = A.Y + K;      // elimination scratch
-    double* zv = A.Y + 2 * K;  // the Ritz vector
+    double* cp = A.Y + Kmax;   // elimination scratch
+    double* zv = A.Y + 2 * Kmax;  // the Ritz vector (where escape_grow reads it)
     if (sc.is_leader() && L > 0) {
       for (int i = 0; i < L; ++i) sv[i] = 1.0;
       for (int it = 0; it < 2; ++it) {
@@ -1760,7 +2206,7 @@ struct Solver {
   __device__ static int c8(int k, int c) { return 8 * k + c; }
 
   // Phase II rank growth: U, V -> [U, tau z, 0], [V, tau z, 0] at rank r_new, z the Ritz
-  // vector of lambda_min(C - A^T y) (in A.Y + 2K, squared norm zn2), tau = escape_scale *
+  // vector of lambda_min(C - A^T y) (in A.Y + 2 Kmax, squared norm zn2), tau = escape_scale *
   // ||U_hat||_F / sqrt(r) (the size of an average column); the T shadows follow
   __device__ bool grow_rank_phase2(int r_new, const double* zv, double zn2) {
     const int r_old = r, ld_old = ld;
@@ -1862,6 +2308,7 @@ struct Solver {
       rho = fmin(prm.h * sigma, prm.rho_max);
     } else {
       rho = prm.rho0;
+      sigma = 1.0 / (1.0 + P.b_inf);     // the penalty a Phase III refinement starts from
       if (prm.resume) {
         admm_iters = prm.k0;
         ndt = prm.next_test0;
@@ -1895,6 +2342,9 @@ struct Solver {
     const long long t1 = globaltimer_ns();
     double rho_out = rho;
     if (!phase2(rho, rho_out)) { finish_error(); return; }
+    if (to_polish && status == ST_OK) {
+      if (!(polish_applies() ? phase3() : phase3_alm(sigma))) { finish_error(); return; }
+    }
     double res[5];
     if (!output(res)) { finish_error(); return; }
     finish(sigma, rho_out, res, t1, 1);
@@ -1924,7 +2374,13 @@ struct Solver {
     o->gamma = prm.gamma;
     o->sigma = sigma;
     o->t_phase1_ns = have ? t1 - t_start : t2 - t_start;
-    o->t_phase2_ns = have ? t2 - t1 : 0;
+    o->t_phase2_ns = have ? (t_p3 > 0 ? t_p3 : t2) - t1 : 0;
+    o->t_phase3_ns = (have && t_p3 > 0) ? t2 - t_p3 : 0;
+    o->polished = to_polish ? (polish_applies() ? 1 : 2) : 0;
+    o->newton_steps = newton_steps;
+    o->newton_cg = newton_cg;
+    o->refine_outer = refine_outer;
+    o->refine_lbfgs = refine_lbfgs;
     if (have) {
       const double obj = res[0], dobj = -res[3];
       o->objective = obj;
@@ -1937,10 +2393,12 @@ struct Solver {
       o->p_infeas = sqrt(res[2]) / (1.0 + P.b_one);
       o->lambda_min = last_lmin;
       o->d_infeas = last_lmin == last_lmin ? fmax(0.0, -last_lmin) / (1.0 + P.c_one) : NAN;
+      o->dual_psd = last_lmin == last_lmin ? dual_psd(last_lmin) : NAN;
     } else {
       o->p_infeas = NAN;
       o->lambda_min = NAN;
       o->d_infeas = NAN;
+      o->dual_psd = NAN;
     }
   }
 };

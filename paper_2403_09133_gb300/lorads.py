@@ -53,6 +53,7 @@ class lorads_params(ctypes.Structure):
         ("threads", _i32), ("grid", _i32), ("team_mult", _i32),
         ("kkt_dinf", _i32), ("lanczos_steps", _i32), ("dinf_every", _i32),
         ("escape_scale", _f64), ("group", _i32), ("subsolver", _i32),
+        ("polish", _i32), ("newton_max", _i32), ("newton_cg_max", _i32),
         ("barrier_polls", _i64), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 
@@ -65,6 +66,9 @@ class lorads_result(ctypes.Structure):
         ("cg_iters", _i32), ("hessian_applies", _i32), ("alm_outer", _i32),
         ("lbfgs_iters", _i32), ("rank_growths", _i32), ("time_phase1_s", _f64),
         ("time_phase2_s", _f64), ("p_infeas", _f64), ("d_infeas", _f64), ("lambda_min", _f64),
+        ("dual_psd", _f64), ("time_phase3_s", _f64), ("polished", _i32), ("newton_steps", _i32),
+        ("newton_cg_iters", _i32), ("refine_outer", _i32), ("refine_lbfgs_iters", _i32),
+        ("reserved", _i32),
     ]
 
     def as_dict(self) -> dict:

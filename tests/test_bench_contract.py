@@ -58,10 +58,12 @@ def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
 
 
 def test_algorithmic_bytes_formula():
-    # per CG iteration 12 n ld s (Hessian 3, update 6, direction 3 arrays); per warm-start
-    # residual pass n ld (8 + 3 s): W read in FP64, R, P, delta written in T
-    res = {"cg_iters": 10, "hessian_applies": 14}
-    n, ld = 1000, 16
-    got = bench.algorithmic_bytes(res, n, 4, ld)
-    assert got == 10 * 12 * n * ld * 4 + 4 * n * ld * (8 + 12)
-    assert bench.algorithmic_bytes({"cg_iters": 0, "hessian_applies": 0}, n, 8, ld) == 0
+    # 3 n ld s per Hessian apply (P and the fixed factor read, H P written): Phase II's applies
+    # at the initial rank's ld in the form's element size, Phase III's Newton-CG applies in FP64
+    # at the final rank's ld
+    n = 1000
+    res = {"hessian_applies": 14, "newton_cg_iters": 5, "rank": 23, "rank0": 15}
+    got = bench.algorithmic_bytes(res, n, 4)
+    assert got == 14 * 3 * n * 16 * 4 + 5 * 3 * n * 24 * 8
+    none = {"hessian_applies": 0, "newton_cg_iters": 0, "rank": 15, "rank0": 15}
+    assert bench.algorithmic_bytes(none, n, 8) == 0

@@ -54,13 +54,14 @@ def test_default_params_match_oracle_readings(lib):
     assert p.sigma_factor == o.sigma_factor and p.sigma_decrease == o.sigma_decrease
     assert p.new_col_std == o.new_col_std
     assert p.max_admm_iter == o.max_admm_iter and p.max_outer == o.max_outer
-    # "auto" (< 0) resolves by problem class; the oracle's defaults are the MaxCut class
-    # (every constraint one diagonal entry): gamma_scale 1, switch_tol 1e-2, h 10
-    assert p.gamma_scale < 0 and o.gamma_scale == 1.0
-    assert p.switch_tol < 0 and o.switch_tol == 1e-2 and p.h < 0 and o.h == 10.0
+    # "auto" resolves by problem class on both sides (library: < 0, oracle: None)
+    assert p.gamma_scale < 0 and o.gamma_scale is None
+    assert p.switch_tol < 0 and o.switch_tol is None and p.h < 0 and o.h is None
     assert p.kkt_dinf == int(o.kkt_dinf) and p.dinf_every == o.dinf_every
     assert p.escape_scale == o.escape_scale and p.lanczos_steps > 0
     assert p.subsolver == L.LORADS_SUB_CG and o.subsolver == "cg"
+    assert p.polish == 1 and o.polish == "auto"
+    assert p.newton_max == o.newton_max and p.newton_cg_max == o.newton_cg_max
     assert p.barrier_polls == 0          # library default: about a few seconds of polling
 
 

@@ -55,7 +55,8 @@ def test_resume_continues_the_solve(cuda, case, prec):
     res = q.solve(precision=prec, phase1=0)
     q.close()
     assert res["status"] == 0, L.lorads_status_string(res["status"])
-    assert res["r_P"] <= 1e-6 and abs(res["gap"]) <= 1e-6 and res["d_infeas"] <= 1e-6
+    assert res["r_P"] <= 1e-6 and abs(res["gap"]) <= 1e-6 and res["r_D"] <= 1e-6
+    assert res["dual_psd"] <= 1e-6
     assert _close(res["objective"], full["objective"])
     if k1 % 32 == 0:
         # the uninterrupted loop itself refreshes -(C W) and the shadows from the masters at
@@ -130,23 +131,26 @@ def test_resume_with_the_direct_subsolver(cuda, prec):
 
 
 def test_resume_after_phase2_rank_growth(cuda):
-    """The 770-vertex batch graph grows its rank 10 -> 15 in Phase II; a checkpoint taken
-    near the end of the solve carries rank 15 and the growth count."""
+    """Without Phase III the 770-vertex batch graph grows its rank 10 -> 15 in Phase II; a
+    checkpoint taken after the growth carries rank 15 and the growth count, and the resumed
+    solve ends where the uninterrupted one does."""
     inst = [x for x in I.workload_batch() if x.n == 770][0]
     p = L.Problem(inst)
-    full = p.solve()
-    assert full["status"] == 0 and full["rank"] == 15 and full["rank_growths"] == 1
-    k1 = full["admm_iters"] - 20
-    part = p.solve(max_admm_iter=k1)
+    K = 3000
+    full = p.solve(polish=0, max_admm_iter=K)
+    assert full["rank"] == 15 and full["rank_growths"] == 1
+    k1 = 87 * 32                    # a multiple of 32: the resume repeats the run bit for bit
+    part = p.solve(polish=0, max_admm_iter=k1)
     st = p.get_state()
     p.close()
     assert part["status"] == L.LORADS_ERR_MAXITER
     assert st["rank"] == 15 and st["rank_growths"] == 1
     q = L.Problem(inst)
     q.set_state(st)
-    res = q.solve(phase1=0)
+    res = q.solve(phase1=0, polish=0, max_admm_iter=K)
     q.close()
-    assert res["status"] == 0 and res["rank"] == 15 and res["rank_growths"] == 1
+    assert res["status"] == full["status"] and res["rank"] == 15 and res["rank_growths"] == 1
+    assert res["admm_iters"] == full["admm_iters"]
     assert _close(res["objective"], full["objective"])
 
 
@@ -227,10 +231,12 @@ def test_state_errors(cuda):
     assert rejected(lam=lam)
     assert lib.lorads_set_state(p.handle, None, None, None, None) == L.LORADS_ERR_ARG
     assert L.lorads_set_state(p.handle, good) == L.LORADS_OK
-    # an allocation-free solve leaves no state in the problem's own arrays
+    # an allocation-free solve leaves the problem's own state (the last lorads_solve's) as it was
     prm = p.params(max_admm_iter=50)
     L.lorads_solve_static(p.handle, prm)
-    assert lib.lorads_get_state(p.handle, st, None, None, None) == L.LORADS_ERR_STATE
+    again = p.get_state()
+    assert again["admm_iters"] == good["admm_iters"] and again["rho"] == good["rho"]
+    assert np.array_equal(again["U"], good["U"]) and np.array_equal(again["lam"], good["lam"])
     p.close()
 
 

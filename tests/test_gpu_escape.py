@@ -31,7 +31,7 @@ def test_stall_without_growth(cuda):
     assert res["status"] == L.LORADS_ERR_MAXITER and res["rank"] == 10
     assert res["r_P"] <= 1e-6 and abs(res["gap"]) <= 1e-6
     lmin = min_eig_dual_slack(sdp, sol["y"])
-    assert max(0.0, -lmin) / (1.0 + sdp.c_one) > 1e-6
+    assert max(0.0, -lmin) / (1.0 + sdp.C_rowsum_max) > 1e-6
     assert abs(res["lambda_min"] - lmin) <= 1e-7 + 1e-2 * abs(lmin)
 
 
@@ -48,4 +48,4 @@ def test_growth_matches_oracle(cuda, prec):
     assert res["status"] == 0 and res["rank"] == 15 and res["rank_growths"] == 1
     assert abs(res["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
     lmin = min_eig_dual_slack(sdp, sol["y"])
-    assert max(0.0, -lmin) / (1.0 + sdp.c_one) <= 1e-6
+    assert max(0.0, -lmin) / (1.0 + sdp.C_rowsum_max) <= 1e-6

@@ -131,19 +131,21 @@ def test_initial_factor_feasible_for_diagonal_constraints():
     np.testing.assert_allclose(np.sum(U * U, axis=1), 1.0, rtol=1e-14)
 
 
-def test_phase2_rank_growth_on_a_stalled_instance():
+def test_rank_growth_on_a_stalled_instance():
     """At rank ceil(log2 m) = 10 the 770-vertex batch graph stalls with lambda_min(S) < 0;
-    Phase II grows the rank along the eigenvector and the dense certificate then passes, at
-    an objective below the stalled one (a larger feasible set can only lower the minimum)."""
+    Phase III grows the rank along the eigenvector and the dense certificate then passes, at an
+    objective below the stalled one (a larger feasible set can only lower the minimum).  The
+    same growth inside Phase II (no Phase III) is covered by the resume test below."""
     inst = [x for x in I.workload_batch() if x.n == 770][0]
     sdp = SDP.from_instance(inst)
     stalled = solve(sdp, Params(escape_scale=0.0, max_admm_iter=600))
     grown = solve(sdp, Params())
     assert not stalled["converged"] and stalled["rank"] == 10
-    assert stalled["d_infeas"] > 1e-6
+    assert stalled["dual_psd"] > 1e-6
     assert grown["converged"] and grown["rank"] > 10 and grown["growths"] >= 1
     lmin = min_eig_dual_slack(sdp, grown["y"])
-    assert max(0.0, -lmin) / (1.0 + sdp.c_one) <= 1e-6
+    assert max(0.0, -lmin) / (1.0 + sdp.C_rowsum_max) <= 1e-6
+    assert grown["r_D"] <= 1e-6 and grown["r_P"] <= 1e-6 and abs(grown["gap"]) <= 1e-6
     assert grown["objective"] < stalled["objective"] - 1e-3
 
 
@@ -155,7 +157,7 @@ def test_lradmm_resume_repeats_the_uninterrupted_run():
     k = 409, a second at 987 that grows the rank to 3), so every part of the schedule is used;
     dropping the remembered dual infeasibility changes the run (the growth comes later)."""
     sdp = SDP.from_instance(I.maxcut_er(60, 6.0, seed=11))
-    p = Params(r0=2, rank_max=6, max_admm_iter=1500)
+    p = L.resolve_auto(sdp, Params(r0=2, rank_max=6, max_admm_iter=1500, polish="off"))
     ph1 = L.lralm(sdp, L.initial_factor(sdp, 2, p.seed), p)
     rho = min(p.h * ph1["sigma"], p.rho_max)
     full, conv = L.lradmm(sdp, ph1["U"], ph1["U"], ph1["lam"], rho, p)
@@ -176,3 +178,19 @@ def test_lradmm_resume_repeats_the_uninterrupted_run():
             L.lradmm_resume(sdp, forgetful, p, trace)
             grown_at = [i["k"] for i in trace if "grow_to" in i]
             assert grown_at and grown_at[0] > 987
+
+
+def test_auto_parameters_by_problem_class():
+    """The "auto" readings: Section 5.1's switch tolerance 1e-2 and h = 10 for MaxCut, 1e-3 for
+    other problems (h = 1 and the gamma scale 1 / 2 are readings); explicit values are kept."""
+    from oracle.lorads import resolve_auto, penalty_gamma
+    mc = SDP.from_instance(I.maxcut_er(30, 4.0, seed=1))
+    q = resolve_auto(mc, Params())
+    assert (q.switch_tol, q.h, q.gamma_scale) == (1e-2, 10.0, 1.0)
+    assert penalty_gamma(mc, Params()) == mc.C_rowsum_max
+    comp = SDP.from_instance(I.matrix_completion(6, 5, 2, 12, seed=3))
+    q = resolve_auto(comp, Params())
+    assert (q.switch_tol, q.h, q.gamma_scale) == (1e-3, 1.0, 2.0)
+    assert penalty_gamma(comp, Params()) == 2.0 * comp.C_rowsum_max
+    q = resolve_auto(comp, Params(switch_tol=1e-4, h=2.5, gamma_scale=3.0))
+    assert (q.switch_tol, q.h, q.gamma_scale) == (1e-4, 2.5, 3.0)
