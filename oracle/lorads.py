@@ -452,17 +452,16 @@ def _lradmm_loop(sdp: SDP, st: AdmmState, p: Params, trace: Optional[list]):
                         converged = True
                     else:
                         st.next_dual_test = st.k + max(p.dinf_every, st.k // 10)
-                        r = st.U.shape[1]
                         if info["d_psd"] <= p.tol:
                             pass
                         elif (st.prev_dinf is not None and info["d_psd"] > 0.9 * st.prev_dinf
-                                and p.escape_scale > 0 and r < cap):
-                            r_new = max(next_rank(r, cap, p), r + 1)
-                            st.U = escape_columns(sdp, st.U, Uh, y, r_new, p)
-                            st.V = escape_columns(sdp, st.V, Uh, y, r_new, p)
-                            st.growths += 1
-                            info["grow_to"] = r_new
-                            st.prev_dinf = None
+                                and p.escape_scale > 0):
+                            Ws, grew = escape(sdp, [st.U, st.V], Uh, y, p, cap)
+                            if Ws is not None:
+                                st.U, st.V = Ws
+                                st.growths += int(grew)
+                                info["grow_to"] = st.U.shape[1]
+                                st.prev_dinf = None
                         else:
                             st.prev_dinf = info["d_psd"]
         if trace is not None:
@@ -484,6 +483,38 @@ def escape_columns(sdp: SDP, W, Uh, y, r_new: int, p: Params):
     return np.concatenate([W, add], axis=1)
 
 
+def first_zero_column(W) -> int:
+    """Index of the first all-zero column of W (the zero padding a rank growth leaves, which every
+    step of the method keeps at zero), or -1."""
+    zero = np.nonzero(~np.any(W != 0.0, axis=0))[0]
+    return int(zero[0]) if zero.size else -1
+
+
+def escape(sdp: SDP, Ws, Uh, y, p: Params, cap: int):
+    """The escape from a point where lambda_min(C - A^T y) < 0: U is then rank-deficient in the
+    zero columns a growth left, and [U, tau z] descends (second order, tau^2 lambda_min), so the
+    first zero column takes tau z, with tau = escape_scale ||U_hat||_F / sqrt(r); with no zero
+    column left the rank grows first (Section 4.3's factor 1.5, at most the cap).  Ws: the
+    factors to change alike (U and V in Phase II, U in Phase III).  Returns (new factors,
+    whether the rank grew), or (None, False) at the cap with no zero column."""
+    c = first_zero_column(Ws[0])
+    if c >= 0:
+        _, z = min_eig_pair_dual_slack(sdp, y)
+        r = Ws[0].shape[1]
+        tau = p.escape_scale * float(np.linalg.norm(Uh)) / math.sqrt(r)
+        out = []
+        for W in Ws:
+            W = W.copy()
+            W[:, c] = tau * z
+            out.append(W)
+        return out, False
+    r = Ws[0].shape[1]
+    if r >= cap:
+        return None, False
+    r_new = max(next_rank(r, cap, p), r + 1)
+    return [escape_columns(sdp, W, Uh, y, r_new, p) for W in Ws], True
+
+
 # ======================================================================================
 # Phase III (not in the paper): Newton refinement of eq. prob:BM's stationarity
 # ======================================================================================
@@ -493,9 +524,10 @@ def escape_columns(sdp: SDP, W, Uh, y, r_new: int, p: Params):
 # feasible set of eq. prob:BM is a product of spheres, and Newton's method on that manifold
 # (Absil, Mahony and Sepulchre, "Optimization Algorithms on Matrix Manifolds", 2008, Ch. 6;
 # the Burer-Monteiro MaxCut setting of Boumal, Voroninski and Bandeira, 2016) converges
-# quadratically from the point Phase II reaches.  Each Newton step solves its system by
-# truncated CG (Nocedal and Wright, "Numerical Optimization", Algorithm 7.1) with Hessian-vector
-# products built from the same C-times-dense product as the ADMM subproblems.
+# quadratically from the point Phase II reaches; its trust-region form reaches second-order
+# critical points, where the rank test of Section 4.3's staircase is meaningful.  Each step
+# solves its model by truncated CG (Steihaug-Toint) with Hessian-vector products built from
+# the same C-times-dense product as the ADMM subproblems.
 def sphere_structure(sdp: SDP):
     """Per row j: the sphere radius sqrt(b_i / a_i) of its constraint i, i, and a_i."""
     rows, target = diagonal_row_scaling(sdp)
@@ -536,10 +568,21 @@ def riemannian_hessian(sdp: SDP, U, mu, Z):
     return 2.0 * tangent_project(U, sdp.C_times(Z) - mu[:, None] * Z)
 
 
-def truncated_cg(hess: Callable, g, max_iter: int):
-    """Newton direction d ~ -Hess^{-1} g by CG from d = 0 (Nocedal and Wright, Algorithm 7.1):
-    stops at ||Hess d + g|| <= eta ||g||, eta = min(0.5, sqrt(||g||)), or at a direction of
-    non-positive curvature (then the steepest-descent direction -g if no step was taken yet)."""
+def boundary_step(d, pdir, delta: float) -> float:
+    """tau >= 0 with ||d + tau p|| = delta (the positive root of a quadratic in tau)."""
+    a = float(np.vdot(pdir, pdir))
+    b = 2.0 * float(np.vdot(d, pdir))
+    c = float(np.vdot(d, d)) - delta * delta
+    return (-b + math.sqrt(max(b * b - 4.0 * a * c, 0.0))) / (2.0 * a)
+
+
+def truncated_cg(hess: Callable, g, delta: float, max_iter: int):
+    """Steihaug-Toint truncated CG for the trust-region model min g.d + d.Hess d / 2 subject to
+    ||d|| <= delta (Absil, Mahony and Sepulchre 2008, Algorithm 11; Nocedal and Wright,
+    Algorithm 7.2), from d = 0: stops at ||Hess d + g|| <= eta ||g||, eta = min(0.5, sqrt(||g||)),
+    and, where a CG direction has non-positive curvature or the next iterate would leave the
+    region, at the boundary point along that direction.  Returns (d, Hessian products, whether d
+    lies on the boundary)."""
     gn = float(np.linalg.norm(g))
     eta = min(0.5, math.sqrt(gn))
     d = np.zeros_like(g)
@@ -550,29 +593,39 @@ def truncated_cg(hess: Callable, g, max_iter: int):
         Hp = hess(pdir)
         pHp = float(np.vdot(pdir, Hp))
         if pHp <= 0.0:
-            return (-g if j == 0 else d), j
+            return d + boundary_step(d, pdir, delta) * pdir, j + 1, True
         alpha = rr / pHp
-        d = d + alpha * pdir
+        d_next = d + alpha * pdir
+        if float(np.vdot(d_next, d_next)) >= delta * delta:
+            return d + boundary_step(d, pdir, delta) * pdir, j + 1, True
+        d = d_next
         res = res - alpha * Hp
         rr_new = float(np.vdot(res, res))
         if math.sqrt(rr_new) <= eta * gn:
-            return d, j + 1
+            return d, j + 1, False
         pdir = res + (rr_new / rr) * pdir
         rr = rr_new
-    return d, max_iter
+    return d, max_iter, False
 
 
 def bm_newton_polish(sdp: SDP, U0, p: Params) -> dict:
-    """Phase III from U0 (Phase II's U_hat): Newton steps on the product of spheres, each
-    followed by an Armijo backtracking line search (sufficient decrease 1e-4, step halved)
-    along the retraction, until r_D(U, lambda(U)) <= tol; then the dual test
-    max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf) <= tol.  A failed dual test means the rank
-    is too small: the rank grows as in Phase II (a column tau z along the eigenvector of
-    lambda_min) and the Newton steps go on.  On the manifold A(U U^T) = b holds to rounding and
-    the gap with y = -lambda(U) vanishes identically (<C, U U^T> = sum_j mu_j ||U_j||^2 = b^T y)."""
+    """Phase III from U0 (Phase II's U_hat): the Riemannian trust-region Newton method on the
+    product of spheres (Absil, Mahony and Sepulchre 2008, Algorithm 10; Absil, Baker and
+    Gallivan 2007), which reaches second-order critical points: each step minimises the
+    quadratic model within radius Delta by truncated CG, then compares the model's decrease with
+    the true one along the retraction, rho = (f(U) - f(R(U + d))) / (m(0) - m(d)); the step is
+    taken when rho > 0.1, Delta shrinks by 4 when rho < 1/4 and doubles (up to Delta_max =
+    ||U||_F) when rho > 3/4 on the boundary; Delta starts at Delta_max / 8.  It runs until
+    r_D(U, lambda(U)) <= tol, then tests max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf) <= tol.
+    A failed dual test at a second-order critical point means the rank is too small: the rank
+    grows as in Phase II (a column tau z along the eigenvector of lambda_min) and the steps go
+    on.  On the manifold A(U U^T) = b holds to rounding and the gap with y = -lambda(U) vanishes
+    identically (<C, U U^T> = sum_j mu_j ||U_j||^2 = b^T y)."""
     rad, con, a = sphere_structure(sdp)
     cap = rank_cap(sdp.m, sdp.n, p)
     U = retract(U0, rad)
+    delta_max = float(np.linalg.norm(U))
+    delta = delta_max / 8.0
     steps = cg_total = growths = 0
     converged = False
     lam = np.zeros(sdp.m)
@@ -584,25 +637,27 @@ def bm_newton_polish(sdp: SDP, U0, p: Params) -> dict:
             if not p.kkt_dinf or dual_psd_measure(sdp, -lam) <= p.tol:
                 converged = True
                 break
-            r = U.shape[1]
-            if r >= cap or p.escape_scale <= 0:
+            Ws, grew = escape(sdp, [U], U, -lam, p, cap) if p.escape_scale > 0 else (None, False)
+            if Ws is None:
                 break
-            U = retract(escape_columns(sdp, U, U, -lam, max(next_rank(r, cap, p), r + 1), p),
-                        rad)
-            growths += 1
+            U = retract(Ws[0], rad)
+            growths += int(grew)
             continue
         if steps >= p.newton_max:
             break
-        d, j = truncated_cg(lambda Z: riemannian_hessian(sdp, U, mu, Z), g, p.newton_cg_max)
-        cg_total += j
-        f0 = sdp.C_inner(U, U)
-        slope = float(np.vdot(g, d))
-        t = 1.0
+        hess = lambda Z: riemannian_hessian(sdp, U, mu, Z)
+        d, j, on_boundary = truncated_cg(hess, g, delta, p.newton_cg_max)
+        cg_total += j + 2                 # the CG's Hessian products and the model's
+        pred = -(float(np.vdot(g, d)) + 0.5 * float(np.vdot(d, hess(d))))
         Un = retract(U + d, rad)
-        while sdp.C_inner(Un, Un) > f0 + 1e-4 * t * slope and t > 2.0 ** -30:
-            t *= 0.5
-            Un = retract(U + t * d, rad)
-        U = Un
+        actual = sdp.C_inner(U, U) - sdp.C_inner(Un, Un)
+        ratio = actual / pred if pred > 0.0 else -1.0
+        if ratio < 0.25:
+            delta *= 0.25
+        elif ratio > 0.75 and on_boundary:
+            delta = min(2.0 * delta, delta_max)
+        if ratio > 0.1:
+            U = Un
         steps += 1
     return dict(U=U, lam=lam, converged=converged, steps=steps, cg=cg_total, growths=growths)
 
@@ -807,11 +862,11 @@ def alm_refine(sdp: SDP, U0, lam0, sigma0: float, p: Params, growth0: int) -> di
         if not p.kkt_dinf or dual_psd_measure(sdp, -lam) <= p.tol:
             converged = True
             break
-        r = U.shape[1]
-        if r >= cap or p.escape_scale <= 0:
+        Ws, grew = escape(sdp, [U], U, -lam, p, cap) if p.escape_scale > 0 else (None, False)
+        if Ws is None:
             break
-        U = escape_columns(sdp, U, U, -lam, max(next_rank(r, cap, p), r + 1), p)
-        growths += 1
+        U = Ws[0]
+        growths += int(grew)
     return dict(U=U, lam=lam, sigma=sigma, converged=converged, outer=outer, inner=inner,
                 growths=growths)
 

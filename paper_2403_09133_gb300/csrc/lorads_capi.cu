@@ -120,6 +120,7 @@ struct lorads_problem {
   bool has_b = false;
   // Phase II start (phase1 == 0): lorads_set_start (V = U) or lorads_set_state (a resume)
   int32_t start_r = 0;
+  int32_t start_nz = 0;   // columns start_nz .. start_r-1 of the start are zero
   std::vector<double> start_U, start_V, start_lam;
   double start_rho = 0.0;
   bool has_start = false;
@@ -171,6 +172,18 @@ static int check_cuda(cudaError_t e) {
     int _s = check_cuda(x);                     \
     if (_s != LORADS_OK) return _s;             \
   } while (0)
+
+// 1 + the last column of the n x r row-major factors (V may be NULL) with a non-zero entry
+static int32_t trailing_zero_from(const double* U, const double* V, int64_t n, int32_t r) {
+  int32_t last = -1;
+  for (int64_t j = 0; j < n; ++j)
+    for (int32_t c = r - 1; c > last; --c)
+      if (U[j * r + c] != 0.0 || (V != nullptr && V[j * r + c] != 0.0)) {
+        last = c;
+        break;
+      }
+  return last + 1;
+}
 
 static void invalidate(lorads_problem* p) {
   p->assembled = false;
@@ -440,6 +453,7 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   dv.seed = prm->seed;
   dv.phase1 = prm->phase1 ? 1 : 0;
   dv.r_start = p->start_r;
+  dv.nz0 = p->start_nz;
   dv.rho0 = p->start_rho > 0 ? p->start_rho : 100.0;
   dv.prev_dinf0 = std::numeric_limits<double>::quiet_NaN();
   if (!dv.phase1 && p->has_start && p->start_resume) {
@@ -954,6 +968,7 @@ int lorads_set_start(lorads_problem* p, int32_t r, const double* U0, const doubl
   for (int64_t t = 0; t < p->n * r; ++t)
     if (!is_finite_value(U0[t])) return LORADS_ERR_ARG;
   p->start_r = r;
+  p->start_nz = trailing_zero_from(U0, nullptr, p->n, r);
   p->start_U.assign(U0, U0 + p->n * r);
   if (lambda0)
     p->start_lam.assign(lambda0, lambda0 + p->m);
@@ -1115,6 +1130,7 @@ int lorads_set_state(lorads_problem* p, const lorads_state* st, const double* U,
     for (int64_t i = 0; i < p->m; ++i)
       if (!is_finite_value(lambda[i])) return LORADS_ERR_ARG;
   p->start_r = st->rank;
+  p->start_nz = trailing_zero_from(U, V, p->n, st->rank);
   p->start_U.assign(U, U + nr);
   p->start_V.assign(V, V + nr);
   if (lambda)

@@ -45,6 +45,7 @@ struct DevParams {
   // continuation of a checkpointed Phase II (resume = 1): V is given apart from U, and the
   // iteration counter, the final-test schedule and the reported counters go on from here
   int resume;
+  int nz0;               // Phase II start: columns nz0 .. r_start-1 of the start are zero
   int k0, next_test0, cg0, hess0, outer0, lbfgs0, growths0;
   double prev_dinf0, sigma0;
 };
@@ -192,13 +193,14 @@ struct Solver {
   int refine_outer, refine_lbfgs;
   int newton_steps, newton_cg;
   long long t_p3;     // start of Phase III (0: none)
+  int nzc;            // columns nzc .. r-1 of U and V are zero (the padding of a rank growth)
 
   __device__ Solver(const SolverArgs<T>& a, Scope& s)
       : A(a), sc(s), P(a.P), prm(a.prm), n(a.P.n), m(a.P.m), r(0), ld(0), status(ST_OK),
         cg_iters(0), hess(0), admm_iters(0), alm_outer(0), lbfgs_iters(0), growths(0),
         last_rs(0.0), last_lmin(NAN), lmin_at(-1), uh_norm2(0.0), rs_num(-1.0), rs_den(0.0),
         ndt(0), pdinf(NAN), last_rd2(0.0), to_polish(false), fp64_bulk(false), alm_done(false),
-        refine_outer(0), refine_lbfgs(0), newton_steps(0), newton_cg(0), t_p3(0) {}
+        refine_outer(0), refine_lbfgs(0), newton_steps(0), newton_cg(0), t_p3(0), nzc(0) {}
 
   __device__ void set_rank(int rr) {
     r = rr;
@@ -656,6 +658,7 @@ struct Solver {
         int r_new = (int)ceil(prm.rank_factor * r - 1e-9);
         if (r_new > prm.rank_cap) r_new = prm.rank_cap;
         if (!grow_rank(r_new, growths)) return false;
+        nzc = r;
         continue;
       }
       for (int i = sc.tid(); i < m; i += sc.nthreads()) A.lam[i] += sigma * A.e[i];
@@ -898,7 +901,7 @@ struct Solver {
     if (d <= prm.tol && rd_ok) return 1;
     ndt = admm_iters + max(prm.dinf_every, admm_iters / 10);
     if (d <= prm.tol) return 0;
-    if (pdinf == pdinf && d > 0.9 * pdinf && prm.escape_scale > 0.0 && r < prm.rank_cap) {
+    if (pdinf == pdinf && d > 0.9 * pdinf && escape_possible()) {
       if (!escape_grow()) return -1;
       pdinf = NAN;
       return 2;
@@ -907,17 +910,43 @@ struct Solver {
     return 0;
   }
 
-  // rank growth along the eigenvector of lambda_min(C - A^T y): r -> ceil(1.5 r) (at least
-  // r + 1, at most the cap), new columns [tau z, 0, ...] in U and V (Section 4.3's rule,
-  // applied where the rank-r problem has stalled)
+  // The escape from a point where lambda_min(C - A^T y) < 0 (Section 4.3's rank rule where the
+  // rank-r problem has stalled): the first zero column of U and V (the padding a growth left,
+  // which every step keeps at zero) takes tau z, z the Ritz vector of lambda_min, tau =
+  // escape_scale ||U_hat||_F / sqrt(r) (uh_norm2 = ||U_hat||_F^2); with no zero column left the
+  // rank grows to ceil(1.5 r) (at least r + 1, at most the cap) with new columns [tau z, 0, ...].
+  // The caller checks escape_possible() first.
+  __device__ bool escape_possible() const {
+    return prm.escape_scale > 0.0 && (nzc < r || r < prm.rank_cap);
+  }
   __device__ bool escape_grow() {
     double zn2 = 0.0, lm;
     if (!lanczos_lambda_min(lm, true, &zn2)) return false;
-    const int K = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
+    const int Kmax = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
+    const double* zv = A.Y + 2 * Kmax;
+    if (nzc < r) {
+      const double tau = zn2 > 0.0 ? prm.escape_scale * sqrt(uh_norm2 / (double)r / zn2) : 0.0;
+      const bool shadow = (const void*)A.Ut != (const void*)A.U;
+      const int c = nzc;
+      for (int j = sc.tid(); j < n; j += sc.nthreads()) {
+        const double x = tau * zv[j];
+        const long long o = (long long)j * ld + c;
+        A.U[o] = x;
+        A.V[o] = x;
+        if (shadow) {
+          A.Ut[o] = (T)x;
+          A.Vt[o] = (T)x;
+        }
+      }
+      ++nzc;
+      return sc.sync();
+    }
+    const int r_old = r;
     int r_new = (int)ceil(prm.rank_factor * r - 1e-9);
     if (r_new <= r) r_new = r + 1;
     if (r_new > prm.rank_cap) r_new = prm.rank_cap;
-    if (!grow_rank_phase2(r_new, A.Y + 2 * K, zn2)) return false;
+    if (!grow_rank_phase2(r_new, zv, zn2)) return false;
+    nzc = r_old + 1;
     ++growths;
     return true;
   }
@@ -1535,32 +1564,40 @@ struct Solver {
   //   Riemannian gradient  g_j = 2 ((C U)_j - mu_j U_j)            (= 2 ((C + A^T lambda) U)_j)
   //   Riemannian Hessian   (H Z)_j = 2 P_j((C Z)_j - mu_j Z_j),  P_j(W) = W - (W.U_j/||U_j||^2) U_j
   // (Absil, Mahony and Sepulchre 2008, Ch. 6), and r_D = ||g|| / (2 (1 + ||C||_F)); on the
-  // manifold A(U U^T) = b holds and the gap with y = -lambda(U) is zero.  Each Newton step solves
-  // H d = -g by truncated CG (Nocedal and Wright, Algorithm 7.1: stop at ||H d + g|| <= eta ||g||,
-  // eta = min(0.5, sqrt(||g||)), or at non-positive curvature, then -g if no step was taken),
-  // run as the Chronopoulos-Gear recurrence (one reduction and one barrier per iteration: the
-  // Hessian reads the neighbours' residual), then backtracks from t = 1 until
-  // f(R(U + t d)) <= f(U) + 1e-4 t g.d, R the row scaling.  Once r_D <= tol the dual measure is
-  // tested (Lanczos); a failure grows the rank along the eigenvector of lambda_min as in Phase II.
-  // All in FP64.  Arrays: U (iterate), V (trial), CWn (C U), grad (g), dir (d), grad_old (CG
-  // residual r), S slot 0 (CG direction p), S slot 1 (s = H p), Y slot 0 (w = H r), e (mu, by row).
+  // manifold A(U U^T) = b holds and the gap with y = -lambda(U) is zero.  The method is the
+  // Riemannian trust-region Newton method (ibid., Algorithm 10), which reaches second-order
+  // critical points: each step minimises the model g.d + d.H d / 2 over ||d|| <= Delta by
+  // truncated CG (Steihaug-Toint, ibid. Algorithm 11: stop at ||H d + g|| <= eta ||g||,
+  // eta = min(0.5, sqrt(||g||)), or on the boundary along a direction of non-positive curvature
+  // or one that leaves the region), run as the Chronopoulos-Gear recurrence (one reduction and one
+  // barrier per iteration: the Hessian reads the neighbours' residual); the step R(U + d), R the
+  // row scaling, is taken when rho = (f(U) - f(R(U + d))) / (model decrease) > 0.1; Delta shrinks
+  // by 4 when rho < 1/4 and doubles (up to ||U||_F) when rho > 3/4 on the boundary, from
+  // ||U||_F / 8.  Once r_D <= tol the dual measure is tested (Lanczos); a failure escapes along
+  // the eigenvector of lambda_min (escape_grow).
+  // The gradient, the multipliers, the line search and the retraction are FP64; the CG of a
+  // Newton step runs in the form's element type T (FP32 in the mixed form: the step is an
+  // inexact solve to a relative residual of at least sqrt(||g||), far above FP32 rounding).
+  // Arrays: U (iterate, FP64; Ut its T shadow), V (trial), grad (g), e (mu, by row), and in T the
+  // CG's R (residual), Pd (direction), Sv (H p), HP (H r) and Dl (the Newton direction d).
   // ----------------------------------------------------------------------------------
-  // (H Z)_j for the tangent field Z (neighbours' rows of Z must be visible); Zj is row j of Z
-  __device__ __forceinline__ void sphere_hess_row(int j, const double* Z, const Frag<double>& Zj,
-                                                  const Frag<double>& Uj, double u2, double mu,
-                                                  Frag<double>& out) const {
-    Frag<double> mCZ;
-    spmm_row<double>(P, Z, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0, tm, mCZ);
+  // (H Z)_j for the tangent field Z (neighbours' rows of Z must be visible); Zj is row j of Z,
+  // Uj row j of the iterate; in T (the CG of a Newton step runs in the form's element type)
+  __device__ __forceinline__ void sphere_hess_row(int j, const T* Z, const Frag<T>& Zj,
+                                                  const Frag<T>& Uj, T u2, T mu,
+                                                  Frag<T>& out) const {
+    Frag<T> mCZ;
+    spmm_row<T>(P, Z, ld, j, nullptr, nullptr, 0.0, 0.0, 0.0, T(0), tm, mCZ);
     // W = (C Z)_j - mu Z_j
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
 #pragma unroll
       for (int e = 0; e < CHUNK; ++e) out.v[k][e] = -mCZ.v[k][e] - mu * Zj.v[k][e];
-    const double c = frag_dot(out, Uj, tm) / u2;
+    const T c = frag_dot(out, Uj, tm) / u2;
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
 #pragma unroll
-      for (int e = 0; e < CHUNK; ++e) out.v[k][e] = 2.0 * (out.v[k][e] - c * Uj.v[k][e]);
+      for (int e = 0; e < CHUNK; ++e) out.v[k][e] = T(2) * (out.v[k][e] - c * Uj.v[k][e]);
   }
 
   // g, mu, lambda(U) and C U at the iterate in A.U; v = (||g||^2, <C, U U^T>, ||U||_F^2, time)
@@ -1592,31 +1629,44 @@ struct Solver {
     return sc.reduce(v, 4);
   }
 
-  // truncated CG for H d = -g (see above); d in A.dir; returns the iterations in it
-  __device__ bool sphere_newton_cg(double g2, int& it) {
-    double* const R = A.grad_old;
-    double* const Pp = A.S;
-    const long long NS = (long long)n * A.ld_cap;
-    double* const Sv = A.S + NS;
-    double* const W = A.Y;
-    // r_0 = -g, w_0 = H r_0 = -H g (the gradient of every row is visible after its reduction)
-    double g3[2] = {0.0, 0.0};
+  // Truncated CG (Steihaug-Toint) for the trust-region model min g.d + d.H d / 2, ||d|| <= delta,
+  // in T: the residual, direction and Hessian products in the CG arrays of Phase II (A.R, A.Pd,
+  // A.Sv, A.HP), d in A.Dl, the iterate's T shadow A.Ut (the mixed form runs this CG in FP32;
+  // the gradient, the model test and the retraction stay FP64).  Run as the Chronopoulos-Gear
+  // recurrence; thread 0 of every CTA carries ||p||^2, d.p and ||d||^2 by their recurrences
+  // (||p_k+1||^2 = r.r + beta^2 ||p_k||^2, d_k+1.p_k+1 = beta (d_k.p_k + alpha ||p_k||^2), since
+  // r_k+1 is orthogonal to p_k and to d_k+1), so that a direction of non-positive curvature, or a
+  // step that would leave the region, ends the CG at the boundary along it.  Returns the Hessian
+  // products in it and whether d lies on the boundary.
+  __device__ bool sphere_tcg(double g2, double delta, int& it, bool& on_boundary) {
+    T* const R = A.R;
+    T* const Pp = A.Pd;
+    T* const Sv = A.Sv;
+    T* const W = A.HP;
+    T* const D = A.Dl;
+    const T* const Us = A.Ut;
+    // r_0 = -g, w_0 = H r_0
     for (int j = tm.id; j < n; j += tm.count) {
-      Frag<double> Uj, gj, w;
-      frag_load(Uj, A.U, j, ld, tm);
+      Frag<double> gj;
+      Frag<T> r;
       frag_load(gj, A.grad, j, ld, tm);
-      const double u2 = frag_dot(Uj, Uj, tm);
-      sphere_hess_row(j, A.grad, gj, Uj, u2, A.e[j], w);
+      frag_convert(r, gj);
 #pragma unroll
       for (int k = 0; k < KMAX; ++k)
 #pragma unroll
-        for (int e = 0; e < CHUNK; ++e) {
-          gj.v[k][e] = -gj.v[k][e];
-          w.v[k][e] = -w.v[k][e];
-        }
-      frag_store(gj, R, j, ld, tm);
+        for (int e = 0; e < CHUNK; ++e) r.v[k][e] = -r.v[k][e];
+      frag_store(r, R, j, ld, tm);
+    }
+    if (!sc.sync()) return false;
+    double g3[2] = {0.0, 0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<T> Uj, r, w;
+      frag_load(Uj, Us, j, ld, tm);
+      frag_load(r, R, j, ld, tm);
+      const T u2 = frag_dot(Uj, Uj, tm);
+      sphere_hess_row(j, R, r, Uj, u2, (T)A.e[j], w);
       frag_store(w, W, j, ld, tm);
-      const double d1 = frag_dot(gj, gj, tm), d2 = frag_dot(w, gj, tm);
+      const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(w, r, tm);
       if (tm.lane == 0) {
         g3[0] += d1;
         g3[1] += d2;
@@ -1624,35 +1674,53 @@ struct Solver {
     }
     if (!sc.reduce(g3, 2)) return false;
     const bool lead = threadIdx.x == 0;
-    double* shs = sc.scratch() + 4;
+    double* shs = sc.scratch() + 4;     // state (0 go on, 1 stop, 2 NaN, 3 last step), a, b
     const double eta = fmin(0.5, sqrt(sqrt(g2)));
     const double target2 = eta * eta * g2;
-    double gam = 0.0, ga = 0.0;
+    const double dl2 = delta * delta;
+    // thread 0: gam = r.r, ga = gam * alpha, pp = ||p||^2, dp = d.p, dd = ||d||^2 (of the
+    // direction / iterate the next pass forms)
+    double gam = 0.0, ga = 0.0, pp = 0.0, dp = 0.0, dd = 0.0;
     if (lead) {
       gam = g3[0];
       const double del = g3[1];
-      const double alpha = del > 0.0 ? gam / del : 0.0;
+      pp = gam;
+      int state = 0;
+      double alpha = 0.0;
+      if (!(gam == gam) || !(del == del)) {
+        state = 2;
+      } else if (gam <= target2) {
+        state = 1;
+      } else if (!(del > 0.0) || gam * (gam / del) * (gam / del) >= dl2) {
+        alpha = delta / sqrt(gam);       // to the boundary along p_0 = -g
+        state = 3;
+      } else {
+        alpha = gam / del;
+      }
       ga = gam * alpha;
-      shs[0] = (gam > target2 && del > 0.0) ? 0.0 : 1.0;
+      shs[0] = (double)state;
       shs[1] = alpha;
       shs[2] = 0.0;
     }
     __syncthreads();
-    int go = shs[0] == 0.0;
-    double a_t = shs[1], b_t = 0.0;
+    int state = (int)shs[0];
+    T a_t = (T)shs[1], b_t = T(0);
     __syncthreads();
+    if (state == 2) status = ST_NAN;
     it = 0;
-    while (go && it < prm.newton_cg_max) {
+    on_boundary = state == 3;
+    bool wrote = false;
+    while ((state == 0 || state == 3) && it < prm.newton_cg_max) {
       for (int j = tm.id; j < n; j += tm.count) {
-        Frag<double> r, w, pp, ss, x;
+        Frag<T> r, w, pd, ss, x;
         frag_load(r, R, j, ld, tm);
         frag_load(w, W, j, ld, tm);
-        if (it > 0) {
-          frag_load(pp, Pp, j, ld, tm);
+        if (wrote) {
+          frag_load(pd, Pp, j, ld, tm);
           frag_load(ss, Sv, j, ld, tm);
-          frag_load(x, A.dir, j, ld, tm);
+          frag_load(x, D, j, ld, tm);
         } else {
-          frag_zero(pp);
+          frag_zero(pd);
           frag_zero(ss);
           frag_zero(x);
         }
@@ -1660,26 +1728,28 @@ struct Solver {
         for (int k = 0; k < KMAX; ++k)
 #pragma unroll
           for (int e = 0; e < CHUNK; ++e) {
-            pp.v[k][e] = fma(b_t, pp.v[k][e], r.v[k][e]);
+            pd.v[k][e] = fma(b_t, pd.v[k][e], r.v[k][e]);
             ss.v[k][e] = fma(b_t, ss.v[k][e], w.v[k][e]);
-            x.v[k][e] = fma(a_t, pp.v[k][e], x.v[k][e]);
+            x.v[k][e] = fma(a_t, pd.v[k][e], x.v[k][e]);
             r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
           }
-        frag_store(pp, Pp, j, ld, tm);
+        frag_store(pd, Pp, j, ld, tm);
         frag_store(ss, Sv, j, ld, tm);
-        frag_store(x, A.dir, j, ld, tm);
+        frag_store(x, D, j, ld, tm);
         frag_store(r, R, j, ld, tm);
       }
+      wrote = true;
+      if (state == 3) break;             // the boundary step: d is final
       if (!sc.sync()) return false;
       double z[2] = {0.0, 0.0};
       for (int j = tm.id; j < n; j += tm.count) {
-        Frag<double> Uj, r, w;
-        frag_load(Uj, A.U, j, ld, tm);
+        Frag<T> Uj, r, w;
+        frag_load(Uj, Us, j, ld, tm);
         frag_load(r, R, j, ld, tm);
-        const double u2 = frag_dot(Uj, Uj, tm);
-        sphere_hess_row(j, R, r, Uj, u2, A.e[j], w);
+        const T u2 = frag_dot(Uj, Uj, tm);
+        sphere_hess_row(j, R, r, Uj, u2, (T)A.e[j], w);
         frag_store(w, W, j, ld, tm);
-        const double d1 = frag_dot(r, r, tm), d2 = frag_dot(w, r, tm);
+        const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(w, r, tm);
         if (tm.lane == 0) {
           z[0] += d1;
           z[1] += d2;
@@ -1687,21 +1757,79 @@ struct Solver {
       }
       if (!sc.reduce(z, 2)) return false;
       ++it;
-      if (!cg_scalars(lead, shs, z, target2, gam, ga, go, a_t, b_t)) break;
-    }
-    if (it == 0) {
-      // non-positive curvature along -g: the steepest-descent direction
-      for (int j = tm.id; j < n; j += tm.count) {
-        Frag<double> gj;
-        frag_load(gj, A.grad, j, ld, tm);
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-#pragma unroll
-          for (int e = 0; e < CHUNK; ++e) gj.v[k][e] = -gj.v[k][e];
-        frag_store(gj, A.dir, j, ld, tm);
+      if (lead) {
+        // the pass just made: d += alpha p (alpha = ga / gam), so d.p and ||d||^2 move on
+        const double alpha_prev = ga / gam;
+        dd += 2.0 * alpha_prev * dp + alpha_prev * alpha_prev * pp;
+        dp += alpha_prev * pp;           // d_k+1 . p_k
+        const double gam_new = z[0], del_new = z[1];
+        int st = 0;
+        double alpha = 0.0, beta = 0.0;
+        if (!(gam_new == gam_new) || !(del_new == del_new)) {
+          st = 2;
+        } else if (gam_new <= target2) {
+          st = 1;
+        } else {
+          beta = gam_new / gam;
+          pp = gam_new + beta * beta * pp;          // ||p_k+1||^2
+          dp = beta * dp;                           // d_k+1 . p_k+1
+          const double D = del_new * ga - gam_new * gam_new;   // p.Hp = D / ga
+          bool to_boundary = !(D > 0.0);
+          if (!to_boundary) {
+            alpha = gam_new * ga / D;
+            to_boundary = dd + 2.0 * alpha * dp + alpha * alpha * pp >= dl2;
+          }
+          if (to_boundary) {
+            const double qa = pp, qb = 2.0 * dp, qc = dd - dl2;
+            alpha = (-qb + sqrt(fmax(qb * qb - 4.0 * qa * qc, 0.0))) / (2.0 * qa);
+            st = 3;
+          }
+          ga = gam_new * alpha;
+          gam = gam_new;
+        }
+        shs[0] = (double)st;
+        shs[1] = alpha;
+        shs[2] = beta;
       }
-      if (!sc.sync()) return false;
+      __syncthreads();
+      state = (int)shs[0];
+      a_t = (T)shs[1];
+      b_t = (T)shs[2];
+      __syncthreads();
+      if (state == 2) status = ST_NAN;
+      if (state == 3) on_boundary = true;
     }
+    if (!wrote) {
+      // no step taken (the gradient already small, or a NaN): d = 0
+      for (int j = tm.id; j < n; j += tm.count) {
+        Frag<T> x;
+        frag_zero(x);
+        frag_store(x, D, j, ld, tm);
+      }
+    }
+    return sc.sync();
+  }
+
+  // the model's decrease -(g.d + d.H d / 2) for the d in A.Dl (neighbours' d visible)
+  __device__ bool sphere_model_decrease(double& pred) {
+    double v[2] = {0.0, 0.0};
+    for (int j = tm.id; j < n; j += tm.count) {
+      Frag<T> Uj, dj, w;
+      Frag<double> gj, dd;
+      frag_load(Uj, A.Ut, j, ld, tm);
+      frag_load(dj, A.Dl, j, ld, tm);
+      const T u2 = frag_dot(Uj, Uj, tm);
+      sphere_hess_row(j, A.Dl, dj, Uj, u2, (T)A.e[j], w);
+      frag_load(gj, A.grad, j, ld, tm);
+      frag_convert(dd, dj);
+      const double a1 = frag_dot(gj, dd, tm), a2 = (double)frag_dot(dj, w, tm);
+      if (tm.lane == 0) {
+        v[0] += a1;
+        v[1] += a2;
+      }
+    }
+    if (!sc.reduce(v, 2)) return false;
+    pred = -(v[0] + 0.5 * v[1]);
     return true;
   }
 
@@ -1710,8 +1838,10 @@ struct Solver {
     double v[1] = {0.0};
     for (int j = tm.id; j < n; j += tm.count) {
       Frag<double> Uj, dj;
+      Frag<T> dt;
       frag_load(Uj, A.U, j, ld, tm);
-      frag_load(dj, A.dir, j, ld, tm);
+      frag_load(dt, A.Dl, j, ld, tm);
+      frag_convert(dj, dt);
       if (want_slope) {
         Frag<double> gj;
         frag_load(gj, A.grad, j, ld, tm);
@@ -1746,18 +1876,28 @@ struct Solver {
     return true;
   }
 
-  // copies src into dst (both n x ld FP64), then a barrier
-  __device__ bool copy_rows(const double* src, double* dst) {
+  // copies src into dst (both n x ld FP64), and into the T shadow tdst unless it aliases the
+  // masters (nullptr: none), then a barrier
+  __device__ bool copy_rows(const double* src, double* dst, T* tdst = nullptr) {
+    const bool sh = tdst != nullptr && (const void*)tdst != (const void*)A.U &&
+                    (const void*)tdst != (const void*)A.V;
     for (int j = tm.id; j < n; j += tm.count) {
       Frag<double> x;
       frag_load(x, src, j, ld, tm);
       frag_store(x, dst, j, ld, tm);
+      if (sh) {
+        Frag<T> t;
+        frag_convert(t, x);
+        frag_store(t, tdst, j, ld, tm);
+      }
     }
     return sc.sync();
   }
 
-  // U <- rows of U scaled onto the spheres (after a rank growth), V = U
+  // U <- rows of U scaled onto the spheres (at the start, after a rank growth), V = U, and the
+  // T shadow of U
   __device__ bool sphere_retract_u() {
+    const bool sh = (const void*)A.Ut != (const void*)A.U;
     for (int j = tm.id; j < n; j += tm.count) {
       Frag<double> Uj;
       frag_load(Uj, A.U, j, ld, tm);
@@ -1768,6 +1908,11 @@ struct Solver {
         for (int e = 0; e < CHUNK; ++e) Uj.v[k][e] *= sc2;
       frag_store(Uj, A.U, j, ld, tm);
       frag_store(Uj, A.V, j, ld, tm);
+      if (sh) {
+        Frag<T> t;
+        frag_convert(t, Uj);
+        frag_store(t, A.Ut, j, ld, tm);
+      }
     }
     return sc.sync();
   }
@@ -1779,17 +1924,22 @@ struct Solver {
     if (!copy_rows(A.tmp, A.U)) return false;
     if (!sphere_retract_u()) return false;
     const double tol_g2 = 4.0 * prm.tol * (1.0 + P.C_fro) * prm.tol * (1.0 + P.C_fro);
+    double delta_max = -1.0, delta = 0.0;
     for (;;) {
       double v[4];
       if (!sphere_gradient(v)) return false;
       const double g2 = v[0], f0 = v[1];
       if (!(g2 == g2) || !(f0 == f0)) { status = ST_NAN; return true; }
+      if (delta_max < 0.0) {
+        delta_max = sqrt(v[2]);          // ||U||_F
+        delta = delta_max / 8.0;
+      }
       if (g2 <= tol_g2) {
         if (!prm.kkt_dinf) return true;
         if (!lanczos_lambda_min(last_lmin)) return false;
         lmin_at = admm_iters;
         if (dual_psd(last_lmin) <= prm.tol) return true;
-        if (!(prm.escape_scale > 0.0) || r >= prm.rank_cap) { status = ST_MAXITER; return true; }
+        if (!escape_possible()) { status = ST_MAXITER; return true; }
         uh_norm2 = v[2];
         if (!copy_rows(A.U, A.V)) return false;
         if (!escape_grow()) return false;
@@ -1799,17 +1949,20 @@ struct Solver {
       if ((long long)v[3] > prm.time_limit_ns) { status = ST_TIMEOUT; return true; }
       if (newton_steps >= prm.newton_max) { status = ST_MAXITER; return true; }
       int it = 0;
-      if (!sphere_newton_cg(g2, it)) return false;
-      newton_cg += it;
+      bool on_boundary = false;
+      if (!sphere_tcg(g2, delta, it, on_boundary)) return false;
       if (status != ST_OK) return true;
-      double slope = 0.0, t = 1.0, f = 0.0;
-      for (int ls = 0; ls < 31; ++ls) {
-        if (!sphere_trial(t, ls == 0, slope)) return false;
-        if (!trial_objective(f)) return false;
-        if (f <= f0 + 1e-4 * t * slope) break;
-        t *= 0.5;
+      double pred = 0.0, slope = 0.0, f = 0.0;
+      if (!sphere_model_decrease(pred)) return false;
+      newton_cg += it + 2;                 // the CG's Hessian products, its first, the model's
+      if (!sphere_trial(1.0, false, slope)) return false;
+      if (!trial_objective(f)) return false;
+      const double ratio = pred > 0.0 ? (f0 - f) / pred : -1.0;
+      if (ratio < 0.25) delta *= 0.25;
+      else if (ratio > 0.75 && on_boundary) delta = fmin(2.0 * delta, delta_max);
+      if (ratio > 0.1) {
+        if (!copy_rows(A.V, A.U, A.Ut)) return false;
       }
-      if (!copy_rows(A.V, A.U)) return false;
       ++newton_steps;
     }
   }
@@ -1844,7 +1997,7 @@ struct Solver {
       if (!lanczos_lambda_min(last_lmin)) return false;
       lmin_at = admm_iters;
       if (dual_psd(last_lmin) <= prm.tol) break;
-      if (!(prm.escape_scale > 0.0) || r >= prm.rank_cap) { status = ST_MAXITER; break; }
+      if (!escape_possible()) { status = ST_MAXITER; break; }
       if (!u_norm2(uh_norm2)) return false;
       if (!copy_rows(A.U, A.V)) return false;
       if (!escape_grow()) return false;
@@ -2302,6 +2455,7 @@ struct Solver {
     t_start = globaltimer_ns();
     double sigma = 0.0, rho = 0.0;
     set_rank(prm.phase1 ? prm.r0 : prm.r_start);
+    nzc = prm.phase1 ? r : min(max(prm.nz0, 0), r);
     if (prm.phase1) {
       if (!phase1(sigma)) { finish_error(); return; }
       if (status != ST_OK) { finish(sigma, rho, nullptr, 0, 0); return; }

@@ -2,8 +2,9 @@
 (n1 = n2 = 20,000), rank-5 M = P Q^T, 15,694,167 observed entries, r = 24 (Section 5.4's
 SDP; the paper's MC_40000).
 
-Parity: the FP32 Hessian apply against the oracle on every row; the solve against what the
-problem fixes (exact recovery: objective 2 ||M||_*, and Z = M on entries never observed)."""
+Parity: the FP32 Hessian apply against the oracle on every row (within FP32 rounding of the
+terms each row sums); the solve against what the problem fixes (exact recovery: objective
+2 ||M||_* to 1e-6, the final test at 1e-6, and Z = M on entries never observed)."""
 import numpy as np
 import pytest
 
@@ -44,18 +45,25 @@ def test_mc_full_size_hessian_parity(cuda, mc):
     want = OL.hessian_apply(sdp, V, P, 50.0, 1.0)
     rel = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert rel <= 1e-5, rel
-    rows = np.linalg.norm(got - want, axis=1) / (np.linalg.norm(want, axis=1) + 1e-30)
-    assert np.quantile(rows, 0.999) <= 1e-4
+    # every row, against the size of the terms it sums: FP32 rounding of each term
+    # rho a q W_k (q = a (P_j.W_k + P_k.W_j)) bounds the row's error by a few units of
+    # 6e-8 times rho sum_k |a| (|P_j||W_k| + |P_k||W_j|) |W_k| + gamma |P_j|
+    nP, nV = np.linalg.norm(P, axis=1), np.linalg.norm(V, axis=1)
+    A = sdp.At_matrix(np.ones(sdp.m))
+    absA = abs(A)
+    scale = 50.0 * (nP * (absA @ (nV * nV)) + nV * (absA @ (nP * nV))) + 1.0 * nP
+    err = np.linalg.norm(got - want, axis=1)
+    assert np.all(err <= 1e-5 * scale), np.max(err / scale)
     prob.close()
 
 
 def test_mc_full_size_solve_recovers_M(cuda, mc):
     prob = L.Problem(mc)
     res = prob.solve(precision=L.LORADS_PREC_MIXED, switch_tol=1e-3, h=2.5, time_limit_s=240.0)
-    assert res["status"] in (0, L.LORADS_ERR_MAXITER), L.lorads_status_string(res["status"])
+    assert res["status"] == 0, L.lorads_status_string(res["status"])
     want = 2.0 * nuclear_norm_rank5(mc.mc_P, mc.mc_Q)
-    assert abs(res["objective"] - want) <= 1e-5 * want, (res["objective"], want)
-    assert res["r_P"] <= 1e-5
+    assert abs(res["objective"] - want) <= 1e-6 * want, (res["objective"], want)
+    assert res["r_P"] <= 1e-6 and res["r_D"] <= 1e-6 and abs(res["gap"]) <= 1e-6
     sol = prob.solution()
     prob.close()
     Uh = sol["U_hat"]

@@ -254,3 +254,32 @@ def test_general_path_scopes_agree(cuda, prec):
     assert abs(one["cg_iters"] - two["cg_iters"]) <= 3
     tol = 1e-9 if prec == L.LORADS_PREC_FP64 else 1e-6
     assert abs(one["objective"] - two["objective"]) <= tol * abs(two["objective"])
+
+
+@pytest.fixture(scope="module")
+def mc500_oracle():
+    inst = I.matrix_completion(500, 500, 3, 20000, seed=7)
+    sdp = SDP.from_instance(inst)
+    return inst, sdp, solve(sdp, Params())
+
+
+@pytest.mark.parametrize("prec", [L.LORADS_PREC_FP64, L.LORADS_PREC_MIXED])
+def test_matrix_completion_against_oracle(cuda, mc500_oracle, prec):
+    """Matrix completion (Section 5.4's SDP, n1 = n2 = 500, rank-3 M, 20,000 samples; off-diagonal
+    constraints, so Phase III continues Phase I's augmented Lagrangian method) against the
+    oracle's solve of the same instance: both pass the final test, both reach 2 ||M||_* (exact
+    recovery), and the objectives agree to 1e-6."""
+    inst, sdp, ref = mc500_oracle
+    res, sol = gpu_solve(inst, precision=prec)
+    want = 2.0 * np.linalg.svd(inst.mc_P @ inst.mc_Q.T, compute_uv=False).sum()
+    assert ref["converged"] and res["status"] == 0, L.lorads_status_string(res["status"])
+    assert res["polished"] == 2 and ref["polished"]
+    assert res["r_P"] <= 1e-6 and res["r_D"] <= 1e-6 and abs(res["gap"]) <= 1e-6
+    assert res["dual_psd"] <= 1e-6
+    assert abs(res["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+    assert abs(res["objective"] - want) <= 1e-6 * want
+    assert abs(ref["objective"] - want) <= 1e-6 * want
+    # the oracle's evaluation of the library's output agrees with the library's report
+    from oracle.lorads import kkt_report
+    rep = kkt_report(sdp, sol["U_hat"], sol["y"])
+    assert rep["r_D"] <= 1e-6 and rep["r_P"] <= 1e-6
