@@ -216,12 +216,12 @@ def oracle_sample(workload, seconds, counts):
 def algorithmic_bytes(res, n, s):
     """Algorithmic bytes of one solve's Hessian applies, 3 n ld s per apply (read P and the fixed
     factor W, write H P; ld = 4 ceil(r / 4), s the element size): Phase II's applies (CG
-    iterations and warm-start residuals, in the form's element type, at the initial rank's ld)
-    plus Phase III's Newton-CG applies (FP64, at the final rank's ld)."""
+    iterations and warm-start residuals, at the initial rank's ld) plus Phase III's Newton-CG
+    applies (at the final rank's ld), both in the form's element type."""
     r0 = res.get("rank0", res["rank"])
     ld0 = (r0 + 3) // 4 * 4
     ld1 = (res["rank"] + 3) // 4 * 4
-    return res["hessian_applies"] * 3 * n * ld0 * s + res["newton_cg_iters"] * 3 * n * ld1 * 8
+    return res["hessian_applies"] * 3 * n * ld0 * s + res["newton_cg_iters"] * 3 * n * ld1 * s
 
 
 def run_gpu(args):

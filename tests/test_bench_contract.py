@@ -59,11 +59,11 @@ def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
 
 def test_algorithmic_bytes_formula():
     # 3 n ld s per Hessian apply (P and the fixed factor read, H P written): Phase II's applies
-    # at the initial rank's ld in the form's element size, Phase III's Newton-CG applies in FP64
-    # at the final rank's ld
+    # at the initial rank's ld, Phase III's Newton-CG applies at the final rank's ld, both in the
+    # form's element size
     n = 1000
     res = {"hessian_applies": 14, "newton_cg_iters": 5, "rank": 23, "rank0": 15}
     got = bench.algorithmic_bytes(res, n, 4)
-    assert got == 14 * 3 * n * 16 * 4 + 5 * 3 * n * 24 * 8
+    assert got == 14 * 3 * n * 16 * 4 + 5 * 3 * n * 24 * 4
     none = {"hessian_applies": 0, "newton_cg_iters": 0, "rank": 15, "rank0": 15}
     assert bench.algorithmic_bytes(none, n, 8) == 0

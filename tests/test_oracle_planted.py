@@ -2,7 +2,9 @@
 through monkeypatch) and checks that the pin that guards that step then fails, while it
 passes on the oracle as written.  Mistakes: a dropped symmetric term in A(U V^T), a dropped
 gamma term in the Hessian, a instead of a^2 in the row-block solve, the sign of lambda in the
-subproblem right-hand side, and y = +lambda in the output."""
+subproblem right-hand side, y = +lambda in the output, and in Phase III the dropped curvature
+term of the Riemannian Hessian and the sign of the sphere multiplier."""
+import dataclasses
 import math
 
 import numpy as np
@@ -112,3 +114,45 @@ def test_dual_sign_in_output(monkeypatch):
     # the report built from the wrong sign no longer closes the gap at the K_n optimum
     assert abs(bad["gap"]) > 1e-3 and abs(good["gap"]) <= 1e-6
     assert math.isclose(bad["objective"], good["objective"], rel_tol=1e-9)
+
+
+def _hessian_fd_error(sdp, seed):
+    """|second derivative of f(R(U + tZ)) - <Z, Hess Z>| at a random point of the spheres."""
+    rng = np.random.default_rng(seed)
+    rad, con, a = L.sphere_structure(sdp)
+    U = L.retract(rng.standard_normal((sdp.n, 3)), rad)
+    _, mu, _ = L.manifold_multiplier(sdp, U, con, a)
+    Z = L.tangent_project(U, rng.standard_normal(U.shape))
+    h = 1e-4
+    f = lambda W: sdp.C_inner(W, W)
+    fd2 = (f(L.retract(U + h * Z, rad)) - 2 * f(U) + f(L.retract(U - h * Z, rad))) / (h * h)
+    return abs(fd2 - float(np.vdot(Z, L.riemannian_hessian(sdp, U, mu, Z)))) / (1 + abs(fd2))
+
+
+def test_dropped_curvature_term_in_riemannian_hessian(monkeypatch):
+    sdp = SDP.from_instance(I.maxcut_er(14, 4.0, seed=3))
+    assert _hessian_fd_error(sdp, 2) <= 1e-5
+    monkeypatch.setattr(L, "riemannian_hessian",
+                        lambda sdp, U, mu, Z: 2.0 * L.tangent_project(U, sdp.C_times(Z)))
+    assert _hessian_fd_error(sdp, 2) > 1e-2
+
+
+def test_multiplier_sign_in_phase3(monkeypatch):
+    """K_8 from a random start: the trust-region Newton method reaches n^2/4 with y = -(n/4) 1;
+    a multiplier of the wrong sign makes the gradient 2(CU + mu U), which is not tangent, and
+    the method no longer reaches the optimum."""
+    n = 8
+    sdp = SDP.from_instance(I.maxcut_complete(n))
+    p = L.resolve_auto(sdp, Params(tol=1e-9))
+    U0 = np.random.default_rng(4).standard_normal((n, 3))
+    good = L.bm_newton_polish(sdp, U0, p)
+    assert good["converged"] and abs(-sdp.C_inner(good["U"], good["U"]) - n * n / 4) <= 1e-9 * n * n
+    real = L.manifold_multiplier
+
+    def planted(sdp, U, con, a):
+        lam, mu, CU = real(sdp, U, con, a)
+        return -lam, -mu, CU
+
+    monkeypatch.setattr(L, "manifold_multiplier", planted)
+    bad = L.bm_newton_polish(sdp, U0, dataclasses.replace(p, newton_max=30))
+    assert not bad["converged"]
