@@ -18,6 +18,9 @@ Workload families:
   * Matrix completion (Section 5.4): X in S^{n1+n2}, constraint k fixes the entry
     (p, n1+q) of the off-diagonal block through <A_k, X> = 2 X_{p,n1+q} = 2 M_pq,
     C = I.
+  * General constraints: the Lovasz theta SDP (tr X = 1 has n entries), the minimum
+    bisection relaxation (<e e^T, X> = 0 as a rank-one term) and sensor network
+    localisation (rank-one distance constraints, Section 2.3).
 """
 from __future__ import annotations
 
@@ -206,6 +209,99 @@ def matrix_completion(n1: int, n2: int, rank: int, num_samples: int, seed: int,
         A_con=np.arange(m), A_row=p, A_col=n1 + q, A_val=np.ones(m),
         b=2.0 * Mpq, kind="mc", name=name or f"mc_{n1}x{n2}_r{rank}_m{m}_s{seed}",
         mc_P=P, mc_Q=Q, mc_n1=n1,
+    )
+
+
+# --------------------------------------------------------------------------------------
+# General constraints: multi-entry (theta), rank-one with a long vector (bisection) and
+# rank-one with short vectors (sensor network localisation, Section 2.3)
+# --------------------------------------------------------------------------------------
+def lovasz_theta(n: int, edges: np.ndarray, name: str = "") -> SDPInstance:
+    """min <-J, X> s.t. tr X = 1 (one constraint with n diagonal entries), X_ij = 0 for every
+    edge (i, j) (b = 0), X PSD: minus the Lovasz theta number of G (the SDPLIB theta family of
+    Section 5.5's general benchmarks).  C = -J is dense: every upper triplet has value -1."""
+    edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    iu, ju = np.triu_indices(n)
+    m = 1 + len(edges)
+    return SDPInstance(
+        n=n, m=m,
+        C_row=iu, C_col=ju, C_val=-np.ones(len(iu)),
+        A_con=np.concatenate([np.zeros(n, dtype=np.int64), 1 + np.arange(len(edges))]),
+        A_row=np.concatenate([np.arange(n), edges[:, 0]]),
+        A_col=np.concatenate([np.arange(n), edges[:, 1]]),
+        A_val=np.ones(n + len(edges)),
+        b=np.concatenate([[1.0], np.zeros(len(edges))]),
+        kind="general", name=name or f"theta_n{n}_e{len(edges)}", edges=edges,
+    )
+
+
+def graph_bisection(n: int, edges: np.ndarray, w: np.ndarray, name: str = "") -> SDPInstance:
+    """min <L(G, w)/4, X> s.t. X_ii = 1 and <e e^T, X> = 0 (a rank-one constraint whose vector
+    is all ones), X PSD: the minimum-bisection relaxation of the SDPLIB gpp family (Section
+    5.5)."""
+    edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    w = np.asarray(w, dtype=np.float64)
+    deg = np.zeros(n)
+    np.add.at(deg, edges[:, 0], w)
+    np.add.at(deg, edges[:, 1], w)
+    C_row = np.concatenate([np.arange(n), edges[:, 0]])
+    C_col = np.concatenate([np.arange(n), edges[:, 1]])
+    C_val = np.concatenate([deg / 4.0, -w / 4.0])
+    keep = C_val != 0.0
+    return SDPInstance(
+        n=n, m=n + 1,
+        C_row=C_row[keep], C_col=C_col[keep], C_val=C_val[keep],
+        A_con=np.arange(n), A_row=np.arange(n), A_col=np.arange(n), A_val=np.ones(n),
+        b=np.concatenate([np.ones(n), [0.0]]),
+        rank1=[(n, np.arange(n), np.ones(n), 1.0)],
+        kind="general", name=name or f"bisection_n{n}", edges=edges, weights=w,
+    )
+
+
+def sensor_network(num_sensors: int, num_anchors: int, dim: int, radius: float, seed: int,
+                   name: str = "") -> SDPInstance:
+    """The SDP relaxation of sensor network localisation in the form Section 2.3 gives with its
+    escape example: Z in S^{d+n} = [[I, X], [X^T, Y]], Z_{1:d,1:d} = I (d diagonal and
+    d(d-1)/2 zero off-diagonal constraints), <(0; e_i - e_j)(0; e_i - e_j)^T, Z> = d_ij^2 for
+    sensor pairs closer than `radius`, <(a_k; -e_j)(a_k; -e_j)^T, Z> = d_kj^2 for
+    anchor-sensor pairs closer than `radius` (rank-one constraints), C = 0.  Sensors and
+    anchors uniform in [-0.5, 0.5]^d; distances exact, so Z with X the true positions and
+    Y = X^T X is feasible.  The true positions are kept in mc_P (d x n) for checks."""
+    rng = np.random.default_rng(seed)
+    d, ns = dim, num_sensors
+    x = rng.uniform(-0.5, 0.5, size=(ns, d))
+    a = rng.uniform(-0.5, 0.5, size=(num_anchors, d))
+    A_con, A_row, A_col, A_val, b = [], [], [], [], []
+    m = 0
+    for k in range(d):
+        for l in range(k, d):
+            A_con.append(m); A_row.append(k); A_col.append(l); A_val.append(1.0)
+            b.append(1.0 if k == l else 0.0)
+            m += 1
+    rank1 = []
+    for i in range(ns):
+        for j in range(i + 1, ns):
+            dist2 = float(np.sum((x[i] - x[j]) ** 2))
+            if dist2 < radius * radius:
+                rank1.append((m, np.array([d + i, d + j]), np.array([1.0, -1.0]), 1.0))
+                b.append(dist2)
+                m += 1
+    for k in range(num_anchors):
+        for j in range(ns):
+            dist2 = float(np.sum((a[k] - x[j]) ** 2))
+            if dist2 < radius * radius:
+                idx = np.concatenate([np.arange(d), [d + j]])
+                rank1.append((m, idx, np.concatenate([a[k], [-1.0]]), 1.0))
+                b.append(dist2)
+                m += 1
+    n = d + ns
+    return SDPInstance(
+        n=n, m=m,
+        C_row=np.zeros(0), C_col=np.zeros(0), C_val=np.zeros(0),
+        A_con=np.array(A_con), A_row=np.array(A_row), A_col=np.array(A_col),
+        A_val=np.array(A_val), b=np.array(b), rank1=rank1,
+        kind="general", name=name or f"snl_n{ns}_a{num_anchors}_d{d}_s{seed}",
+        mc_P=x.T.copy(),
     )
 
 
