@@ -352,7 +352,8 @@ def run_gpu(args):
                                     "lambda_min", "admm_iters", "cg_iters", "hessian_applies",
                                     "alm_outer", "lbfgs_iters", "rank", "rank_growths", "gamma",
                                     "polished", "newton_steps", "newton_cg_iters",
-                                    "time_phase1_s", "time_phase2_s", "time_phase3_s")},
+                                    "time_phase1_s", "time_phase2_s", "time_phase3_s",
+                                    "lanczos_steps", "time_lanczos_s")},
         # the final test: max(r_P, r_D) <= 1e-6 with r_D = ||(C - A^T y) U_hat||_F/(1+||C||_F),
         # the Appendix B gap, and lambda_min(C - A^T y) >= -1e-6 (1 + ||C||_inf) (Lanczos)
         "kkt": {"tol": tol, "reached": kkt_ok(rm), "r_P": rm["r_P"], "r_D": rm["r_D"],
@@ -386,8 +387,8 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "traffic": solver_traffic(),
                      "kernel": "lorads::solve_grid_kernel<float, 0>",
-                     "unit_bytes": "3 n ld s per Hessian apply (Phase II, FP32) plus 3 n ld 8 "
-                                   "per Phase III Newton-CG apply (FP64)",
+                     "unit_bytes": "3 n ld s per Hessian apply (Phase II's eq. linU and Phase "
+                                   "III's truncated CG), s the form's element size",
                      "bytes_per_launch": bytes_mixed,
                      "l2_resident": True,
                      "working_set_bytes": 3 * inst.n * ((rm["rank"] + 3) // 4 * 4) * 8,

@@ -107,6 +107,9 @@ typedef struct lorads_params {
   int32_t max_outer;       /* ALM outer iterations (500)                                     */
   double sigma_factor;     /* ALM penalty growth when r_P fell less than 4x (2)              */
   double sigma_decrease;   /* the "4x": 0.25                                                 */
+  double sigma_max;        /* cap of the ALM penalty (paper silent): 1e4, twice rho_max; an  */
+                           /*    uncapped penalty overflows on constraints that converge      */
+                           /*    slowly (the theta SDP)                                       */
   double new_col_std;      /* std of columns added by rank growth (1e-2)                     */
   uint64_t seed;           /* SplitMix64 seed for U_0 and rank growth                        */
   int32_t precision;       /* LORADS_PREC_FP64 or LORADS_PREC_MIXED                          */
@@ -196,7 +199,8 @@ typedef struct lorads_result {
   int32_t newton_cg_iters; /* Phase III CG iterations, summed over the Newton steps          */
   int32_t refine_outer;    /* Phase III augmented-Lagrangian outer iterations                */
   int32_t refine_lbfgs_iters; /* Phase III L-BFGS iterations                                 */
-  int32_t reserved;        /* 0                                                              */
+  int32_t lanczos_steps;   /* Lanczos steps of the dual tests (both passes), over the solve  */
+  double time_lanczos_s;   /* device time of those Lanczos runs (part of the phase times)    */
 } lorads_result;
 
 typedef struct lorads_problem lorads_problem;
@@ -212,13 +216,18 @@ int lorads_set_C(lorads_problem *p, int64_t nnz, const int32_t *row, const int32
                  const double *val);
 
 /* Adds sparse terms to constraints: for t < nnz, A_{con[t]} gets val[t] at (row[t], col[t])
- * (and its mirror).  Sparse form of the A_i of eq. prob:linear-SDP. */
+ * (and its mirror).  Sparse form of the A_i of eq. prob:linear-SDP.  A constraint may carry
+ * any number of entries (one for MaxCut and matrix completion, n for tr X = 1); repeated
+ * (row, col) pairs of a constraint, in either order, are summed.  At the first solve a
+ * constraint with no non-zero entry gives LORADS_ERR_ARG. */
 int lorads_add_A_sparse(lorads_problem *p, int64_t nnz, const int32_t *con, const int32_t *row,
                         const int32_t *col, const double *val);
 
 /* Adds a rank-one term A_con += scale * a a^T with a given by nnz (idx, a) pairs (the
- * sensor-localisation constraints of Section 2.3).  Accepted and kept; the device solver
- * returns LORADS_ERR_UNSUPPORTED for problems that use it. */
+ * sensor-localisation constraints of Section 2.3); repeated indices are summed.  Assembly
+ * expands the term into its nnz (nnz + 1) / 2 symmetric entries (scale a_k a_l at (k, l)),
+ * so it suits short vectors; above 2^29 entries in all the solve returns
+ * LORADS_ERR_UNSUPPORTED. */
 int lorads_add_A_rank1(lorads_problem *p, int32_t con, int64_t nnz, const int32_t *idx,
                        const double *a, double scale);
 
@@ -427,7 +436,9 @@ int lorads_op_sddmm(lorads_problem *p, int32_t prec, int32_t r, int32_t ld, cons
 int lorads_op_spmm(lorads_problem *p, int32_t prec, int32_t r, int32_t ld, const double *w,
                    double gamma, const void *V, void *out, void *stream);
 
-/* out = rho A^T(A(P V^T)) V + gamma P (the matrix of eq. linU applied to P, never formed). */
+/* out = rho A^T(A(P V^T)) V + gamma P (the matrix of eq. linU applied to P, never formed).
+ * With multi-entry constraints A(P V^T) goes through m values of scratch owned by the
+ * problem: calls on one problem must not overlap on the device. */
 int lorads_op_hessian(lorads_problem *p, int32_t prec, int32_t r, int32_t ld, double rho,
                       double gamma, const void *V, const void *P, void *out, void *stream);
 

@@ -35,20 +35,24 @@ are the readings the CUDA library uses as well):
     start, at most cg_max_iter steps;
   * the CG for the V-step starts from U^{k+1};
   * Phase II stops when the output X = U_hat U_hat^T, y = -lambda meets the paper's own
-    termination (primal infeasibility ||A(X) - b||_2 / (1 + ||b||_inf) <= tol, the
-    SDPLR-aligned rule of Section 5.2) and, in addition, the two other error measures of
-    Appendix B: the primal-dual gap and the dual infeasibility
-    max(0, -lambda_min(C - A^T y)) / (1 + ||c||_1), each <= tol.  The tests are taken in
-    that order (each only when the previous ones hold); after a failed dual-infeasibility
-    test the next one waits max(10, k // 10) iterations.  Eq. stop's second term
-    gamma ||dV|| / (1 + ||V||) is reported, not tested;
+    termination (primal infeasibility ||A(X) - b||_2 / (1 + ||b||_inf) <= tol, Section 5.2),
+    then Appendix B's primal-dual gap, the stationarity of eq. def:eKKT
+    r_D = ||(C - A^T y) U_hat||_F / (1 + ||C||_F) and the dual measure
+    max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf), each <= tol (Appendix B divides the
+    eigenvalue by 1 + ||vec C||_1, which grows with n).  The tests are taken in that order
+    (each only when the previous ones hold); after a failed dual test the next one waits
+    max(10, k // 10) iterations.  Eq. stop's second term gamma ||dV|| / (1 + ||V||) is
+    reported, not tested.  An output that passes r_P and the gap with r_D > tol goes to
+    Phase III (not in the paper: ``bm_newton_polish`` on the product of spheres, else
+    ``alm_refine``);
   * a dual infeasibility that fell by less than 10% since the previous (failed) test means
     the rank is too small for the instance (lambda_min(C - A^T y) < 0 persists at a primal-dual
     pair that is otherwise converged): Phase II then raises the rank as Section 4.3 does
     (factor 1.5, same cap), the new columns of U and V being tau z, 0, ..., 0 with z the unit
     eigenvector of lambda_min and tau = escape_scale ||U_hat||_F / sqrt(r);
   * Phase I: sigma_0 = 1/(1+||b||_inf), sigma *= 2 when r_P fails to fall 4x in an outer
-    step, L-BFGS memory 4, inner stop at ||grad||_F/(1+||C||_F) <= min(0.1, 10 r_P), rank growth
+    step, up to sigma_max = 1e4 (twice rho_max; an uncapped sigma overflowed on the theta SDP,
+    whose primal infeasibility falls slowly), L-BFGS memory 4, inner stop at ||grad||_F/(1+||C||_F) <= min(0.1, 10 r_P), rank growth
     when an inner solve needs more than 300 iterations (switch test first).
 
 Random draws (the initial factor and the columns added by rank growth) come from a
@@ -58,6 +62,7 @@ generator independently.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 import time
 from dataclasses import dataclass, field, asdict
@@ -99,6 +104,7 @@ class Params:
     max_outer: int = 500
     sigma_factor: float = 2.0
     sigma_decrease: float = 0.25
+    sigma_max: float = 1e4          # ALM penalty cap (paper silent): twice rho_max
     new_col_std: float = 1e-2
     seed: int = 1
     phase1: bool = True           # False: caller supplies U0 / lambda0 / rho0
@@ -835,38 +841,57 @@ def lralm(sdp: SDP, U0, p: Params, trace: Optional[list] = None, lam0=None, sigm
             continue
         lam = lam + sigma * e
         if rp > p.sigma_decrease * rp_prev:
-            sigma *= p.sigma_factor
+            sigma = min(sigma * p.sigma_factor, p.sigma_max)
         rp_prev = rp
     return dict(U=U, lam=lam, sigma=sigma, outer=outer, inner=inner_total,
                 growths=growths - growth0, rp=rp, done=done)
 
 
+# Phase III outside the sphere class runs the augmented Lagrangian method in chunks of this many
+# outer iterations, with the dual test between chunks.
+REFINE_CHUNK = 25
+
+
 def alm_refine(sdp: SDP, U0, lam0, sigma0: float, p: Params, growth0: int) -> dict:
     """Phase III for problems outside the product-of-spheres class: the augmented Lagrangian
     method of Phase I continued from Phase II's output (U_hat, lambda) with Phase I's last
-    penalty sigma, until r_P <= tol and r_D <= tol, then the dual test
-    max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf) <= tol; a failed dual test grows the rank
-    along the eigenvector of lambda_min (as in Phase II) and the method goes on."""
+    penalty sigma, until r_P <= tol and r_D <= tol and the dual measure
+    max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf) <= tol.  It runs in chunks of
+    REFINE_CHUNK outer iterations with the dual measure taken after each: a dual measure above
+    tol after a chunk that converged, or after one that did not but left the measure less than
+    10% below the previous chunk's, means the rank is too small, and the escape of Phase II
+    (tau z along the eigenvector of lambda_min, into a zero column or a grown rank) follows.
+    At most max_outer outer iterations in all."""
     cap = rank_cap(sdp.m, sdp.n, p)
     U, lam, sigma = U0.copy(), np.asarray(lam0, dtype=np.float64).copy(), float(sigma0)
     outer = inner = growths = 0
     converged = False
-    while True:
-        ph = lralm(sdp, U, p, lam0=lam, sigma0=sigma, refine=True, growth0=growth0 + growths)
+    prev = None
+    while outer < p.max_outer:
+        q = dataclasses.replace(p, max_outer=min(REFINE_CHUNK, p.max_outer - outer))
+        ph = lralm(sdp, U, q, lam0=lam, sigma0=sigma, refine=True, growth0=growth0 + growths)
         U, lam, sigma = ph["U"], ph["lam"], ph["sigma"]
         outer += ph["outer"]
         inner += ph["inner"]
         growths += ph["growths"]
-        if not ph["done"]:
-            break
-        if not p.kkt_dinf or dual_psd_measure(sdp, -lam) <= p.tol:
+        if not p.kkt_dinf:
+            if ph["done"]:
+                converged = True
+                break
+            continue
+        d = dual_psd_measure(sdp, -lam)
+        if ph["done"] and d <= p.tol:
             converged = True
             break
+        if d <= p.tol or (not ph["done"] and (prev is None or d < 0.9 * prev)):
+            prev = d
+            continue
         Ws, grew = escape(sdp, [U], U, -lam, p, cap) if p.escape_scale > 0 else (None, False)
         if Ws is None:
             break
         U = Ws[0]
         growths += int(grew)
+        prev = None
     return dict(U=U, lam=lam, sigma=sigma, converged=converged, outer=outer, inner=inner,
                 growths=growths)
 

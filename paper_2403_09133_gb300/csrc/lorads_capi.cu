@@ -223,39 +223,82 @@ static int assemble(lorads_problem* p, const DevAlloc& al) {
   if (!p->has_b) return LORADS_ERR_STATE;
   if (cudaSetDevice(p->device) != cudaSuccess) return check_cuda(cudaGetLastError());
   const int64_t n = p->n, m = p->m;
-  if (!p->rank1.empty()) return LORADS_ERR_UNSUPPORTED;
-  // merge duplicate (con,row,col) triplets, then require one entry per constraint
-  std::vector<int64_t> order(p->A_con.size());
-  std::iota(order.begin(), order.end(), 0);
-  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-    if (p->A_con[a] != p->A_con[b]) return p->A_con[a] < p->A_con[b];
-    if (p->A_row[a] != p->A_row[b]) return p->A_row[a] < p->A_row[b];
-    return p->A_col[a] < p->A_col[b];
+  // Constraint entries in constraint order.  A sparse triplet (r, c, a) with r != c is the
+  // symmetric entry a (E_rc + E_cr), so (r, c) and (c, r) are the same entry; a rank-one term
+  // s a a^T expands into s a_k a_l at (k, l), k <= l (a's repeated indices summed first).
+  struct ConEntry {
+    int32_t con, r, c;
+    double a;
+  };
+  std::vector<ConEntry> ce;
+  ce.reserve(p->A_con.size());
+  for (size_t t = 0; t < p->A_con.size(); ++t)
+    ce.push_back({p->A_con[t], std::min(p->A_row[t], p->A_col[t]),
+                  std::max(p->A_row[t], p->A_col[t]), p->A_val[t]});
+  const size_t kMaxEntries = (size_t)1 << 29;   // the symmetric CSR indexes 2x with int32
+  for (const auto& term : p->rank1) {
+    std::vector<std::pair<int32_t, double>> av;
+    for (size_t k = 0; k < term.idx.size(); ++k) av.push_back({term.idx[k], term.a[k]});
+    std::sort(av.begin(), av.end());
+    std::vector<std::pair<int32_t, double>> merged;
+    for (const auto& x : av) {
+      if (!merged.empty() && merged.back().first == x.first)
+        merged.back().second += x.second;
+      else
+        merged.push_back(x);
+    }
+    const size_t sz = merged.size();
+    if (ce.size() + sz * (sz + 1) / 2 > kMaxEntries) return LORADS_ERR_UNSUPPORTED;
+    for (size_t k = 0; k < sz; ++k)
+      for (size_t l = k; l < sz; ++l)
+        ce.push_back({term.con, merged[k].first, merged[l].first,
+                      term.scale * merged[k].second * merged[l].second});
+  }
+  if (ce.size() > kMaxEntries) return LORADS_ERR_UNSUPPORTED;
+  std::sort(ce.begin(), ce.end(), [](const ConEntry& x, const ConEntry& y) {
+    if (x.con != y.con) return x.con < y.con;
+    return x.r != y.r ? x.r < y.r : x.c < y.c;
   });
-  std::vector<int32_t> con_r(m, -1), con_c(m, -1);
-  std::vector<double> con_a(m, 0.0);
-  for (size_t k = 0; k < order.size(); ++k) {
-    const int64_t t = order[k];
-    const int32_t i = p->A_con[t];
-    if (con_r[i] < 0) {
-      con_r[i] = p->A_row[t];
-      con_c[i] = p->A_col[t];
-      con_a[i] = p->A_val[t];
-    } else if (con_r[i] == p->A_row[t] && con_c[i] == p->A_col[t]) {
-      con_a[i] += p->A_val[t];
-    } else {
-      return LORADS_ERR_UNSUPPORTED;   // a constraint with several entries
+  std::vector<int32_t> con_ptr(m + 1, 0), con_r, con_c;
+  std::vector<double> con_a;
+  for (size_t k = 0; k < ce.size();) {
+    size_t l = k;
+    double v = 0.0;
+    for (; l < ce.size() && ce[l].con == ce[k].con && ce[l].r == ce[k].r && ce[l].c == ce[k].c; ++l)
+      v += ce[l].a;
+    if (v != 0.0) {
+      con_r.push_back(ce[k].r);
+      con_c.push_back(ce[k].c);
+      con_a.push_back(v);
+      con_ptr[ce[k].con + 1]++;
+    }
+    k = l;
+  }
+  bool multi = false;
+  for (int64_t i = 0; i < m; ++i) {
+    if (con_ptr[i + 1] == 0) return LORADS_ERR_ARG;   // A_i = 0
+    multi = multi || con_ptr[i + 1] > 1;
+    con_ptr[i + 1] += con_ptr[i];
+  }
+  const size_t nent = con_a.size();
+  // chunks of at most CON_CHUNK entries per constraint (multi-entry problems)
+  std::vector<int32_t> chunk_ptr(1, 0), con_chunk(m + 1, 0);
+  if (multi) {
+    for (int64_t i = 0; i < m; ++i) {
+      for (int32_t e = con_ptr[i]; e < con_ptr[i + 1]; e += CON_CHUNK)
+        chunk_ptr.push_back(std::min(e + CON_CHUNK, con_ptr[i + 1]));
+      con_chunk[i + 1] = (int32_t)chunk_ptr.size() - 1;
     }
   }
-  for (int64_t i = 0; i < m; ++i)
-    if (con_r[i] < 0 || con_a[i] == 0.0) return LORADS_ERR_UNSUPPORTED;
+  const int64_t nchunk = (int64_t)chunk_ptr.size() - 1;
   // A as symmetric CSR
   std::vector<SymEntry> ent;
-  ent.reserve(2 * m);
-  for (int64_t i = 0; i < m; ++i) {
-    ent.push_back({con_r[i], con_c[i], (int32_t)i, con_a[i]});
-    if (con_r[i] != con_c[i]) ent.push_back({con_c[i], con_r[i], (int32_t)i, con_a[i]});
-  }
+  ent.reserve(2 * nent);
+  for (int64_t i = 0; i < m; ++i)
+    for (int32_t e = con_ptr[i]; e < con_ptr[i + 1]; ++e) {
+      ent.push_back({con_r[e], con_c[e], (int32_t)i, con_a[e]});
+      if (con_r[e] != con_c[e]) ent.push_back({con_c[e], con_r[e], (int32_t)i, con_a[e]});
+    }
   std::vector<int32_t> A_rp, A_col, A_con;
   std::vector<double> A_val;
   build_sym_csr(n, ent, A_rp, A_col, A_con, A_val);
@@ -308,16 +351,18 @@ static int assemble(lorads_problem* p, const DevAlloc& al) {
   std::vector<double> row_norm(n, -1.0);
   bool dsep = true;
   for (int64_t i = 0; i < m && dsep; ++i) {
-    const double ratio = p->b[i] / con_a[i];
-    if (con_r[i] != con_c[i] || row_norm[con_r[i]] >= 0.0 || !(ratio > 0.0))
+    const int32_t e = con_ptr[i];
+    const double ratio = p->b[i] / con_a[e];
+    if (multi || con_r[e] != con_c[e] || row_norm[con_r[e]] >= 0.0 || !(ratio > 0.0))
       dsep = false;
     else
-      row_norm[con_r[i]] = std::sqrt(ratio);
+      row_norm[con_r[e]] = std::sqrt(ratio);
   }
   p->diag_separable = dsep;
   // upload
   std::vector<float> A_valf(A_val.begin(), A_val.end()), C_valf(C_val.begin(), C_val.end());
-  size_t bytes = Arena::need(m, 4) * 2 + Arena::need(m, 8) * 2 + Arena::need(n + 1, 4) * 2 +
+  size_t bytes = Arena::need(nent, 4) * 2 + Arena::need(nent, 8) + Arena::need(m + 1, 4) * 2 +
+                 Arena::need(nchunk + 1, 4) + Arena::need(m, 8) * 2 + Arena::need(n + 1, 4) * 2 +
                  Arena::need(A_col.size(), 4) * 2 + Arena::need(A_val.size(), 8) +
                  Arena::need(A_val.size(), 4) + Arena::need(C_col.size(), 4) +
                  Arena::need(C_val.size(), 8) + Arena::need(C_val.size(), 4) +
@@ -331,9 +376,13 @@ static int assemble(lorads_problem* p, const DevAlloc& al) {
   DevProblem dp{};
   dp.n = (int)n;
   dp.m = (int)m;
-  int* d_con_r = a.take<int>(m);
-  int* d_con_c = a.take<int>(m);
-  double* d_con_a = a.take<double>(m);
+  int* d_con_ptr = a.take<int>(m + 1);
+  int* d_con_r = a.take<int>(nent);
+  int* d_con_c = a.take<int>(nent);
+  double* d_con_a = a.take<double>(nent);
+  int* d_chunk_ptr = a.take<int>(nchunk + 1);
+  int* d_con_chunk = a.take<int>(m + 1);
+  double* d_op_q = a.take<double>(m);
   double* d_b = a.take<double>(m);
   int* d_A_rp = a.take<int>(n + 1);
   int* d_A_col = a.take<int>(A_col.size());
@@ -345,9 +394,12 @@ static int assemble(lorads_problem* p, const DevAlloc& al) {
   double* d_C_val = a.take<double>(C_val.size());
   float* d_C_valf = a.take<float>(C_val.size());
   double* d_row_norm = a.take<double>(n);
-  CU(up(d_con_r, con_r.data(), m * 4));
-  CU(up(d_con_c, con_c.data(), m * 4));
-  CU(up(d_con_a, con_a.data(), m * 8));
+  CU(up(d_con_ptr, con_ptr.data(), (m + 1) * 4));
+  CU(up(d_con_r, con_r.data(), nent * 4));
+  CU(up(d_con_c, con_c.data(), nent * 4));
+  CU(up(d_con_a, con_a.data(), nent * 8));
+  CU(up(d_chunk_ptr, chunk_ptr.data(), (nchunk + 1) * 4));
+  CU(up(d_con_chunk, con_chunk.data(), (m + 1) * 4));
   CU(up(d_b, p->b.data(), m * 8));
   CU(up(d_A_rp, A_rp.data(), (n + 1) * 4));
   CU(up(d_A_col, A_col.data(), A_col.size() * 4));
@@ -359,9 +411,15 @@ static int assemble(lorads_problem* p, const DevAlloc& al) {
   CU(up(d_C_val, C_val.data(), C_val.size() * 8));
   CU(up(d_C_valf, C_valf.data(), C_valf.size() * 4));
   CU(up(d_row_norm, row_norm.data(), n * 8));
+  dp.con_ptr = d_con_ptr;
   dp.con_r = d_con_r;
   dp.con_c = d_con_c;
   dp.con_a = d_con_a;
+  dp.a_multi = multi ? 1 : 0;
+  dp.nchunk = (int)nchunk;
+  dp.chunk_ptr = d_chunk_ptr;
+  dp.con_chunk = d_con_chunk;
+  dp.op_q = d_op_q;
   dp.b = d_b;
   dp.A_rp = d_A_rp;
   dp.A_col = d_A_col;
@@ -378,9 +436,9 @@ static int assemble(lorads_problem* p, const DevAlloc& al) {
   dp.C_inf = cinf;
   dp.b_one = bone;
   dp.c_one = cone;
-  bool diag_only = true;
-  for (int64_t i = 0; i < m; ++i) diag_only = diag_only && (con_r[i] == con_c[i]);
-  // row-local form needs at most one constraint per row
+  // row-local form: every constraint one diagonal entry, at most one constraint per row
+  bool diag_only = !multi;
+  for (int64_t i = 0; i < m && diag_only; ++i) diag_only = con_r[i] == con_c[i];
   std::vector<int32_t> row_con(n, -1);
   std::vector<double> row_a(n, 0.0);
   for (int64_t i = 0; i < m && diag_only; ++i) {
@@ -449,6 +507,7 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   dv.max_outer = prm->max_outer;
   dv.sigma_factor = prm->sigma_factor;
   dv.sigma_decrease = prm->sigma_decrease;
+  dv.sigma_max = prm->sigma_max;
   dv.new_col_std = prm->new_col_std;
   dv.seed = prm->seed;
   dv.phase1 = prm->phase1 ? 1 : 0;
@@ -532,7 +591,8 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   int dev_sms = 0;
   CU(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
   size_t bytes = Arena::need(NS, 8) * 8 + Arena::need(NS, sizeof(T)) * (mixed ? 7 : 5) +
-                 Arena::need(m, 8) * 2 + Arena::need(NS * ring, 8) * 2 +
+                 Arena::need(m, 8) * 2 + Arena::need(3 * (size_t)p->dp.nchunk + m, 8) +
+                 Arena::need(NS * ring, 8) * 2 +
                  Arena::need(1, sizeof(SolverArgs<T>)) + Arena::need(1, sizeof(SolveOut)) +
                  Arena::need(1, sizeof(GridCtl)) +
                  Arena::need((size_t)dev_sms * 8 * MAXRED * 3, 8) + Arena::need(4, 4) + 4096;
@@ -558,6 +618,7 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   h.Sv = a.take<T>(NS);
   h.lam = a.take<double>(m);
   h.e = a.take<double>(m);
+  h.cq = a.take<double>(3 * (size_t)p->dp.nchunk + m);
   h.grad = a.take<double>(NS);
   h.grad_old = a.take<double>(NS);
   h.dir = a.take<double>(NS);
@@ -627,6 +688,8 @@ static void to_result(const SolveOut& out, lorads_result& r) {
   r.newton_cg_iters = out.newton_cg;
   r.refine_outer = out.refine_outer;
   r.refine_lbfgs_iters = out.refine_lbfgs;
+  r.lanczos_steps = out.lanczos_steps;
+  r.time_lanczos_s = out.t_lanczos_ns * 1e-9;
 }
 
 static void record_solution(lorads_problem* p, const SolveOut& out, const lorads_result& r) {
@@ -944,6 +1007,7 @@ void lorads_default_params(lorads_params* prm) {
   prm->max_outer = 500;
   prm->sigma_factor = 2.0;
   prm->sigma_decrease = 0.25;
+  prm->sigma_max = 1e4;
   prm->new_col_std = 1e-2;
   prm->seed = 1;
   prm->precision = LORADS_PREC_FP64;
@@ -1371,6 +1435,7 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   h.Sv = a.take<T>(NS);
   h.lam = a.take<double>(m);
   h.e = a.take<double>(m);
+  h.cq = a.take<double>(3 * (size_t)p->dp.nchunk + m);
   h.grad = a.take<double>(NS);
   h.grad_old = a.take<double>(NS);
   h.dir = a.take<double>(NS);
@@ -1384,9 +1449,9 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   GridCtl* dctl = a.take<GridCtl>(1);
   double* dpartials = a.take<double>((size_t)dev_sms * 8 * MAXRED * 3);
   int* dqueue = a.take<int>(4);
-  if (!h.U || !h.V || !h.Ut || !h.Vt || !h.Dl || !h.R || !h.Pd || !h.HP || !h.Sv || !h.lam || !h.e ||
-      !h.grad || !h.grad_old || !h.dir || !h.tmp || !h.CWn || !h.S || !h.Y || !dargs || !dout ||
-      !dctl || !dpartials || !dqueue)
+  if (!h.U || !h.V || !h.Ut || !h.Vt || !h.Dl || !h.R || !h.Pd || !h.HP || !h.Sv || !h.lam ||
+      !h.e || !h.cq || !h.grad || !h.grad_old || !h.dir || !h.tmp || !h.CWn || !h.S || !h.Y ||
+      !dargs || !dout || !dctl || !dpartials || !dqueue)
     return LORADS_ERR_TOO_LARGE;
   h.out = dout;
   if (!dv.phase1) {

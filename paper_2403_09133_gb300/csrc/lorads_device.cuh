@@ -5,11 +5,15 @@
 //   * A row is processed by a "team" of G lanes (G a power of two <= 32, aligned inside a
 //     warp).  Lane l of a team owns the 4-element chunks c = l, l + G, ... (at most KMAX),
 //     loaded as 128-bit accesses (float4, or two double2 for FP64).
-//   * Every constraint of the device path is a single symmetric entry a (E_rc + E_cr) or
-//     a E_rr (MaxCut: A_i = e_i e_i^T, Section 5.3; matrix completion: Section 5.4).  The
-//     entries are kept twice: in constraint order (con_r, con_c, con_a) for the dual step,
-//     and as a symmetric CSR over rows (both triangles) that carries the constraint id, for
-//     the sparse-times-dense products.
+//   * A constraint is a list of symmetric entries a (E_rc + E_cr) or a E_rr: one entry for
+//     MaxCut (A_i = e_i e_i^T, Section 5.3) and matrix completion (Section 5.4), several for
+//     general constraints (tr X = 1) and for the rank-one terms of sensor-network localisation
+//     (Section 2.3), which assembly expands into their entries (s a a^T has s a_k a_l at (k, l)).
+//     The entries are kept twice: in constraint order (con_ptr, con_r, con_c, con_a) for the
+//     products <A_i, X Y^T>, and as a symmetric CSR over rows (both triangles) that carries the
+//     constraint id, for the sparse-times-dense products.  Constraints with several entries
+//     are also cut into chunks of at most CON_CHUNK entries (chunk_ptr; con_chunk gives each
+//     constraint's chunks) so that a long constraint is summed by many teams.
 //   * Reductions are deterministic: fixed shuffle trees inside warps, warps summed in order,
 //     CTAs summed in order by the last CTA to arrive at the grid barrier.
 #pragma once
@@ -22,17 +26,26 @@ constexpr int KMAX = 2;      // chunks per lane
 constexpr int CHUNK = 4;     // elements per chunk (16 B of float, 32 B of double)
 constexpr int MAXRED = 12;   // values per reduction (the last slot carries the barrier status)
 constexpr int MAXMEM = 8;    // L-BFGS memory cap
+constexpr int CON_CHUNK = 32;  // entries per chunk of a multi-entry constraint
 
 // ------------------------------------------------------------------------------------
 // problem view
 // ------------------------------------------------------------------------------------
 struct DevProblem {
   int n, m;
-  // constraints in constraint order (single symmetric entry each)
+  // entries in constraint order: constraint i owns entries con_ptr[i] .. con_ptr[i+1]-1
+  const int* con_ptr;
   const int* con_r;
   const int* con_c;
   const double* con_a;
   const double* b;
+  // some constraint has several entries; then the chunks (chunk_ptr into the entries,
+  // con_chunk[i] .. con_chunk[i+1]-1 the chunks of constraint i) are set
+  int a_multi;
+  int nchunk;
+  const int* chunk_ptr;
+  const int* con_chunk;
+  double* op_q;   // m values of scratch for the operator entry points (multi-entry only)
   // A as symmetric CSR over rows; entry e of row j: column A_col[e], constraint A_con[e]
   const int* A_rp;
   const int* A_col;
@@ -558,12 +571,11 @@ __device__ __forceinline__ void spmm_row(const DevProblem& P, const T* Wm, int l
   out = acc;
 }
 
-// <A_i, U V^T> for single-entry constraint i (team-cooperative)
+// <a (E_rc + E_cr), U V^T> = a (U_r . V_c + U_c . V_r), or a U_r . V_r when r = c
+// (team-cooperative; the value in every lane)
 template <typename T>
-__device__ __forceinline__ double sddmm_con(const DevProblem& P, const T* Um, const T* Vm, int ld,
-                                            int i, const Team& t) {
-  const int r = P.con_r[i], c = P.con_c[i];
-  const double a = P.con_a[i];
+__device__ __forceinline__ double sddmm_entry(const T* Um, const T* Vm, int ld, int r, int c,
+                                              double a, const Team& t) {
   Frag<T> Ur, Vc;
   frag_load(Ur, Um, r, ld, t);
   frag_load(Vc, Vm, c, ld, t);
@@ -575,6 +587,36 @@ __device__ __forceinline__ double sddmm_con(const DevProblem& P, const T* Um, co
     loc += frag_dot_local(Uc, Vr);
   }
   return a * (double)team_sum(loc, t);
+}
+
+// <A_i, U V^T>: the sum over constraint i's entries (team-cooperative)
+template <typename T>
+__device__ __forceinline__ double sddmm_con(const DevProblem& P, const T* Um, const T* Vm, int ld,
+                                            int i, const Team& t) {
+  double s = 0.0;
+  for (int e = P.con_ptr[i]; e < P.con_ptr[i + 1]; ++e)
+    s += sddmm_entry<T>(Um, Vm, ld, P.con_r[e], P.con_c[e], P.con_a[e], t);
+  return s;
+}
+
+// Hessian row of eq. linU for multi-entry constraints, from q_i = <A_i, P W^T> computed
+// beforehand: (H P)_j = rho sum_{entries (j,k) of A_i} a q_i W_k + gamma P_j (one team)
+template <typename T>
+__device__ __forceinline__ void hessian_row_q(const DevProblem& P, const T* Wm, int ld, int j,
+                                              const Frag<T>& Pj, const double* q, T rho, T gamma,
+                                              const Team& t, Frag<T>& out) {
+  Frag<T> acc;
+  frag_zero(acc);
+  const T* av = aval<T>(P);
+  for (int e = P.A_rp[j]; e < P.A_rp[j + 1]; ++e) {
+    Frag<T> Wk;
+    frag_load(Wk, Wm, P.A_col[e], ld, t);
+    frag_axpy(acc, av[e] * (T)q[P.A_con[e]], Wk);
+  }
+#pragma unroll
+  for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+    for (int ee = 0; ee < CHUNK; ++ee) out.v[kk][ee] = fma(rho, acc.v[kk][ee], gamma * Pj.v[kk][ee]);
 }
 
 // ------------------------------------------------------------------------------------
@@ -718,6 +760,27 @@ __device__ void spmm_row_warp(const DevProblem& P, const T* Wm, int ld, int j, c
     frag_axpy(acc, gamma, Wj);
   }
   out = acc;
+}
+
+// hessian_row_q with the whole warp (entries split across sub-teams); out in every lane
+template <typename T>
+__device__ void hessian_row_q_warp(const DevProblem& P, const T* Wm, int ld, int j,
+                                   const Frag<T>& Pj, const double* q, T rho, T gamma,
+                                   const WarpRow& w, Frag<T>& out) {
+  const Team& t = w.st;
+  Frag<T> acc;
+  frag_zero(acc);
+  const T* av = aval<T>(P);
+  for (int e = P.A_rp[j] + w.sub; e < P.A_rp[j + 1]; e += w.S) {
+    Frag<T> Wk;
+    frag_load(Wk, Wm, P.A_col[e], ld, t);
+    frag_axpy(acc, av[e] * (T)q[P.A_con[e]], Wk);
+  }
+  frag_warp_combine(acc, t.G);
+#pragma unroll
+  for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+    for (int ee = 0; ee < CHUNK; ++ee) out.v[kk][ee] = fma(rho, acc.v[kk][ee], gamma * Pj.v[kk][ee]);
 }
 
 }  // namespace lorads

@@ -120,6 +120,20 @@ __global__ void op_hessian_kernel(DevProblem P, int ld, T rho, T gamma, const T*
   }
 }
 
+// Hessian of eq. linU for multi-entry constraints from q_i = <A_i, P V^T> (op_sddmm_kernel)
+template <typename T>
+__global__ void op_hessian_q_kernel(DevProblem P, int ld, T rho, T gamma, const T* V,
+                                    const T* Pm, const double* q, T* out) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  const WarpRow wr = make_warp_row(ld, tid, nt);
+  for (int j = wr.warp; j < P.n; j += wr.nwarps) {
+    Frag<T> Pj, H;
+    frag_load(Pj, Pm, j, ld, wr.st);
+    hessian_row_q_warp<T>(P, V, ld, j, Pj, q, rho, gamma, wr, H);
+    if (wr.sub == 0) frag_store(H, out, j, ld, wr.st);
+  }
+}
+
 // host-side launchers of the solver kernels, per element type and subproblem solver
 // (defined in lorads_f64.cu / lorads_f32.cu for SUB 0 and lorads_f64_direct.cu /
 // lorads_f32_direct.cu for SUB 1, compiled in parallel)
@@ -274,7 +288,12 @@ LORADS_DECLARE_LAUNCH(float)
   cudaError_t Launch<T>::op_hessian(const DevProblem& P, int ld, double rho, double gamma,     \
                                     const T* V, const T* Pm, T* out, int grid,                 \
                                     cudaStream_t s) {                                          \
-    op_hessian_kernel<T><<<grid, 256, 0, s>>>(P, ld, (T)rho, (T)gamma, V, Pm, out);            \
+    if (P.a_multi) {                                                                           \
+      op_sddmm_kernel<T><<<grid, 256, 0, s>>>(P, ld, Pm, V, P.op_q);                           \
+      op_hessian_q_kernel<T><<<grid, 256, 0, s>>>(P, ld, (T)rho, (T)gamma, V, Pm, P.op_q, out); \
+    } else {                                                                                   \
+      op_hessian_kernel<T><<<grid, 256, 0, s>>>(P, ld, (T)rho, (T)gamma, V, Pm, out);          \
+    }                                                                                          \
     return cudaGetLastError();                                                                 \
   }
 

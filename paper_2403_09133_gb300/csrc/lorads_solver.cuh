@@ -28,7 +28,7 @@ struct DevParams {
   int lbfgs_mem, inner_max_iter;
   double inner_tol_factor, inner_tol_max;
   int max_outer;
-  double sigma_factor, sigma_decrease, new_col_std;
+  double sigma_factor, sigma_decrease, sigma_max, new_col_std;
   unsigned long long seed;
   int phase1;
   int r_start;
@@ -51,6 +51,7 @@ struct DevParams {
 };
 
 constexpr int LANCZOS_MAX = 2048;  // Lanczos steps of one lambda_min estimate, at most
+constexpr int REFINE_CHUNK = 25;   // Phase III augmented-Lagrangian outer iterations between dual tests
 
 struct SolveOut {
   int status, rank, ld, admm_iters, cg_iters, hess_applies, alm_outer, lbfgs_iters, growths;
@@ -61,7 +62,8 @@ struct SolveOut {
   double objective, dual_objective, r_P, r_P_split, r_stop, r_D, gap, rho, gamma, sigma;
   double p_infeas, d_infeas, lambda_min, dual_psd;
   long long t_phase1_ns, t_phase2_ns, t_phase3_ns;
-  int polished, newton_steps, newton_cg, refine_outer, refine_lbfgs, pad2;
+  int polished, newton_steps, newton_cg, refine_outer, refine_lbfgs, lanczos_steps;
+  long long t_lanczos_ns;
 };
 
 // status values written to SolveOut (mirror the public codes)
@@ -82,6 +84,7 @@ struct SolverArgs {
   T* Sv;          // s = H p of the single-reduction CG (row-local form)
   double* lam;    // m
   double* e;      // m
+  double* cq;     // multi-entry constraints: 3 * nchunk chunk sums, then m values q_i
   double* grad;   // n * ld_cap (Phase I)
   double* grad_old;
   double* dir;
@@ -192,6 +195,8 @@ struct Solver {
   bool alm_done;      // the augmented Lagrangian loop met its stopping rule
   int refine_outer, refine_lbfgs;
   int newton_steps, newton_cg;
+  int lz_steps;       // Lanczos steps (both passes) over the solve
+  long long lz_ns;    // device time spent in lanczos_lambda_min
   long long t_p3;     // start of Phase III (0: none)
   int nzc;            // columns nzc .. r-1 of U and V are zero (the padding of a rank growth)
 
@@ -200,7 +205,7 @@ struct Solver {
         cg_iters(0), hess(0), admm_iters(0), alm_outer(0), lbfgs_iters(0), growths(0),
         last_rs(0.0), last_lmin(NAN), lmin_at(-1), uh_norm2(0.0), rs_num(-1.0), rs_den(0.0),
         ndt(0), pdinf(NAN), last_rd2(0.0), to_polish(false), fp64_bulk(false), alm_done(false),
-        refine_outer(0), refine_lbfgs(0), newton_steps(0), newton_cg(0), t_p3(0), nzc(0) {}
+        refine_outer(0), refine_lbfgs(0), newton_steps(0), newton_cg(0), lz_steps(0), lz_ns(0), t_p3(0), nzc(0) {}
 
   __device__ void set_rank(int rr) {
     r = rr;
@@ -250,16 +255,70 @@ struct Solver {
     }
   }
 
+  // ----------------------------------------------------------------------------------
+  // Multi-entry constraints: the products <A_i, X Y^T> are sums over each constraint's
+  // entries.  One team per chunk of at most CON_CHUNK entries forms K per-entry sums
+  // f(r, c, a, s) at once (so a long constraint such as tr X = 1 is spread over many teams);
+  // after a barrier, con_total(i, k) adds constraint i's chunks in a fixed order.
+  // ----------------------------------------------------------------------------------
+  template <int K, typename F>
+  __device__ bool con_chunks(F f) {
+    const int nch = P.nchunk;
+    for (int ch = tmc.id; ch < nch; ch += tmc.count) {
+      double s[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[k] = 0.0;
+      for (int e = P.chunk_ptr[ch]; e < P.chunk_ptr[ch + 1]; ++e)
+        f(P.con_r[e], P.con_c[e], P.con_a[e], s);
+      if (tmc.lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) A.cq[(long long)k * nch + ch] = s[k];
+      }
+    }
+    return sc.sync();
+  }
+
+  __device__ double con_total(int i, int k) const {
+    const double* part = A.cq + (long long)k * P.nchunk;
+    double s = 0.0;
+    for (int ch = P.con_chunk[i]; ch < P.con_chunk[i + 1]; ++ch) s += part[ch];
+    return s;
+  }
+
+  // q_i = <A_i, X Y^T> for every constraint into A.cq + 3 nchunk, visible to the whole scope
+  template <typename E>
+  __device__ bool con_q(const E* X, const E* Y) {
+    if (!con_chunks<1>([&](int r, int c, double a, double* s) {
+          s[0] += sddmm_entry<E>(X, Y, ld, r, c, a, tmc);
+        }))
+      return false;
+    double* q = A.cq + 3LL * P.nchunk;
+    for (int i = sc.tid(); i < m; i += sc.nthreads()) q[i] = con_total(i, 0);
+    return sc.sync();
+  }
+
   // e = A(U U^T) - b (stored), returns ||e||^2
   template <typename E>
   __device__ bool eval_residual_UU_e(const E* Ub, double& e2) {
     double v[1] = {0.0};
-    for (int i = tmc.id; i < m; i += tmc.count) {
-      const double q = sddmm_con<E>(P, Ub, Ub, ld, i, tmc);
-      const double ei = q - P.b[i];
-      if (tmc.lane == 0) {
+    if (P.a_multi) {
+      if (!con_chunks<1>([&](int r, int c, double a, double* s) {
+            s[0] += sddmm_entry<E>(Ub, Ub, ld, r, c, a, tmc);
+          }))
+        return false;
+      for (int i = sc.tid(); i < m; i += sc.nthreads()) {
+        const double ei = con_total(i, 0) - P.b[i];
         A.e[i] = ei;
         v[0] += ei * ei;
+      }
+    } else {
+      for (int i = tmc.id; i < m; i += tmc.count) {
+        const double q = sddmm_con<E>(P, Ub, Ub, ld, i, tmc);
+        const double ei = q - P.b[i];
+        if (tmc.lane == 0) {
+          A.e[i] = ei;
+          v[0] += ei * ei;
+        }
       }
     }
     if (!sc.reduce(v, 1)) return false;
@@ -456,31 +515,42 @@ struct Solver {
         v[8] += c2;
       }
     }
-    for (int i = tmc.id; i < m; i += tmc.count) {
-      const int rr = P.con_r[i], cc = P.con_c[i];
-      const double aa = P.con_a[i];
-      Frag<E> Ur, Dc, Dr, Uc;
-      frag_load(Ur, Ub, rr, ld, tmc);
-      frag_load(Dc, Dt, cc, ld, tmc);
-      frag_load(Dr, Dt, rr, ld, tmc);
-      frag_load(Uc, Ub, cc, ld, tmc);
-      double e1, e2;
-      if (rr != cc) {
-        e1 = 2.0 * aa * (double)team_sum(frag_dot_local(Ur, Dc) + frag_dot_local(Uc, Dr), tmc);
-        e2 = 2.0 * aa * (double)frag_dot(Dr, Dc, tmc);
-      } else {
-        e1 = 2.0 * aa * (double)frag_dot(Ur, Dr, tmc);
-        e2 = aa * (double)frag_dot(Dr, Dr, tmc);
-      }
-      if (tmc.lane == 0) {
-        const double l = A.lam[i], e0 = A.e[i];
-        v[0] += l * e1;
-        v[1] += l * e2;
-        v[2] += e0 * e1;
-        v[3] += e0 * e2;
-        v[4] += e1 * e1;
-        v[5] += e1 * e2;
-        v[6] += e2 * e2;
+    // e1 = <A_i, U D^T + D U^T> = 2 <A_i, U D^T>, e2 = <A_i, D D^T>
+    auto accumulate = [&](int i, double e1, double e2) {
+      const double l = A.lam[i], e0 = A.e[i];
+      v[0] += l * e1;
+      v[1] += l * e2;
+      v[2] += e0 * e1;
+      v[3] += e0 * e2;
+      v[4] += e1 * e1;
+      v[5] += e1 * e2;
+      v[6] += e2 * e2;
+    };
+    if (P.a_multi) {
+      if (!con_chunks<2>([&](int r, int c, double a, double* s) {
+            s[0] += 2.0 * sddmm_entry<E>(Ub, Dt, ld, r, c, a, tmc);
+            s[1] += sddmm_entry<E>(Dt, Dt, ld, r, c, a, tmc);
+          }))
+        return false;
+      for (int i = sc.tid(); i < m; i += sc.nthreads()) accumulate(i, con_total(i, 0), con_total(i, 1));
+    } else {
+      for (int i = tmc.id; i < m; i += tmc.count) {
+        const int rr = P.con_r[i], cc = P.con_c[i];
+        const double aa = P.con_a[i];
+        Frag<E> Ur, Dc, Dr, Uc;
+        frag_load(Ur, Ub, rr, ld, tmc);
+        frag_load(Dc, Dt, cc, ld, tmc);
+        frag_load(Dr, Dt, rr, ld, tmc);
+        frag_load(Uc, Ub, cc, ld, tmc);
+        double e1, e2;
+        if (rr != cc) {
+          e1 = 2.0 * aa * (double)team_sum(frag_dot_local(Ur, Dc) + frag_dot_local(Uc, Dr), tmc);
+          e2 = 2.0 * aa * (double)frag_dot(Dr, Dc, tmc);
+        } else {
+          e1 = 2.0 * aa * (double)frag_dot(Ur, Dr, tmc);
+          e2 = aa * (double)frag_dot(Dr, Dr, tmc);
+        }
+        if (tmc.lane == 0) accumulate(i, e1, e2);
       }
     }
     if (!sc.reduce(v, 9)) return false;
@@ -576,7 +646,7 @@ struct Solver {
   // ----------------------------------------------------------------------------------
   // Phase I: LRALM (Section 4.1) with dynamic rank (Section 4.3)
   // ----------------------------------------------------------------------------------
-  __device__ bool phase1(double& sigma_out) { return alm(sigma_out, false); }
+  __device__ bool phase1(double& sigma_out) { return alm(sigma_out, false, prm.max_outer); }
 
   // The augmented Lagrangian method of Phase I.  refine = false: from U_0 (init_factor),
   // lambda = 0, sigma_0 = 1/(1+||b||_inf), until r_P <= switch_tol.  refine = true (Phase III
@@ -584,7 +654,7 @@ struct Solver {
   // the bulk products on the FP64 masters, until r_P <= tol and r_D <= tol, where r_D of the
   // multiplier-updated pair is ||grad phi|| / (2 (1 + ||C||_F)) at the end of an inner solve.
   // alm_done tells whether the stopping rule was met (else max_outer ran out).
-  __device__ bool alm(double& sigma_io, bool refine) {
+  __device__ bool alm(double& sigma_io, bool refine, int max_outer) {
     double sigma;
     if (!refine) {
       for (int i = sc.tid(); i < m; i += sc.nthreads()) A.lam[i] = 0.0;
@@ -600,7 +670,7 @@ struct Solver {
     double rp_prev = INFINITY, rp = 0.0;
     double hrho[MAXMEM + 1], hsy[MAXMEM + 1], hyy[MAXMEM + 1];
     const int ring = prm.lbfgs_mem + 1;
-    for (int outer = 1; outer <= prm.max_outer; ++outer) {
+    for (int outer = 1; outer <= max_outer; ++outer) {
       if (refine) ++refine_outer;
       else alm_outer = outer;
       int cnt = 0, head = 0;
@@ -663,7 +733,7 @@ struct Solver {
       }
       for (int i = sc.tid(); i < m; i += sc.nthreads()) A.lam[i] += sigma * A.e[i];
       if (!sc.sync()) return false;
-      if (rp > prm.sigma_decrease * rp_prev) sigma *= prm.sigma_factor;
+      if (rp > prm.sigma_decrease * rp_prev) sigma = fmin(sigma * prm.sigma_factor, prm.sigma_max);
       rp_prev = rp;
     }
     sigma_io = sigma;
@@ -682,6 +752,10 @@ struct Solver {
     // one warp per row (entries split across sub-teams): rows with many entries
     const WarpRow wr = make_warp_row(ld, sc.tid(), sc.nthreads(), prm.team_mult);
     const Team& st = wr.st;
+    // multi-entry constraints: q_i = <A_i, W W^T> for every constraint first
+    const bool multi = P.a_multi != 0;
+    const double* qv = A.cq + 3LL * P.nchunk;
+    if (multi && !con_q<double>(Wm, Wm)) return false;
     for (int j = wr.warp; j < n; j += wr.nwarps) {
       Frag<double> Wj, accR, accG;
       frag_load(Wj, Wm, j, ld, st);
@@ -692,13 +766,14 @@ struct Solver {
         const double a = P.A_val[q];
         double qi;
         Frag<double> Wk;
-        if (k == j) {
+        if (k == j)
           Wk = Wj;
-          qi = a * frag_dot(Wj, Wj, st);
-        } else {
+        else
           frag_load(Wk, Wm, k, ld, st);
-          qi = 2.0 * a * frag_dot(Wj, Wk, st);
-        }
+        if (multi)
+          qi = qv[i];
+        else
+          qi = (k == j ? 1.0 : 2.0) * a * frag_dot(Wj, Wk, st);
         const double w = rho * P.b[i] - A.lam[i];
         frag_axpy(accG, a * w, Wk);
         frag_axpy(accR, a * (w - rho * qi), Wk);
@@ -737,10 +812,14 @@ struct Solver {
     while (sqrt(rr) > target && it < prm.cg_max_iter) {
       // HP = H P, p.Hp
       double w[1] = {0.0};
+      if (multi && !con_q<T>(A.Pd, Wt)) return false;
       for (int j = wr.warp; j < n; j += wr.nwarps) {
         Frag<T> Pj, Hj;
         frag_load(Pj, A.Pd, j, ld, st);
-        hessian_row_warp<T>(P, Wt, A.Pd, ld, j, Pj, rho_t, gamma_t, wr, Hj);
+        if (multi)
+          hessian_row_q_warp<T>(P, Wt, ld, j, Pj, qv, rho_t, gamma_t, wr, Hj);
+        else
+          hessian_row_warp<T>(P, Wt, A.Pd, ld, j, Pj, rho_t, gamma_t, wr, Hj);
         if (wr.sub == 0) {
           frag_store(Hj, A.HP, j, ld, st);
           const double d = (double)team_sum(frag_dot_local(Pj, Hj), st);
@@ -840,33 +919,50 @@ struct Solver {
 
   // dual step lambda += rho (A(U V^T) - b); partial sums of ||e||^2 and of the output
   // infeasibility ||A(U_hat U_hat^T) - b||^2, U_hat = (U + V)/2
-  __device__ void dual_step(double rho, double* v) {
-    for (int i = tmc.id; i < m; i += tmc.count) {
-      const int rr = P.con_r[i], cc = P.con_c[i];
-      const double a = P.con_a[i];
-      Frag<double> Ur, Vc, Uc, Vr;
-      frag_load(Ur, A.U, rr, ld, tmc);
-      frag_load(Vc, A.V, cc, ld, tmc);
-      frag_load(Uc, A.U, cc, ld, tmc);
-      frag_load(Vr, A.V, rr, ld, tmc);
-      Frag<double> Hr = Ur, Hc = Uc;
-      frag_axpy(Hr, 1.0, Vr);
-      frag_axpy(Hc, 1.0, Vc);
-      double q, qh;
-      if (rr != cc) {
-        q = a * team_sum(frag_dot_local(Ur, Vc) + frag_dot_local(Uc, Vr), tmc);
-        qh = 0.5 * a * frag_dot(Hr, Hc, tmc);      // 2 (Hr/2).(Hc/2)
-      } else {
-        q = a * frag_dot(Ur, Vr, tmc);
-        qh = 0.25 * a * frag_dot(Hr, Hr, tmc);
-      }
-      if (tmc.lane == 0) {
-        const double e = q - P.b[i], eh = qh - P.b[i];
-        A.lam[i] += rho * e;
-        v[0] += e * e;
-        v[1] += eh * eh;
-      }
+  // entry (r, c, a) of a constraint: its terms of <A_i, U V^T> and <A_i, U_hat U_hat^T>
+  __device__ __forceinline__ void dual_entry(int rr, int cc, double a, double& q,
+                                             double& qh) const {
+    Frag<double> Ur, Vc, Uc, Vr;
+    frag_load(Ur, A.U, rr, ld, tmc);
+    frag_load(Vc, A.V, cc, ld, tmc);
+    frag_load(Uc, A.U, cc, ld, tmc);
+    frag_load(Vr, A.V, rr, ld, tmc);
+    Frag<double> Hr = Ur, Hc = Uc;
+    frag_axpy(Hr, 1.0, Vr);
+    frag_axpy(Hc, 1.0, Vc);
+    if (rr != cc) {
+      q = a * team_sum(frag_dot_local(Ur, Vc) + frag_dot_local(Uc, Vr), tmc);
+      qh = 0.5 * a * frag_dot(Hr, Hc, tmc);      // 2 (Hr/2).(Hc/2)
+    } else {
+      q = a * frag_dot(Ur, Vr, tmc);
+      qh = 0.25 * a * frag_dot(Hr, Hr, tmc);
     }
+  }
+
+  __device__ bool dual_step(double rho, double* v) {
+    auto update = [&](int i, double q, double qh) {
+      const double e = q - P.b[i], eh = qh - P.b[i];
+      A.lam[i] += rho * e;
+      v[0] += e * e;
+      v[1] += eh * eh;
+    };
+    if (P.a_multi) {
+      if (!con_chunks<2>([&](int r, int c, double a, double* s) {
+            double q, qh;
+            dual_entry(r, c, a, q, qh);
+            s[0] += q;
+            s[1] += qh;
+          }))
+        return false;
+      for (int i = sc.tid(); i < m; i += sc.nthreads()) update(i, con_total(i, 0), con_total(i, 1));
+      return true;
+    }
+    for (int i = tmc.id; i < m; i += tmc.count) {
+      double q, qh;
+      dual_entry(P.con_r[i], P.con_c[i], P.con_a[i], q, qh);
+      if (tmc.lane == 0) update(i, q, qh);
+    }
+    return true;
   }
 
   // the dual measure of the final test: max(0, -lambda_min(C - A^T y)) / (1 + ||C||_inf).
@@ -973,7 +1069,7 @@ struct Solver {
       // V-step: eq. linV with W = U^{k+1}, CG warm-started from U^{k+1}
       if (!cg_solve(A.U, A.Ut, A.V, A.Vt, rho, gamma, true, dv)) return false;
       if (status != ST_OK) break;
-      dual_step(rho, v);
+      if (!dual_step(rho, v)) return false;
       v[2] = dv[0];
       v[3] = dv[1];
       if (sc.is_leader()) v[4] = (double)(globaltimer_ns() - t_start);
@@ -1629,21 +1725,101 @@ struct Solver {
     return sc.reduce(v, 4);
   }
 
-  // Truncated CG (Steihaug-Toint) for the trust-region model min g.d + d.H d / 2, ||d|| <= delta,
-  // in T: the residual, direction and Hessian products in the CG arrays of Phase II (A.R, A.Pd,
-  // A.Sv, A.HP), d in A.Dl, the iterate's T shadow A.Ut (the mixed form runs this CG in FP32;
-  // the gradient, the model test and the retraction stay FP64).  Run as the Chronopoulos-Gear
-  // recurrence; thread 0 of every CTA carries ||p||^2, d.p and ||d||^2 by their recurrences
-  // (||p_k+1||^2 = r.r + beta^2 ||p_k||^2, d_k+1.p_k+1 = beta (d_k.p_k + alpha ||p_k||^2), since
-  // r_k+1 is orthogonal to p_k and to d_k+1), so that a direction of non-positive curvature, or a
-  // step that would leave the region, ends the CG at the boundary along it.  Returns the Hessian
-  // products in it and whether d lies on the boundary.
+  // One pass of the truncated CG for row j: with the scalars (a, b) of the step, p = r + b p,
+  // s = w + b s, d += a p, r' = r - a s (the Chronopoulos-Gear recurrence), and with want_h also
+  // w' = Hess r' and the row's shares of r'.r' and w'.r'.  Hess r' needs the neighbours' r',
+  // which the pass recomputes from their r, w and s of the previous step (the same operations
+  // as the rows' owners, so the same values): r, w and s are double-buffered (read from the
+  // *c buffers, written to the *n ones) and one barrier per CG step remains, the reduction.
+  __device__ __forceinline__ void sphere_tcg_row(int j, const T* Rc, const T* Wc, const T* Sc,
+                                                 T* Rn, T* Wn, T* Sn, T a_t, T b_t, bool have_ps,
+                                                 bool want_h, double* z) {
+    Frag<T> r, w, pd, ss, x;
+    frag_load(r, Rc, j, ld, tm);
+    frag_load(w, Wc, j, ld, tm);
+    if (have_ps) {
+      frag_load(pd, A.Pd, j, ld, tm);
+      frag_load(ss, Sc, j, ld, tm);
+      frag_load(x, A.Dl, j, ld, tm);
+    } else {
+      frag_zero(pd);
+      frag_zero(ss);
+      frag_zero(x);
+    }
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+      for (int e = 0; e < CHUNK; ++e) {
+        pd.v[k][e] = fma(b_t, pd.v[k][e], r.v[k][e]);
+        ss.v[k][e] = fma(b_t, ss.v[k][e], w.v[k][e]);
+        x.v[k][e] = fma(a_t, pd.v[k][e], x.v[k][e]);
+        r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
+      }
+    frag_store(pd, A.Pd, j, ld, tm);
+    frag_store(ss, Sn, j, ld, tm);
+    frag_store(x, A.Dl, j, ld, tm);
+    frag_store(r, Rn, j, ld, tm);
+    if (!want_h) return;
+    // (C r')_j with the neighbours' r' = r - a (w + b s) formed from the previous step's rows
+    Frag<T> acc;
+    frag_zero(acc);
+    const T* cv = cval<T>(P);
+    for (int q = P.C_rp[j]; q < P.C_rp[j + 1]; ++q) {
+      const int k = P.C_col[q];
+      const T c = cv[q];
+      if (k == j) {
+        frag_axpy(acc, c, r);
+        continue;
+      }
+      Frag<T> rk, wk, sk;
+      frag_load(rk, Rc, k, ld, tm);
+      frag_load(wk, Wc, k, ld, tm);
+      if (have_ps) frag_load(sk, Sc, k, ld, tm);
+      else frag_zero(sk);
+#pragma unroll
+      for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+        for (int e = 0; e < CHUNK; ++e) {
+          const T sv = fma(b_t, sk.v[kk][e], wk.v[kk][e]);
+          acc.v[kk][e] = fma(c, fma(-a_t, sv, rk.v[kk][e]), acc.v[kk][e]);
+        }
+    }
+    // w' = 2 P_U((C r')_j - mu_j r'_j)
+    Frag<T> Uj;
+    frag_load(Uj, A.Ut, j, ld, tm);
+    const T u2 = frag_dot(Uj, Uj, tm);
+    const T mu = (T)A.e[j];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+      for (int e = 0; e < CHUNK; ++e) acc.v[k][e] = acc.v[k][e] - mu * r.v[k][e];
+    const T cp = frag_dot(acc, Uj, tm) / u2;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+      for (int e = 0; e < CHUNK; ++e) acc.v[k][e] = T(2) * (acc.v[k][e] - cp * Uj.v[k][e]);
+    frag_store(acc, Wn, j, ld, tm);
+    const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(acc, r, tm);
+    if (tm.lane == 0) {
+      z[0] += d1;
+      z[1] += d2;
+    }
+  }
+
+  // Steihaug-Toint truncated CG (Absil, Mahony and Sepulchre 2008, Algorithm 11) for the
+  // trust-region model at U with gradient g (A.grad, ||g||^2 = g2) and radius delta, as the
+  // single-reduction Chronopoulos-Gear recurrence (the iterates of textbook CG in exact
+  // arithmetic): stops at ||r|| <= min(0.5, sqrt ||g||) ||g||, where p.Hp <= 0 (to the boundary
+  // along p) or where the next iterate would leave the region (to the boundary).  Thread 0 of
+  // each CTA evaluates the scalar recurrence, including ||d||^2, d.p and ||p||^2 for the
+  // boundary tests.  The vectors are in T (the mixed form runs this CG in FP32; the gradient,
+  // the model test and the retraction stay FP64) at the iterate's T shadow A.Ut.  d ends in
+  // A.Dl; it = CG steps (Hessian products after the first).
   __device__ bool sphere_tcg(double g2, double delta, int& it, bool& on_boundary) {
-    T* const R = A.R;
-    T* const Pp = A.Pd;
-    T* const Sv = A.Sv;
-    T* const W = A.HP;
-    T* const D = A.Dl;
+    // double-buffered r, w, s (free in Phase III: the FP64 scratch of Phase I / II viewed as T)
+    T* Rb[2] = {A.R, reinterpret_cast<T*>(A.CWn)};
+    T* Wb[2] = {A.HP, reinterpret_cast<T*>(A.grad_old)};
+    T* Sb[2] = {A.Sv, reinterpret_cast<T*>(A.dir)};
     const T* const Us = A.Ut;
     // r_0 = -g, w_0 = H r_0
     for (int j = tm.id; j < n; j += tm.count) {
@@ -1655,17 +1831,17 @@ struct Solver {
       for (int k = 0; k < KMAX; ++k)
 #pragma unroll
         for (int e = 0; e < CHUNK; ++e) r.v[k][e] = -r.v[k][e];
-      frag_store(r, R, j, ld, tm);
+      frag_store(r, Rb[0], j, ld, tm);
     }
     if (!sc.sync()) return false;
     double g3[2] = {0.0, 0.0};
     for (int j = tm.id; j < n; j += tm.count) {
       Frag<T> Uj, r, w;
       frag_load(Uj, Us, j, ld, tm);
-      frag_load(r, R, j, ld, tm);
+      frag_load(r, Rb[0], j, ld, tm);
       const T u2 = frag_dot(Uj, Uj, tm);
-      sphere_hess_row(j, R, r, Uj, u2, (T)A.e[j], w);
-      frag_store(w, W, j, ld, tm);
+      sphere_hess_row(j, Rb[0], r, Uj, u2, (T)A.e[j], w);
+      frag_store(w, Wb[0], j, ld, tm);
       const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(w, r, tm);
       if (tm.lane == 0) {
         g3[0] += d1;
@@ -1710,51 +1886,16 @@ struct Solver {
     it = 0;
     on_boundary = state == 3;
     bool wrote = false;
+    int cur = 0;
     while ((state == 0 || state == 3) && it < prm.newton_cg_max) {
-      for (int j = tm.id; j < n; j += tm.count) {
-        Frag<T> r, w, pd, ss, x;
-        frag_load(r, R, j, ld, tm);
-        frag_load(w, W, j, ld, tm);
-        if (wrote) {
-          frag_load(pd, Pp, j, ld, tm);
-          frag_load(ss, Sv, j, ld, tm);
-          frag_load(x, D, j, ld, tm);
-        } else {
-          frag_zero(pd);
-          frag_zero(ss);
-          frag_zero(x);
-        }
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-#pragma unroll
-          for (int e = 0; e < CHUNK; ++e) {
-            pd.v[k][e] = fma(b_t, pd.v[k][e], r.v[k][e]);
-            ss.v[k][e] = fma(b_t, ss.v[k][e], w.v[k][e]);
-            x.v[k][e] = fma(a_t, pd.v[k][e], x.v[k][e]);
-            r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
-          }
-        frag_store(pd, Pp, j, ld, tm);
-        frag_store(ss, Sv, j, ld, tm);
-        frag_store(x, D, j, ld, tm);
-        frag_store(r, R, j, ld, tm);
-      }
-      wrote = true;
-      if (state == 3) break;             // the boundary step: d is final
-      if (!sc.sync()) return false;
+      const bool want_h = state == 0;
       double z[2] = {0.0, 0.0};
-      for (int j = tm.id; j < n; j += tm.count) {
-        Frag<T> Uj, r, w;
-        frag_load(Uj, Us, j, ld, tm);
-        frag_load(r, R, j, ld, tm);
-        const T u2 = frag_dot(Uj, Uj, tm);
-        sphere_hess_row(j, R, r, Uj, u2, (T)A.e[j], w);
-        frag_store(w, W, j, ld, tm);
-        const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(w, r, tm);
-        if (tm.lane == 0) {
-          z[0] += d1;
-          z[1] += d2;
-        }
-      }
+      for (int j = tm.id; j < n; j += tm.count)
+        sphere_tcg_row(j, Rb[cur], Wb[cur], Sb[cur], Rb[cur ^ 1], Wb[cur ^ 1], Sb[cur ^ 1], a_t,
+                       b_t, wrote, want_h, z);
+      wrote = true;
+      cur ^= 1;
+      if (!want_h) break;                // the boundary step: d is final
       if (!sc.reduce(z, 2)) return false;
       ++it;
       if (lead) {
@@ -1804,7 +1945,7 @@ struct Solver {
       for (int j = tm.id; j < n; j += tm.count) {
         Frag<T> x;
         frag_zero(x);
-        frag_store(x, D, j, ld, tm);
+        frag_store(x, A.Dl, j, ld, tm);
       }
     }
     return sc.sync();
@@ -1983,25 +2124,42 @@ struct Solver {
 
   // Phase III outside the product-of-spheres class: the augmented Lagrangian method of Phase I
   // continued from Phase II's output (U = U_hat, lambda, sigma = Phase I's last penalty) until
-  // r_P <= tol and r_D <= tol, then the dual test; a failed dual test grows the rank along the
-  // eigenvector of lambda_min (as in Phase II) and the method goes on.  V = U at the end.
+  // r_P <= tol, r_D <= tol and the dual measure <= tol, in chunks of REFINE_CHUNK outer
+  // iterations with the dual measure taken after each.  Above tol after a chunk that
+  // converged, or after one that did not but left it less than 10% below the previous chunk's,
+  // the rank is too small: the escape (tau z into a zero column or a grown rank) follows.  At
+  // most max_outer outer iterations in all; V = U at the end.
   __device__ bool phase3_alm(double sigma) {
     t_p3 = globaltimer_ns();
     if (!form_u_hat()) return false;
     if (!copy_rows(A.tmp, A.U)) return false;
-    for (;;) {
-      if (!alm(sigma, true)) return false;
+    int outer = 0;
+    double prev = -1.0;
+    bool converged = false;
+    while (outer < prm.max_outer) {
+      const int before = refine_outer;
+      if (!alm(sigma, true, min(REFINE_CHUNK, prm.max_outer - outer))) return false;
       if (status != ST_OK) break;
-      if (!alm_done) { status = ST_MAXITER; break; }
-      if (!prm.kkt_dinf) break;
+      outer += refine_outer - before;
+      if (!prm.kkt_dinf) {
+        if (alm_done) { converged = true; break; }
+        continue;
+      }
       if (!lanczos_lambda_min(last_lmin)) return false;
       lmin_at = admm_iters;
-      if (dual_psd(last_lmin) <= prm.tol) break;
-      if (!escape_possible()) { status = ST_MAXITER; break; }
+      const double d = dual_psd(last_lmin);
+      if (alm_done && d <= prm.tol) { converged = true; break; }
+      if (d <= prm.tol || (!alm_done && (prev < 0.0 || d < 0.9 * prev))) {
+        prev = d;
+        continue;
+      }
+      if (!escape_possible()) break;
       if (!u_norm2(uh_norm2)) return false;
       if (!copy_rows(A.U, A.V)) return false;
       if (!escape_grow()) return false;
+      prev = -1.0;
     }
+    if (status == ST_OK && !converged) status = ST_MAXITER;
     return copy_rows(A.U, A.V);
   }
 
@@ -2149,8 +2307,15 @@ struct Solver {
   // chosen T_c by inverse iteration, then a second pass of the same recurrence (the stored
   // alpha / beta, the same start) accumulates z = sum_k s_k q_k into A.Y + 2 Kmax (n entries);
   // zn2 receives ||z||^2.
-  __device__ __noinline__ bool lanczos_lambda_min(double& lmin, bool want_vec = false,
-                                                  double* zn2 = nullptr) {
+  __device__ bool lanczos_lambda_min(double& lmin, bool want_vec = false,
+                                     double* zn2 = nullptr) {
+    const long long t0 = globaltimer_ns();
+    const bool ok = lanczos_run(lmin, want_vec, zn2);
+    lz_ns += globaltimer_ns() - t0;
+    return ok;
+  }
+
+  __device__ __noinline__ bool lanczos_run(double& lmin, bool want_vec, double* zn2) {
     constexpr int NC = 4;
     const int Kmax = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
     if (Kmax <= 0) {
@@ -2192,6 +2357,7 @@ struct Solver {
       len[c] = v[c] > 0.0 ? K : 0;
     }
     for (int k = 0; k < Kmax; ++k) {
+      ++lz_steps;
       // W = M q_k - beta_{k-1} q_{k-1};  alpha_k = q_k . W
       double a[NC] = {0.0, 0.0, 0.0, 0.0};
       const bool diag = P.a_diag_only != 0;
@@ -2314,6 +2480,7 @@ struct Solver {
     }
     if (!sc.sync()) return false;
     for (int k = 0; k < L; ++k) {
+      ++lz_steps;
       double a[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) a[c] = hist[c8(k, c)];
@@ -2436,14 +2603,24 @@ struct Solver {
         }
       }
     }
-    for (int i = tmc.id; i < m; i += tmc.count) {
-      const double q = sddmm_con<double>(P, A.tmp, A.tmp, ld, i, tmc);
-      const double qs = sddmm_con<double>(P, A.U, A.V, ld, i, tmc);
-      if (tmc.lane == 0) {
-        const double eh = q - P.b[i], es = qs - P.b[i];
-        v[2] += eh * eh;
-        v[3] += P.b[i] * A.lam[i];
-        v[4] += es * es;
+    auto add = [&](int i, double q, double qs) {
+      const double eh = q - P.b[i], es = qs - P.b[i];
+      v[2] += eh * eh;
+      v[3] += P.b[i] * A.lam[i];
+      v[4] += es * es;
+    };
+    if (P.a_multi) {
+      if (!con_chunks<2>([&](int r, int c, double a, double* s) {
+            s[0] += sddmm_entry<double>(A.tmp, A.tmp, ld, r, c, a, tmc);
+            s[1] += sddmm_entry<double>(A.U, A.V, ld, r, c, a, tmc);
+          }))
+        return false;
+      for (int i = sc.tid(); i < m; i += sc.nthreads()) add(i, con_total(i, 0), con_total(i, 1));
+    } else {
+      for (int i = tmc.id; i < m; i += tmc.count) {
+        const double q = sddmm_con<double>(P, A.tmp, A.tmp, ld, i, tmc);
+        const double qs = sddmm_con<double>(P, A.U, A.V, ld, i, tmc);
+        if (tmc.lane == 0) add(i, q, qs);
       }
     }
     if (!sc.reduce(v, 5)) return false;
@@ -2533,6 +2710,8 @@ struct Solver {
     o->polished = to_polish ? (polish_applies() ? 1 : 2) : 0;
     o->newton_steps = newton_steps;
     o->newton_cg = newton_cg;
+    o->lanczos_steps = lz_steps;
+    o->t_lanczos_ns = lz_ns;
     o->refine_outer = refine_outer;
     o->refine_lbfgs = refine_lbfgs;
     if (have) {

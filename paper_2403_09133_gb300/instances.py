@@ -235,12 +235,16 @@ def lovasz_theta(n: int, edges: np.ndarray, name: str = "") -> SDPInstance:
     )
 
 
-def graph_bisection(n: int, edges: np.ndarray, w: np.ndarray, name: str = "") -> SDPInstance:
-    """min <L(G, w)/4, X> s.t. X_ii = 1 and <e e^T, X> = 0 (a rank-one constraint whose vector
-    is all ones), X PSD: the minimum-bisection relaxation of the SDPLIB gpp family (Section
-    5.5)."""
+def graph_bisection(n: int, edges: np.ndarray, w: np.ndarray, name: str = "",
+                    small_side: Optional[int] = None) -> SDPInstance:
+    """min <L(G, w)/4, X> s.t. X_ii = 1 and <e e^T / n^2, X> = ((n - 2k) / n)^2 (a rank-one
+    constraint whose vector is all ones, scaled like the diagonal ones), X PSD: the relaxation
+    of the minimum cut into sides of k and n - k vertices (x in {-1, 1}^n with e^T x = n - 2k).
+    k = n/2 (the default) is the bisection of the SDPLIB gpp family (Section 5.5); there
+    <e e^T, X> = 0 leaves no strictly feasible X."""
     edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
     w = np.asarray(w, dtype=np.float64)
+    k = n // 2 if small_side is None else int(small_side)
     deg = np.zeros(n)
     np.add.at(deg, edges[:, 0], w)
     np.add.at(deg, edges[:, 1], w)
@@ -252,10 +256,31 @@ def graph_bisection(n: int, edges: np.ndarray, w: np.ndarray, name: str = "") ->
         n=n, m=n + 1,
         C_row=C_row[keep], C_col=C_col[keep], C_val=C_val[keep],
         A_con=np.arange(n), A_row=np.arange(n), A_col=np.arange(n), A_val=np.ones(n),
-        b=np.concatenate([np.ones(n), [0.0]]),
-        rank1=[(n, np.arange(n), np.ones(n), 1.0)],
-        kind="general", name=name or f"bisection_n{n}", edges=edges, weights=w,
+        b=np.concatenate([np.ones(n), [(float(n - 2 * k) / n) ** 2]]),
+        rank1=[(n, np.arange(n), np.ones(n), 1.0 / (float(n) * n))],
+        kind="general", name=name or f"partition_n{n}_k{k}", edges=edges, weights=w,
     )
+
+
+def maxcut_rank_one(n: int, avg_degree: float, count: int, support: int, seed: int,
+                    name: str = "") -> SDPInstance:
+    """The Erdos-Renyi MaxCut SDP of `maxcut_er` plus `count` rank-one constraints
+    <a_t a_t^T, X> / ||a_t||^2 = 1, a_t Gaussian on `support` random rows: X = I meets them
+    strictly inside the cone.  Rank-one constraints with long vectors (the `support` entries of
+    a_t expand into support (support + 1) / 2 matrix entries)."""
+    base = maxcut_er(n, avg_degree, seed)
+    rng = np.random.default_rng(seed + 1000)
+    rank1 = []
+    for t in range(count):
+        idx = np.sort(rng.choice(n, size=support, replace=False))
+        a = rng.standard_normal(support)
+        rank1.append((n + t, idx, a, 1.0 / float(a @ a)))
+    base.rank1 = rank1
+    base.m = n + count
+    base.b = np.concatenate([base.b, np.ones(count)])
+    base.kind = "general"
+    base.name = name or f"maxcut_r1_n{n}_q{count}_s{support}_seed{seed}"
+    return base
 
 
 def sensor_network(num_sensors: int, num_anchors: int, dim: int, radius: float, seed: int,

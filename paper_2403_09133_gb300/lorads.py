@@ -48,7 +48,8 @@ class lorads_params(ctypes.Structure):
         ("max_admm_iter", _i32), ("cg_max_iter", _i32), ("cg_rel_tol", _f64),
         ("cg_abs_floor", _f64), ("lbfgs_mem", _i32), ("inner_max_iter", _i32),
         ("inner_tol_factor", _f64), ("inner_tol_max", _f64), ("max_outer", _i32),
-        ("sigma_factor", _f64), ("sigma_decrease", _f64), ("new_col_std", _f64),
+        ("sigma_factor", _f64), ("sigma_decrease", _f64), ("sigma_max", _f64),
+        ("new_col_std", _f64),
         ("seed", _u64), ("precision", _i32), ("phase1", _i32), ("time_limit_s", _f64),
         ("threads", _i32), ("grid", _i32), ("team_mult", _i32),
         ("kkt_dinf", _i32), ("lanczos_steps", _i32), ("dinf_every", _i32),
@@ -68,7 +69,7 @@ class lorads_result(ctypes.Structure):
         ("time_phase2_s", _f64), ("p_infeas", _f64), ("d_infeas", _f64), ("lambda_min", _f64),
         ("dual_psd", _f64), ("time_phase3_s", _f64), ("polished", _i32), ("newton_steps", _i32),
         ("newton_cg_iters", _i32), ("refine_outer", _i32), ("refine_lbfgs_iters", _i32),
-        ("reserved", _i32),
+        ("lanczos_steps", _i32), ("time_lanczos_s", _f64),
     ]
 
     def as_dict(self) -> dict:

@@ -52,6 +52,7 @@ def test_default_params_match_oracle_readings(lib):
     assert p.lbfgs_mem == o.lbfgs_mem and p.inner_max_iter == o.inner_max_iter
     assert p.inner_tol_factor == o.inner_tol_factor and p.inner_tol_max == o.inner_tol_max
     assert p.sigma_factor == o.sigma_factor and p.sigma_decrease == o.sigma_decrease
+    assert p.sigma_max == o.sigma_max
     assert p.new_col_std == o.new_col_std
     assert p.max_admm_iter == o.max_admm_iter and p.max_outer == o.max_outer
     # "auto" resolves by problem class on both sides (library: < 0, oracle: None)

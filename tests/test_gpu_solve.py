@@ -114,15 +114,6 @@ def test_status_codes(cuda):
     inst = I.maxcut_er(100, 5.0, seed=1)
     res, _ = gpu_solve(inst, max_admm_iter=2)
     assert res["status"] == L.LORADS_ERR_MAXITER
-    # a constraint with two entries is outside the single-entry device path
-    bad = I.maxcut_er(20, 3.0, seed=1)
-    bad.A_con = np.concatenate([bad.A_con, [0]]).astype(np.int32)
-    bad.A_row = np.concatenate([bad.A_row, [1]]).astype(np.int32)
-    bad.A_col = np.concatenate([bad.A_col, [2]]).astype(np.int32)
-    bad.A_val = np.concatenate([bad.A_val, [1.0]])
-    p = L.Problem(bad)
-    assert p.solve()["status"] == L.LORADS_ERR_UNSUPPORTED
-    p.close()
 
 
 def test_phase2_start_from_caller(cuda):

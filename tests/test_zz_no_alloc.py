@@ -18,6 +18,8 @@ CASES = {
     # the whole GPU (cooperative launch, grid barriers and partial sums in the fixed array);
     # capped so that both paths stop at the same iteration whatever the final test does
     "torus40": (lambda: I.maxcut_torus(40, 40, seed=4), {"max_admm_iter": 600}),
+    # multi-entry constraints (tr X = 1 of the theta SDP): the chunk sums in the fixed array
+    "theta60": (lambda: I.lovasz_theta(60, I.cycle_edges(60)), {"max_admm_iter": 200}),
 }
 
 
