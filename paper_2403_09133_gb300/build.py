@@ -20,8 +20,8 @@ SOURCES = ["lorads_f64.cu", "lorads_f64_block.cu", "lorads_f32.cu", "lorads_f64_
            "lorads_f32_direct.cu", "lorads_capi.cu", "lorads_gnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
-# per-unit ptxas flags: the one-CTA FP64 solver kernel is built at ptxas -O1 (see that file)
-UNIT_FLAGS = {"lorads_f64_block.cu": ["-Xptxas", "-O1"]}
+# per-unit extra flags (none at present; see lorads_f64_block.cu)
+UNIT_FLAGS = {}
 
 
 def nvcc() -> str:

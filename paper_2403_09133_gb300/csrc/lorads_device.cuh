@@ -410,9 +410,11 @@ struct GridScope {
   // next partial while a later CTA still loads this round's, so one buffer would let the later
   // CTA add a value of the wrong round.  Two rounds suffice, since no CTA passes the next
   // barrier before every CTA has arrived there, that is, has finished reading this round.
-  // Thread 0 knows the generation in advance (the one it saw released, plus one), so the store
-  // needs no load before it; the generation load the wait needs anyway checks it, and a
-  // mismatch is reported as a failed barrier rather than summed.
+  // Thread 0 knows the generation in advance (the one it saw released, plus one), so nothing
+  // is loaded before the arrival: on the critical path are the arrival's atomic, the release's
+  // visibility to the waiters and the load of the partials.  (Loading the generation first, as
+  // a check, cost one more L2 round trip per barrier.  Per-CTA release flags that every CTA
+  // polls, with no atomic, were slower: 152 CTAs polling 152 lines.)
   __device__ bool barrier(int k) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
@@ -422,11 +424,7 @@ struct GridScope {
         parity = gen_next & 1u;
         double* mine = partials + (size_t)parity * gridDim.x * MAXRED;
         for (int i = 0; i < k; ++i) mine[blockIdx.x * MAXRED + i] = red[32 * MAXRED + i];
-        const unsigned my_gen = ld_acquire_u32(&ctl->gen);
-        if (my_gen != gen_next) {
-          atomicExch(&ctl->error, 1);
-          ok = 0;
-        }
+        const unsigned my_gen = gen_next;
         gen_next = my_gen + 1u;
         const unsigned arrived = atom_add_acq_rel_u32(&ctl->count, 1u);
         if (arrived == (unsigned)count() - 1) {

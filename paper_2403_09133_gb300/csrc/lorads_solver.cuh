@@ -197,6 +197,8 @@ struct Solver {
   int newton_steps, newton_cg;
   int lz_steps;       // Lanczos steps (both passes) over the solve
   long long lz_ns;    // device time spent in lanczos_lambda_min
+  int lz_len[4], lz_cs;  // the last first pass: recurrence lengths, column of the estimate
+  double lz_qs0[4], lz_best;
   long long t_p3;     // start of Phase III (0: none)
   int nzc;            // columns nzc .. r-1 of U and V are zero (the padding of a rank growth)
 
@@ -1011,13 +1013,14 @@ struct Solver {
   // which every step keeps at zero) takes tau z, z the Ritz vector of lambda_min, tau =
   // escape_scale ||U_hat||_F / sqrt(r) (uh_norm2 = ||U_hat||_F^2); with no zero column left the
   // rank grows to ceil(1.5 r) (at least r + 1, at most the cap) with new columns [tau z, 0, ...].
-  // The caller checks escape_possible() first.
+  // The caller checks escape_possible() first, right after the failed dual test whose Lanczos
+  // coefficients give z.
   __device__ bool escape_possible() const {
     return prm.escape_scale > 0.0 && (nzc < r || r < prm.rank_cap);
   }
   __device__ bool escape_grow() {
-    double zn2 = 0.0, lm;
-    if (!lanczos_lambda_min(lm, true, &zn2)) return false;
+    double zn2 = 0.0;
+    if (!lanczos_ritz_vector(zn2)) return false;
     const int Kmax = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
     const double* zv = A.Y + 2 * Kmax;
     if (nzc < r) {
@@ -1887,15 +1890,34 @@ struct Solver {
     on_boundary = state == 3;
     bool wrote = false;
     int cur = 0;
+    // FP64: recomputing the neighbours' r' costs two DFMAs per element and neighbour (FP64 issues
+    // at 1/64 of FP32 here), more than the barrier it saves; that form takes a second pass
+    constexpr bool fuse = sizeof(T) == 4;
     while ((state == 0 || state == 3) && it < prm.newton_cg_max) {
       const bool want_h = state == 0;
       double z[2] = {0.0, 0.0};
       for (int j = tm.id; j < n; j += tm.count)
         sphere_tcg_row(j, Rb[cur], Wb[cur], Sb[cur], Rb[cur ^ 1], Wb[cur ^ 1], Sb[cur ^ 1], a_t,
-                       b_t, wrote, want_h, z);
+                       b_t, wrote, want_h && fuse, z);
       wrote = true;
       cur ^= 1;
       if (!want_h) break;                // the boundary step: d is final
+      if (!fuse) {
+        if (!sc.sync()) return false;
+        for (int j = tm.id; j < n; j += tm.count) {
+          Frag<T> Uj, r, w;
+          frag_load(Uj, Us, j, ld, tm);
+          frag_load(r, Rb[cur], j, ld, tm);
+          const T u2 = frag_dot(Uj, Uj, tm);
+          sphere_hess_row(j, Rb[cur], r, Uj, u2, (T)A.e[j], w);
+          frag_store(w, Wb[cur], j, ld, tm);
+          const double d1 = (double)frag_dot(r, r, tm), d2 = (double)frag_dot(w, r, tm);
+          if (tm.lane == 0) {
+            z[0] += d1;
+            z[1] += d2;
+          }
+        }
+      }
       if (!sc.reduce(z, 2)) return false;
       ++it;
       if (lead) {
@@ -2307,15 +2329,22 @@ struct Solver {
   // chosen T_c by inverse iteration, then a second pass of the same recurrence (the stored
   // alpha / beta, the same start) accumulates z = sum_k s_k q_k into A.Y + 2 Kmax (n entries);
   // zn2 receives ||z||^2.
-  __device__ bool lanczos_lambda_min(double& lmin, bool want_vec = false,
-                                     double* zn2 = nullptr) {
+  __device__ bool lanczos_lambda_min(double& lmin) {
     const long long t0 = globaltimer_ns();
-    const bool ok = lanczos_run(lmin, want_vec, zn2);
+    const bool ok = lanczos_run(lmin);
     lz_ns += globaltimer_ns() - t0;
     return ok;
   }
 
-  __device__ __noinline__ bool lanczos_run(double& lmin, bool want_vec, double* zn2) {
+  // the Ritz vector of the last lanczos_lambda_min into A.Y + 2 Kmax (squared norm zn2)
+  __device__ bool lanczos_ritz_vector(double& zn2) {
+    const long long t0 = globaltimer_ns();
+    const bool ok = lanczos_vector(zn2);
+    lz_ns += globaltimer_ns() - t0;
+    return ok;
+  }
+
+  __device__ __noinline__ bool lanczos_run(double& lmin) {
     constexpr int NC = 4;
     const int Kmax = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
     if (Kmax <= 0) {
@@ -2324,7 +2353,9 @@ struct Solver {
     }
     // steps taken: Kmax, or fewer once the estimate settles (checked at 128, 256, 512, ...
     // steps: the largest Ritz value of M grows with the step count, and the recurrence stops
-    // when it rose by at most 0.05 tol (1 + ||C||_inf) over the last doubling)
+    // when it rose by at most 0.05 tol (1 + ||C||_inf) over the last doubling), or once it
+    // proves the dual test failed: a Ritz value of M never exceeds lambda_max(M), so an
+    // estimate of lambda_min(C - A^T y) that already fails the test fails it for the true value
     int K = Kmax;
     int next_check = min(128, Kmax);
     double theta_prev = -INFINITY;
@@ -2417,7 +2448,7 @@ struct Solver {
 #pragma unroll
         for (int c = 0; c < NC; ++c) lc[c] = min(len[c], k + 1);
         ritz_top(hist, lc, th, cc);
-        if (th - theta_prev <= settle) {
+        if (th - theta_prev <= settle || dual_psd(-th) > prm.tol) {
           K = k + 1;
           break;
         }
@@ -2432,7 +2463,37 @@ struct Solver {
     int cs;
     ritz_top(hist, len, best, cs);
     lmin = best > -INFINITY ? -best : NAN;
-    if (!want_vec) return true;
+    // what the Ritz vector pass needs (the coefficients stay in hist)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      lz_len[c] = len[c];
+      lz_qs0[c] = qs0[c];
+    }
+    lz_best = best;
+    lz_cs = cs;
+    return true;
+  }
+
+  // Second pass of the last first pass (same start, same recurrence with its stored
+  // coefficients): the Ritz vector of its estimate.  Callers run it right after a failed dual
+  // test, before anything else touches the Lanczos blocks or the multiplier.
+  __device__ __noinline__ bool lanczos_vector(double& zn2_out) {
+    constexpr int NC = 4;
+    const int Kmax = min(min(prm.lanczos_steps, LANCZOS_MAX), n);
+    double* hist = A.S;
+    const Team t4 = make_team(NC, sc.tid(), sc.nthreads(), 1);     // one thread per row
+    const WarpRow w4 = make_warp_row(NC, sc.tid(), sc.nthreads(), 1);
+    const uint64_t key = stream_key(prm.seed, 4000);
+    int len[NC];
+    double qs[NC], qps[NC], bp[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) len[c] = lz_len[c];
+    const double best = lz_best;
+    const int cs = lz_cs;
+    double* Qp;
+    double* Q;
+    double* W;
+    double* zn2 = &zn2_out;
     // eigenvector of T_cs for theta by two steps of inverse iteration (Thomas elimination of
     // T_cs - theta I; pivots below 1e-300 are nudged), one thread
     const int L = len[cs];
@@ -2474,7 +2535,7 @@ struct Solver {
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      qs[c] = qs0[c];
+      qs[c] = lz_qs0[c];
       qps[c] = 0.0;
       bp[c] = 0.0;
     }
@@ -2519,7 +2580,7 @@ struct Solver {
     double z2[1] = {0.0};
     for (int j = sc.tid(); j < n; j += sc.nthreads()) z2[0] += zv[j] * zv[j];
     if (!sc.reduce(z2, 1)) return false;
-    if (zn2) *zn2 = z2[0];
+    *zn2 = z2[0];
     return true;
   }
 
