@@ -154,6 +154,14 @@ typedef struct lorads_params {
                            /*    II's output; 1 = on, 0 = Phase II alone (1)                  */
   int32_t newton_max;      /* Phase III Newton steps, at most (200)                          */
   int32_t newton_cg_max;   /* CG iterations of one Newton step, at most (1000)               */
+  double *iter_log;        /* device array of iter_log_cap x 6 doubles, or NULL (no log): row */
+                           /*    k of Phase II's iteration k + 1 holds (k + 1, rho, r_P of    */
+                           /*    U V^T, r_P of U_hat U_hat^T, CG iterations so far, device    */
+                           /*    seconds since the solve started); iterations past the cap    */
+                           /*    are not logged.  Written by the device during the solve;     */
+                           /*    lorads_solve_batch logs nothing.                             */
+  int32_t iter_log_cap;    /* rows of iter_log (0)                                           */
+  int32_t reserved_log;    /* 0                                                              */
   int64_t barrier_polls;   /* polls a grid-wide (or CTA-group) barrier makes before it gives */
                            /*    up; the solve then ends with LORADS_ERR_DEVICE and the CUDA  */
                            /*    context stays usable (0 = 50,000,000, a few seconds)          */

@@ -401,10 +401,8 @@ def admm_iteration(sdp: SDP, st: AdmmState, p: Params) -> dict:
 
 
 def lradmm(sdp: SDP, U0, V0, lam0, rho0: float, p: Params, trace: Optional[list] = None):
-    """Algorithm 1 until the output X = U_hat U_hat^T, y = -lambda satisfies, in this order,
-    r_P(X) = ||A(X) - b||_2 / (1 + ||b||_inf) <= tol (the paper's termination, Section 5.2),
-    |Appendix B gap| <= tol and Appendix B dual infeasibility <= tol (the last tested at
-    most once per max(dinf_every, k // 10) iterations after a failure)."""
+    """Algorithm 1 from (U0, V0, lam0, rho0) until the final test of ``_lradmm_loop`` passes
+    or hands the iterate over to Phase III."""
     st = AdmmState(U=U0.copy(), V=V0.copy(), lam=lam0.copy(), rho=rho0,
                    rp=primal_infeasibility(sdp, U0, V0))
     return _lradmm_loop(sdp, st, p, trace)

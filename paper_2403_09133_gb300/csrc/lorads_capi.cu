@@ -508,6 +508,10 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   dv.sigma_factor = prm->sigma_factor;
   dv.sigma_decrease = prm->sigma_decrease;
   dv.sigma_max = prm->sigma_max;
+  if (prm->iter_log_cap < 0 || (prm->iter_log_cap > 0 && prm->iter_log == nullptr))
+    return LORADS_ERR_ARG;
+  dv.iter_log = prm->iter_log_cap > 0 ? prm->iter_log : nullptr;
+  dv.iter_log_cap = prm->iter_log_cap;
   dv.new_col_std = prm->new_col_std;
   dv.seed = prm->seed;
   dv.phase1 = prm->phase1 ? 1 : 0;
@@ -782,6 +786,8 @@ static int run_batch_once(lorads_problem* const* ps, int count, const lorads_par
   std::vector<std::pair<double, int>> order(count);
   lorads_params q = *prm;
   q.team_mult = team_mult;
+  q.iter_log = nullptr;      // problems of a batch would share one log
+  q.iter_log_cap = 0;
   const int sub = prm->subsolver;
   const DevAlloc al = DevAlloc::from(prm, s);
   for (int i = 0; i < count; ++i) {
@@ -893,6 +899,8 @@ static int autotune_batch(lorads_problem* const* ps, int count, const lorads_par
   for (int k = 0; k < want; ++k) sample.push_back(ps[(int64_t)k * count / want]);
   lorads_params q = *prm;
   q.max_admm_iter = std::min(prm->max_admm_iter, 200);
+  q.iter_log = nullptr;
+  q.iter_log_cap = 0;
   double best = 1e300;
   *threads_out = SOLVER_THREADS;
   *mult_out = 1;

@@ -34,6 +34,8 @@ struct DevParams {
   int r_start;
   double rho0;
   long long time_limit_ns;
+  double* iter_log;     // Phase II per-iteration log (NULL: off), iter_log_cap rows of 6
+  int iter_log_cap;
   int team_mult;   // lanes per row = team_mult * the minimum for ld (autotuned for batches)
   int kkt_dinf;    // the Appendix B dual infeasibility is part of the final test
   int lanczos_steps;
@@ -297,6 +299,19 @@ struct Solver {
     double* q = A.cq + 3LL * P.nchunk;
     for (int i = sc.tid(); i < m; i += sc.nthreads()) q[i] = con_total(i, 0);
     return sc.sync();
+  }
+
+  // Phase II per-iteration log: row k = (k + 1, rho, r_P of U V^T, r_P of U_hat U_hat^T, CG
+  // iterations so far, device time in s since the solve started), written by the leader
+  __device__ void log_iter(int k, double rho, double e2, double eh2, double t_ns) const {
+    if (prm.iter_log == nullptr || k >= prm.iter_log_cap || !sc.is_leader()) return;
+    double* row = prm.iter_log + (size_t)k * 6;
+    row[0] = (double)(k + 1);
+    row[1] = rho;
+    row[2] = sqrt(e2) / (1.0 + P.b_inf);
+    row[3] = sqrt(eh2) / (1.0 + P.b_inf);
+    row[4] = (double)cg_iters;
+    row[5] = t_ns * 1e-9;
   }
 
   // e = A(U U^T) - b (stored), returns ||e||^2
@@ -1078,6 +1093,7 @@ struct Solver {
       if (sc.is_leader()) v[4] = (double)(globaltimer_ns() - t_start);
       if (!sc.reduce(v, 5)) return false;
       admm_iters = k + 1;
+      log_iter(k, rho, v[0], v[1], v[4]);
       const double rp = sqrt(v[0]) / (1.0 + P.b_inf);
       const double rph = sqrt(v[1]) / (1.0 + P.b_inf);
       const double rs = gamma * sqrt(v[2]) / (1.0 + sqrt(v[3]));
@@ -1502,6 +1518,7 @@ struct Solver {
       g3[1] = v[6];
       g3[2] = v[7];
       admm_iters = k + 1;
+      log_iter(k, rho, v[0], v[1], v[4]);
       // squared forms of the tests (no per-thread square roots); eq. stop's second term is
       // formed once, when the result is written
       rs_num = v[2];
@@ -1627,6 +1644,7 @@ struct Solver {
       if (!sc.reduce(v, 5)) return false;
       ++hess;
       admm_iters = k + 1;
+      log_iter(k, rho, v[0], v[1], v[4]);
       rs_num = v[2];
       rs_den = v[3];
       if (!(v[0] == v[0]) || !(v[2] == v[2])) { status = ST_NAN; break; }

@@ -4,8 +4,9 @@ network against the same solves started from the Burer-Monteiro phase.
 
 What the network gains is measured, not assumed: the test prints the mean ADMM iterations
 of the three starts (BM, untrained network, trained network) and requires that training
-lowered the loss, that the trained start needs fewer iterations than the untrained one, and
-that every start reaches the same objective."""
+lowered the loss, that the trained start needs fewer iterations than the untrained one and at
+most 10 % more than the Burer-Monteiro start (at this scale it needs fewer: 653 against 703
+in the bench's own evaluation), and that every start reaches the same objective."""
 import numpy as np
 import pytest
 
@@ -40,3 +41,4 @@ def test_trained_start_against_bm_and_untrained(cuda):
     print(f"\nmean ADMM iterations to the final test at 1e-6 on {len(ok)} held-out graphs: "
           f"BM start {it_bm:.0f}, untrained network {it_un:.0f}, trained network {it_tr:.0f}")
     assert it_tr < it_un
+    assert it_tr <= 1.1 * it_bm
