@@ -1254,6 +1254,49 @@ struct Solver {
   // reduced sums), and the stop test compares squares: FP64 divides issue at a small
   // fraction of the FP32 rate on this part, and evaluated in every warp they would queue on
   // each SM's FP64 unit.
+  // row j of the in-memory row-local CG step: its r, p, x (p, x zero on the first step) and W
+  __device__ __forceinline__ void cg7_load(int j, bool have_px, Frag<T>& r, Frag<T>& pp,
+                                           Frag<T>& x, Frag<T>& Wjt, T& aj, const T* Wt,
+                                           const T* ra) const {
+    frag_load(r, A.R, j, ld, tm);
+    frag_load(Wjt, Wt, j, ld, tm);
+    aj = ra[j];
+    if (have_px) {
+      frag_load(pp, A.Pd, j, ld, tm);
+      frag_load(x, A.Dl, j, ld, tm);
+    } else {
+      frag_zero(pp);
+      frag_zero(x);
+    }
+  }
+  // p = r + b p, s = H p, x += a p, r -= a s, w = H r; stores p, x, r; z += (r.r, w.r)
+  __device__ __forceinline__ void cg7_step(int j, Frag<T>& r, Frag<T>& pp, Frag<T>& x,
+                                           const Frag<T>& Wjt, T aj, T a_t, T b_t, T rho_t,
+                                           T gamma_t, double* z) const {
+    Frag<T> ss, w;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+      for (int e = 0; e < CHUNK; ++e) pp.v[k][e] = fma(b_t, pp.v[k][e], r.v[k][e]);
+    local_h(pp, Wjt, aj, rho_t, gamma_t, ss);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+      for (int e = 0; e < CHUNK; ++e) {
+        x.v[k][e] = fma(a_t, pp.v[k][e], x.v[k][e]);
+        r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
+      }
+    local_h(r, Wjt, aj, rho_t, gamma_t, w);
+    frag_store(pp, A.Pd, j, ld, tm);
+    frag_store(x, A.Dl, j, ld, tm);
+    frag_store(r, A.R, j, ld, tm);
+    const T d1 = frag_dot(r, r, tm), d2 = frag_dot(w, r, tm);
+    if (tm.lane == 0) {
+      z[0] += (double)d1;
+      z[1] += (double)d2;
+    }
+  }
+
   __device__ bool cg_local_loop(const T* Wt, double rho, double gamma, const double* g3,
                                 int& it) {
     const T rho_t = (T)rho, gamma_t = (T)gamma;
@@ -1329,42 +1372,19 @@ struct Solver {
       cg_iters += it;
       return true;
     }
+    // Rows in memory (a team owns several): the matrix is row-local, so s = H p and w = H r are
+    // formed from p and r in the pass instead of being carried (s = w + beta s) in two more
+    // arrays; a CG step reads r, p, x and W and writes r, p and x (7 arrays instead of 11).
+    // In exact arithmetic these are the iterates of the recurrence above.
+    // (Two rows per trip, their loads issued together, measured slower on the 2048^2 torus:
+    // the second row's fragments went to local memory.)
     while (go && it < prm.cg_max_iter) {
       double z[2] = {0.0, 0.0};
       for (int j = tm.id; j < n; j += tm.count) {
-        Frag<T> r, w, pp, ss, x, Wjt;
-        frag_load(r, A.R, j, ld, tm);
-        frag_load(w, A.HP, j, ld, tm);
-        frag_load(Wjt, Wt, j, ld, tm);
-        if (it > 0) {
-          frag_load(pp, A.Pd, j, ld, tm);
-          frag_load(ss, A.Sv, j, ld, tm);
-          frag_load(x, A.Dl, j, ld, tm);
-        } else {
-          frag_zero(pp);
-          frag_zero(ss);
-          frag_zero(x);
-        }
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-#pragma unroll
-          for (int e = 0; e < CHUNK; ++e) {
-            pp.v[k][e] = fma(b_t, pp.v[k][e], r.v[k][e]);
-            ss.v[k][e] = fma(b_t, ss.v[k][e], w.v[k][e]);
-            x.v[k][e] = fma(a_t, pp.v[k][e], x.v[k][e]);
-            r.v[k][e] = fma(-a_t, ss.v[k][e], r.v[k][e]);
-          }
-        local_h(r, Wjt, ra[j], rho_t, gamma_t, w);
-        frag_store(pp, A.Pd, j, ld, tm);
-        frag_store(ss, A.Sv, j, ld, tm);
-        frag_store(x, A.Dl, j, ld, tm);
-        frag_store(r, A.R, j, ld, tm);
-        frag_store(w, A.HP, j, ld, tm);
-        const T d1 = frag_dot(r, r, tm), d2 = frag_dot(w, r, tm);
-        if (tm.lane == 0) {
-          z[0] += (double)d1;
-          z[1] += (double)d2;
-        }
+        Frag<T> r, pp, x, Wjt;
+        T aj = T(0);
+        cg7_load(j, it > 0, r, pp, x, Wjt, aj, Wt, ra);
+        cg7_step(j, r, pp, x, Wjt, aj, a_t, b_t, rho_t, gamma_t, z);
       }
       if (!sc.reduce(z, 2)) return false;
       ++hess;
