@@ -1895,9 +1895,9 @@ struct Solver {
     const double eta = fmin(0.5, sqrt(sqrt(g2)));
     const double target2 = eta * eta * g2;
     const double dl2 = delta * delta;
-    // thread 0: gam = r.r, ga = gam * alpha, pp = ||p||^2, dp = d.p, dd = ||d||^2 (of the
-    // direction / iterate the next pass forms)
-    double gam = 0.0, ga = 0.0, pp = 0.0, dp = 0.0, dd = 0.0;
+    // thread 0: gam = r.r, ga = gam * alpha, a_prev = alpha, pp = ||p||^2, dp = d.p,
+    // dd = ||d||^2 (of the direction / iterate the next pass forms)
+    double gam = 0.0, ga = 0.0, a_prev = 0.0, pp = 0.0, dp = 0.0, dd = 0.0;
     if (lead) {
       gam = g3[0];
       const double del = g3[1];
@@ -1915,6 +1915,7 @@ struct Solver {
         alpha = gam / del;
       }
       ga = gam * alpha;
+      a_prev = alpha;
       shs[0] = (double)state;
       shs[1] = alpha;
       shs[2] = 0.0;
@@ -1959,8 +1960,9 @@ struct Solver {
       if (!sc.reduce(z, 2)) return false;
       ++it;
       if (lead) {
-        // the pass just made: d += alpha p (alpha = ga / gam), so d.p and ||d||^2 move on
-        const double alpha_prev = ga / gam;
+        // the pass just made: d += alpha p (the alpha of the previous step), so d.p and ||d||^2
+        // move on
+        const double alpha_prev = a_prev;
         dd += 2.0 * alpha_prev * dp + alpha_prev * alpha_prev * pp;
         dp += alpha_prev * pp;           // d_k+1 . p_k
         const double gam_new = z[0], del_new = z[1];
@@ -1971,15 +1973,21 @@ struct Solver {
         } else if (gam_new <= target2) {
           st = 1;
         } else {
-          beta = gam_new / gam;
-          pp = gam_new + beta * beta * pp;          // ||p_k+1||^2
-          dp = beta * dp;                           // d_k+1 . p_k+1
-          const double D = del_new * ga - gam_new * gam_new;   // p.Hp = D / ga
+          // with D = del_new ga - gam_new^2 (p.Hp = D / ga), beta = gam_new / gam and
+          // alpha = gam_new ga / D both come from the one reciprocal 1 / (gam D) when D > 0
+          const double D = del_new * ga - gam_new * gam_new;
           bool to_boundary = !(D > 0.0);
           if (!to_boundary) {
-            alpha = gam_new * ga / D;
-            to_boundary = dd + 2.0 * alpha * dp + alpha * alpha * pp >= dl2;
+            const double inv = 1.0 / (gam * D);
+            beta = gam_new * D * inv;
+            alpha = gam_new * ga * gam * inv;
+          } else {
+            beta = gam_new / gam;
           }
+          pp = gam_new + beta * beta * pp;          // ||p_k+1||^2
+          dp = beta * dp;                           // d_k+1 . p_k+1
+          if (!to_boundary)
+            to_boundary = dd + 2.0 * alpha * dp + alpha * alpha * pp >= dl2;
           if (to_boundary) {
             const double qa = pp, qb = 2.0 * dp, qc = dd - dl2;
             alpha = (-qb + sqrt(fmax(qb * qb - 4.0 * qa * qc, 0.0))) / (2.0 * qa);
@@ -1987,6 +1995,7 @@ struct Solver {
           }
           ga = gam_new * alpha;
           gam = gam_new;
+          a_prev = alpha;
         }
         shs[0] = (double)st;
         shs[1] = alpha;
