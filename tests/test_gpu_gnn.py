@@ -47,8 +47,9 @@ def test_forward_matches_oracle(setup, r):
     U, y = L.lorads_gnn_forward(g, inst.n, r)
     Uo, yo, _ = G.forward(P, X0, A, r)
     np.testing.assert_allclose(np.sum(U * U, axis=1), 1.0, rtol=1e-5)
-    assert np.linalg.norm(U - Uo) <= 3e-2 * np.linalg.norm(Uo)
-    assert np.linalg.norm(y - yo) <= 3e-2 * np.linalg.norm(yo)
+    # about five BF16 roundings (2^-9 each) in sequence: measured 0.3-0.6 %
+    assert np.linalg.norm(U - Uo) <= 2e-2 * np.linalg.norm(Uo)
+    assert np.linalg.norm(y - yo) <= 2e-2 * np.linalg.norm(yo)
 
 
 def test_gradients_match_oracle(setup):
@@ -59,14 +60,17 @@ def test_gradients_match_oracle(setup):
     ys = rng.standard_normal(inst.n)
     loss, grads = L.lorads_gnn_train_step(g, r, Xs, ys, 0.0, want_grads=True)
     lo, Go, _, _ = G.loss_and_grad(P, X0, A, ei, ej, Xs, ys, r)
-    assert abs(loss - lo) <= 2e-2 * abs(lo)
+    assert abs(loss - lo) <= 2e-3 * abs(lo)           # measured <= 3e-4: the errors average out
     Gg = G.unflatten(grads)
     for name in ["theta0", "b0", "theta1", "b1", "theta2", "b2", "theta_u", "theta_y", "b_y"]:
         a, b = Gg[name], Go[name]
         if name == "theta_u":
             a, b = a[:, :r], b[:, :r]
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
-        assert rel <= 5e-2, (name, rel)
+        # the first two layers' gradients cross every BF16 layer back (~15 roundings,
+        # measured <= 2.1e-2); the rest pass through as many as the forward pass again
+        tol = 3e-2 if name in ("theta0", "b0", "theta1", "b1") else 2e-2
+        assert rel <= tol, (name, rel)
 
 
 def test_training_reduces_loss(setup):
