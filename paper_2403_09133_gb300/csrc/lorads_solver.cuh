@@ -2300,33 +2300,74 @@ struct Solver {
   }
 
   // Largest eigenvalue of each Lanczos tridiagonal T_c (alpha at hist[8k + c], beta at
-  // hist[8k + 4 + c], L[c] steps): warp c of every CTA runs a 32-point multisection on the
-  // Sturm count (identical in every CTA, so every thread ends with the same values).  best is
-  // the largest over the columns (-inf when none has a step), cs its column.
-  __device__ void ritz_top(const double* hist, const int* L, double& best, int& cs) {
+  // hist[8k + 4 + c], L[c] steps) by Sturm counts: the LDL^T pivots of T_c - x I,
+  //   d_0 = alpha_0 - x,   d_i = (alpha_i - x) - beta_{i-1}^2 / d_{i-1},
+  // have as many negative entries as T_c has eigenvalues below x.  The multisection spreads its
+  // points over the whole scope: in each round lane l of warp c in the CTA of rank q takes point
+  // g = 32 q + l of Np = 32 (CTAs in the scope) evenly spaced interior points of chain c's
+  // bracket, one reduction counts the points at or below the top eigenvalue, and the bracket
+  // shrinks to the two points around it (a factor Np + 1; the first bracket is Gershgorin's).
+  // Rounds continue until the factors reach 2^46 (4 rounds over 152 CTAs, 10 in one CTA).
+  // Every CTA takes the same sums and so the same brackets.  The pivot's reciprocal is the
+  // FP32 reciprocal refined by one Newton step in FP64, r <- r + r (1 - d r), relative error
+  // about 2^-48: the count is then that of T_c with its beta^2 perturbed by as much.  Pivots
+  // below 1e-30 in magnitude become -1e-30 (a shift of x by at most that, and inside the range
+  // of the FP32 seed).  best is the largest over the columns (-inf when none has a step), cs
+  // its column.  Called by every thread of the scope.
+  __device__ bool ritz_top(const double* hist, const int* L, double& best, int& cs) {
     constexpr int NC = 4;
-    double* theta = sc.scratch();     // NC entries
+    double* sh = sc.scratch();     // 2 NC entries: the Gershgorin brackets
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < NC) {
       const int c = warp, Lc = L[c];
-      double th = -INFINITY;
-      if (Lc > 0) {
-        double lo = INFINITY, hi = -INFINITY;
-        for (int i = lane; i < Lc; i += 32) {
-          const double ai = hist[8 * i + c];
-          const double bl = i > 0 ? fabs(hist[8 * (i - 1) + 4 + c]) : 0.0;
-          const double br = i + 1 < Lc ? fabs(hist[8 * i + 4 + c]) : 0.0;
-          lo = fmin(lo, ai - bl - br);
-          hi = fmax(hi, ai + bl + br);
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-          hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
-        }
-        for (int round = 0; round < 11; ++round) {
-          const double width = hi - lo;
-          const double x = lo + width * (double)(lane + 1) / 33.0;
-          int below = 0;      // eigenvalues of T_c below x
+      double lo = INFINITY, hi = -INFINITY;
+      for (int i = lane; i < Lc; i += 32) {
+        const double ai = hist[8 * i + c];
+        const double bl = i > 0 ? fabs(hist[8 * (i - 1) + 4 + c]) : 0.0;
+        const double br = i + 1 < Lc ? fabs(hist[8 * i + 4 + c]) : 0.0;
+        lo = fmin(lo, ai - bl - br);
+        hi = fmax(hi, ai + bl + br);
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+      }
+      if (lane == 0) {
+        sh[c] = lo;
+        sh[NC + c] = hi;
+      }
+    }
+    __syncthreads();
+    double lo[NC], hi[NC];
+    int Ls[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      lo[c] = sh[c];
+      hi[c] = sh[NC + c];
+      Ls[c] = L[c];
+    }
+    __syncthreads();
+    const int Np = 32 * (sc.nthreads() / (int)blockDim.x);
+    const double span = (double)(Np + 1);
+    int rounds = 0;
+    for (double f = 1.0; f < 70368744177664.0; f *= span) ++rounds;     // 2^46
+    const int g = 32 * (sc.tid() / (int)blockDim.x) + lane;
+    for (int round = 0; round < rounds; ++round) {
+      double v[NC] = {0.0, 0.0, 0.0, 0.0};
+      if (warp < NC) {
+        double clo = lo[0], chi = hi[0];
+        int Lc = Ls[0];
+#pragma unroll
+        for (int c = 1; c < NC; ++c)
+          if (c == warp) {
+            clo = lo[c];
+            chi = hi[c];
+            Lc = Ls[c];
+          }
+        if (Lc > 0) {
+          const double x = clo + (chi - clo) * (double)(g + 1) / span;
+          const int c = warp;
+          int below = 0;
           double d = 1.0;
           for (int i = 0; i < Lc; ++i) {
             const double ai = hist[8 * i + c];
@@ -2334,34 +2375,40 @@ struct Solver {
               d = ai - x;
             } else {
               const double bi = hist[8 * (i - 1) + 4 + c];
-              d = (ai - x) - bi * bi / d;
+              double r = (double)__frcp_rn((float)d);
+              r = fma(r, fma(-d, r, 1.0), r);
+              d = (ai - x) - (bi * bi) * r;
             }
-            if (fabs(d) < 1e-300) d = -1e-300;
+            if (fabs(d) < 1e-30) d = -1e-30;
             below += d < 0.0;
           }
-          // lanes whose x lies above every eigenvalue form a suffix; the top eigenvalue
-          // lies between the last x below it and the first x above it
-          const unsigned above = __ballot_sync(0xffffffffu, below >= Lc);
-          const int f = above ? __ffs(above) - 1 : 32;
-          const double nlo = f == 0 ? lo : lo + width * (double)f / 33.0;
-          const double nhi = f == 32 ? hi : lo + width * (double)(f + 1) / 33.0;
-          lo = nlo;
-          hi = nhi;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) v[k] = (k == warp && below < Lc) ? 1.0 : 0.0;
         }
-        th = 0.5 * (lo + hi);
       }
-      if (lane == 0) theta[c] = th;
+      if (!sc.reduce(v, NC)) return false;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (Ls[c] <= 0) continue;
+        const int F = (int)v[c];      // points at or below the top eigenvalue
+        const double w = hi[c] - lo[c];
+        const double nlo = F == 0 ? lo[c] : lo[c] + w * (double)F / span;
+        const double nhi = F >= Np ? hi[c] : lo[c] + w * (double)(F + 1) / span;
+        lo[c] = nlo;
+        hi[c] = nhi;
+      }
     }
-    __syncthreads();
     best = -INFINITY;
     cs = 0;
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (theta[c] > best) {
-        best = theta[c];
+    for (int c = 0; c < NC; ++c) {
+      const double th = Ls[c] > 0 ? 0.5 * (lo[c] + hi[c]) : -INFINITY;
+      if (th > best) {
+        best = th;
         cs = c;
       }
-    __syncthreads();
+    }
+    return true;
   }
 
   // lambda_min(C - A^T y), y = -lambda: Lanczos on M = -(C + A^T(lambda)) from four random
@@ -2494,7 +2541,7 @@ struct Solver {
         int lc[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) lc[c] = min(len[c], k + 1);
-        ritz_top(hist, lc, th, cc);
+        if (!ritz_top(hist, lc, th, cc)) return false;
         if (th - theta_prev <= settle || dual_psd(-th) > prm.tol) {
           K = k + 1;
           break;
@@ -2508,7 +2555,7 @@ struct Solver {
     if (!sc.sync()) return false;       // the coefficients written by the leader
     double best;
     int cs;
-    ritz_top(hist, len, best, cs);
+    if (!ritz_top(hist, len, best, cs)) return false;
     lmin = best > -INFINITY ? -best : NAN;
     // what the Ritz vector pass needs (the coefficients stay in hist)
 #pragma unroll
