@@ -161,7 +161,13 @@ typedef struct lorads_params {
                            /*    are not logged.  Written by the device during the solve;     */
                            /*    lorads_solve_batch logs nothing.                             */
   int32_t iter_log_cap;    /* rows of iter_log (0)                                           */
-  int32_t reserved_log;    /* 0                                                              */
+  int32_t lanczos_store_mb; /* device memory (MiB) lorads_solve may add to its state to keep  */
+                           /*    the Lanczos vectors of a dual test, (lanczos_steps + 1) x n */
+                           /*    x 32 bytes (at most 2049 x n x 32): when they fit, the      */
+                           /*    escape's eigenvector is summed from them instead of from a */
+                           /*    second pass of the recurrence (same vector up to rounding */
+                           /*    order); 0 = always the second pass; batches and           */
+                           /*    lorads_solve_static always take the second pass (2048)    */
   int64_t barrier_polls;   /* polls a grid-wide (or CTA-group) barrier makes before it gives */
                            /*    up; the solve then ends with LORADS_ERR_DEVICE and the CUDA  */
                            /*    context stays usable (0 = 50,000,000, a few seconds)          */

@@ -508,6 +508,7 @@ static int fill_params(const lorads_problem* p, const lorads_params* prm, DevPar
   dv.sigma_factor = prm->sigma_factor;
   dv.sigma_decrease = prm->sigma_decrease;
   dv.sigma_max = prm->sigma_max;
+  if (prm->lanczos_store_mb < 0) return LORADS_ERR_ARG;
   if (prm->iter_log_cap < 0 || (prm->iter_log_cap > 0 && prm->iter_log == nullptr))
     return LORADS_ERR_ARG;
   dv.iter_log = prm->iter_log_cap > 0 ? prm->iter_log : nullptr;
@@ -585,7 +586,8 @@ static int upload_start(const lorads_problem* p, double* dU, double* dV, double*
 // start if any and the argument block, and clears what must start at zero
 template <typename T>
 static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
-                         const DevAlloc& al, SolverArgs<T>& h, SolverArgs<T>** dargs_out) {
+                         const DevAlloc& al, SolverArgs<T>& h, SolverArgs<T>** dargs_out,
+                         size_t store_cap_bytes = 0) {
   const int64_t n = p->n, m = p->m;
   const int rmax = std::max(dv.rank_cap, dv.phase1 ? 0 : p->start_r);
   const long long ld_cap = round4(rmax);
@@ -600,6 +602,11 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
                  Arena::need(1, sizeof(SolverArgs<T>)) + Arena::need(1, sizeof(SolveOut)) +
                  Arena::need(1, sizeof(GridCtl)) +
                  Arena::need((size_t)dev_sms * 8 * MAXRED * 3, 8) + Arena::need(4, 4) + 4096;
+  // the Lanczos vectors of a dual test: slots 0..Kmax of n x 4 doubles, when they fit the cap
+  const int kmax = std::min(std::min(dv.lanczos_steps, LANCZOS_MAX), (int)std::min<int64_t>(n, INT32_MAX));
+  const size_t store_count = dv.kkt_dinf && kmax > 0 ? (size_t)(kmax + 1) * (size_t)n * 4 : 0;
+  const bool store = store_count > 0 && store_count * 8 <= store_cap_bytes;
+  if (store) bytes += Arena::need(store_count, 8);
   int st = p->state_mem.reserve(bytes, al);
   if (st != LORADS_OK) return st;
   Arena& a = p->state_mem;
@@ -630,6 +637,7 @@ static int prepare_state(lorads_problem* p, const DevParams& dv, cudaStream_t s,
   h.CWn = a.take<double>(NS);
   h.S = a.take<double>(NS * ring);
   h.Y = a.take<double>(NS * ring);
+  h.lz_store = store ? a.take<double>(store_count) : nullptr;
   h.ld_cap = ld_cap;
   SolverArgs<T>* dargs = a.take<SolverArgs<T>>(1);
   p->dout = a.take<SolveOut>(1);
@@ -754,7 +762,8 @@ static int run_solve(lorads_problem* p, const lorads_params* prm, cudaStream_t s
   if (st != LORADS_OK) return st;
   SolverArgs<T> h;
   SolverArgs<T>* dargs = nullptr;
-  st = prepare_state<T>(p, dv, s, DevAlloc::from(prm, s), h, &dargs);
+  st = prepare_state<T>(p, dv, s, DevAlloc::from(prm, s), h, &dargs,
+                        (size_t)prm->lanczos_store_mb << 20);
   if (st != LORADS_OK) return st;
   cudaError_t le;
   if (!whole) {
@@ -1026,6 +1035,7 @@ void lorads_default_params(lorads_params* prm) {
   prm->team_mult = 0;
   prm->kkt_dinf = 1;
   prm->lanczos_steps = 2048;
+  prm->lanczos_store_mb = 2048;
   prm->dinf_every = 10;
   prm->escape_scale = 0.3;
   prm->group = 0;
@@ -1451,6 +1461,7 @@ static int run_solve_static(lorads_problem* p, const lorads_params* prm, cudaStr
   h.CWn = a.take<double>(NS);
   h.S = a.take<double>(NS * ring);
   h.Y = a.take<double>(NS * ring);
+  h.lz_store = nullptr;              // the escape vector by the second pass: no room here
   h.ld_cap = ld_cap;
   SolverArgs<T>* dargs = a.take<SolverArgs<T>>(1);
   SolveOut* dout = a.take<SolveOut>(1);

@@ -96,6 +96,7 @@ struct SolverArgs {
   double* CWn;    // n * ld_cap: -(C W) of the row-local Phase II pipeline
   // Phase II reuses grad / grad_old / dir as the three n x 4 Lanczos blocks and S as the
   // Lanczos coefficients (8 per step; S holds ring * n * ld_cap >= 8 n doubles)
+  double* lz_store;   // null, or slots 0..Kmax of n x 4 doubles: every Lanczos block of a test
   long long ld_cap;
   SolveOut* out;
 };
@@ -2420,9 +2421,10 @@ struct Solver {
   // moves from +6e-5 (128 steps) to -3.6e-6 (2048).  Column c stops early when its beta
   // vanishes (its Krylov space is exhausted).
   // With want_vec the Ritz vector of the estimate is rebuilt too: the eigenvector s of the
-  // chosen T_c by inverse iteration, then a second pass of the same recurrence (the stored
-  // alpha / beta, the same start) accumulates z = sum_k s_k q_k into A.Y + 2 Kmax (n entries);
-  // zn2 receives ||z||^2.
+  // chosen T_c by inverse iteration, then z = sum_k s_k q_k into A.Y + 2 Kmax (n entries),
+  // from the blocks kept in A.lz_store when the state has room for them, else by a second
+  // pass of the same recurrence (the stored alpha / beta, the same start); zn2 receives
+  // ||z||^2.
   __device__ bool lanczos_lambda_min(double& lmin) {
     const long long t0 = globaltimer_ns();
     const bool ok = lanczos_run(lmin);
@@ -2457,6 +2459,12 @@ struct Solver {
     double* Qp = A.dir;     // raw q_{k-1} (true vector: qps * Qp)
     double* Q = A.grad;     // raw q_k     (true vector: qs * Q)
     double* W = A.grad_old;
+    double* const store = A.lz_store;     // raw q_k in slot k, when kept
+    const long long slot = (long long)n * NC;
+    if (store) {
+      Q = store;
+      W = store + slot;
+    }
     double* hist = A.S;     // alpha_k[c] at hist[8k + c], beta_k[c] at hist[8k + 4 + c]
     const Team t4 = make_team(NC, sc.tid(), sc.nthreads(), 1);     // one thread per row
     const WarpRow w4 = make_warp_row(NC, sc.tid(), sc.nthreads(), 1);
@@ -2533,7 +2541,7 @@ struct Solver {
       double* t = Qp;
       Qp = Q;
       Q = W;
-      W = t;
+      W = store ? store + (long long)min(k + 2, Kmax) * slot : t;
       if (k + 1 == next_check && k + 1 < Kmax) {
         if (!sc.sync()) return false;   // the coefficients written by the leader
         double th;
@@ -2615,6 +2623,21 @@ struct Solver {
         for (int i = 0; i < L; ++i) sv[i] *= nrm;
       }
     }
+    if (A.lz_store) {
+      // z_j = sum_k (s_k qs_k) Q_k[j, cs], the raw blocks of the first pass and their scales
+      // (qs_0 the start's, qs_k = 1 / beta_{k-1}), in the order the second pass adds them;
+      // the leader folds the scales into s
+      if (sc.is_leader())
+        for (int k = 0; k < L; ++k)
+          sv[k] = sv[k] * (k == 0 ? lz_qs0[cs] : 1.0 / hist[c8(k - 1, cs) + 4]);
+      if (!sc.sync()) return false;       // s, written by the leader
+      const long long slot = (long long)n * NC;
+      for (int j = sc.tid(); j < n; j += sc.nthreads()) {
+        double z = 0.0;
+        for (int k = 0; k < L; ++k) z += sv[k] * A.lz_store[k * slot + (long long)j * NC + cs];
+        zv[j] = z;
+      }
+    } else {
     // second pass: the same start and recurrence with the stored coefficients
     Qp = A.dir;
     Q = A.grad;
@@ -2670,6 +2693,7 @@ struct Solver {
       Qp = Q;
       Q = W;
       W = t;
+    }
     }
     double z2[1] = {0.0};
     for (int j = sc.tid(); j < n; j += sc.nthreads()) z2[0] += zv[j] * zv[j];

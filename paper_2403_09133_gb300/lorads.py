@@ -55,7 +55,7 @@ class lorads_params(ctypes.Structure):
         ("kkt_dinf", _i32), ("lanczos_steps", _i32), ("dinf_every", _i32),
         ("escape_scale", _f64), ("group", _i32), ("subsolver", _i32),
         ("polish", _i32), ("newton_max", _i32), ("newton_cg_max", _i32),
-        ("iter_log", ctypes.c_void_p), ("iter_log_cap", _i32), ("reserved_log", _i32),
+        ("iter_log", ctypes.c_void_p), ("iter_log_cap", _i32), ("lanczos_store_mb", _i32),
         ("barrier_polls", _i64), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 

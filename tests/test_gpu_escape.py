@@ -49,3 +49,21 @@ def test_growth_matches_oracle(cuda, prec):
     assert abs(res["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
     lmin = min_eig_dual_slack(sdp, sol["y"])
     assert max(0.0, -lmin) / (1.0 + sdp.C_rowsum_max) <= 1e-6
+
+
+@pytest.mark.parametrize("which", ["er770", "torus141"])
+def test_kept_lanczos_blocks_match_second_pass(cuda, which):
+    """The escape's eigenvector from the first pass's kept blocks (the default when the state
+    has room) against the second pass of the recurrence (lanczos_store_mb = 0): the same vector
+    up to the rounding order, so the same growths and rank, the same objective to rounding, and
+    no second-pass steps where the blocks are kept."""
+    inst = _instance() if which == "er770" else I.workload_torus141()
+    p = L.Problem(inst)
+    kept = p.solve(precision=L.LORADS_PREC_MIXED)
+    again = p.solve(precision=L.LORADS_PREC_MIXED, lanczos_store_mb=0)
+    p.close()
+    assert kept["status"] == 0 and again["status"] == 0
+    assert kept["rank"] == again["rank"] and kept["rank_growths"] == again["rank_growths"] >= 1
+    assert abs(kept["objective"] - again["objective"]) <= 1e-9 * abs(again["objective"])
+    assert kept["r_D"] <= 1e-6 and kept["dual_psd"] <= 1e-6
+    assert kept["lanczos_steps"] < again["lanczos_steps"]
