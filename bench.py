@@ -39,7 +39,7 @@ METRIC = "time-to-KKT<=1e-6 & CG-operator HBM GB/s: chosen form vs plain FP64, 1
 # (profiles/solver_traffic_torus141.md); reported only while the solver sources are unchanged.
 SOLVER_SOURCES = ["lorads_solver.cuh", "lorads_device.cuh", "lorads_kernels.cuh", "lorads_f32.cu",
                   "lorads_capi.cu"]
-SOLVER_TRAFFIC = {"sources_sha256_16": "6c7ea8f44fa5456a", "bytes_per_launch": 152.33e6}
+SOLVER_TRAFFIC = {"sources_sha256_16": "77eea9648b3d4366", "bytes_per_launch": 4144.08e6}
 
 
 def solver_traffic():
@@ -392,6 +392,10 @@ def run_gpu(args):
                      "bytes_per_launch": bytes_mixed,
                      "l2_resident": True,
                      "working_set_bytes": 3 * inst.n * ((rm["rank"] + 3) // 4 * 4) * 8,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                       "whole solve: nearly all of it the dual tests' kept "
+                                       "Lanczos blocks (written once, the failing test's read "
+                                       "back once); the iterations' working set stays in L2",
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
         "gpu_launches": args.steps,
         "clocks": clocks,
