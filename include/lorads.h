@@ -270,7 +270,11 @@ int lorads_set_start(lorads_problem *p, int32_t r, const double *U0, const doubl
  * test that did not end the solve).  With polish = 1 the first Phase II output that passes
  * r_P and the gap is handed to Phase III, which ends the solve when r_P, r_D and the dual
  * measure pass.  Otherwise the solve ends with LORADS_ERR_MAXITER after max_admm_iter Phase II
- * iterations, newton_max Newton steps or max_outer augmented-Lagrangian iterations. */
+ * iterations, newton_max Newton steps or max_outer augmented-Lagrangian iterations.
+ * The solve's state (factors, CG vectors, L-BFGS history, reduction scratch and, when they fit
+ * lanczos_store_mb, the Lanczos blocks of the dual tests) is one device allocation from the
+ * params' allocator, kept with the problem and reused by its next solve when large enough;
+ * LORADS_ERR_NOMEM when it cannot be had. */
 int lorads_solve(lorads_problem *p, const lorads_params *prm, void *stream, lorads_result *res);
 
 /* Solves count independent problems (same device) in one persistent launch: one CTA (or a
