@@ -64,6 +64,7 @@ def test_default_params_match_oracle_readings(lib):
     assert p.polish == 1 and o.polish == "auto"
     assert p.newton_max == o.newton_max and p.newton_cg_max == o.newton_cg_max
     assert p.barrier_polls == 0          # library default: about a few seconds of polling
+    assert p.lanczos_store_mb == 2048    # the dual tests' Lanczos blocks kept up to 2 GiB
 
 
 def test_status_strings(lib):
