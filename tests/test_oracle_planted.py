@@ -2,8 +2,10 @@
 through monkeypatch) and checks that the pin that guards that step then fails, while it
 passes on the oracle as written.  Mistakes: a dropped symmetric term in A(U V^T), a dropped
 gamma term in the Hessian, a instead of a^2 in the row-block solve, the sign of lambda in the
-subproblem right-hand side, y = +lambda in the output, and in Phase III the dropped curvature
-term of the Riemannian Hessian and the sign of the sphere multiplier."""
+subproblem right-hand side, y = +lambda in the output, in Phase III the dropped curvature
+term of the Riemannian Hessian and the sign of the sphere multiplier, and in Phase I a dropped
+cubic term of the exact line search's quartic, L-BFGS without its initial scaling s'y / y'y,
+and the Burer-Monteiro gradient without its factor 2."""
 import dataclasses
 import math
 
@@ -156,3 +158,103 @@ def test_multiplier_sign_in_phase3(monkeypatch):
     monkeypatch.setattr(L, "manifold_multiplier", planted)
     bad = L.bm_newton_polish(sdp, U0, dataclasses.replace(p, newton_max=30))
     assert not bad["converged"]
+
+
+def _quartic_error(sdp, rng):
+    """max over t of |phi(U + tD) - phi(U) - (a1 t + a2 t^2 + a3 t^3 + a4 t^4)| (Phase I's
+    exact line search, Algorithm 1)."""
+    U = rng.standard_normal((sdp.n, 3))
+    D = rng.standard_normal((sdp.n, 3))
+    lam = rng.standard_normal(sdp.m)
+    sigma = 1.3
+    phi0, _, e0 = L.bm_objective_and_gradient(sdp, U, lam, sigma)
+    a1, a2, a3, a4 = L.quartic_coefficients(sdp, U, D, lam, sigma, e0)
+    err = 0.0
+    for t in [-0.7, 0.1, 0.5, 2.0]:
+        phit, _, _ = L.bm_objective_and_gradient(sdp, U + t * D, lam, sigma)
+        got = a1 * t + a2 * t ** 2 + a3 * t ** 3 + a4 * t ** 4
+        err = max(err, abs(got - (phit - phi0)) / (1 + abs(phit - phi0)))
+    return err
+
+
+def test_dropped_cubic_term_in_line_search(rng, monkeypatch):
+    sdp = SDP.from_instance(random_general_sdp(n=9, m=7, nnz_per_con=3, rng=rng))
+    assert _quartic_error(sdp, np.random.default_rng(3)) <= 1e-9
+    real = L.quartic_coefficients
+
+    def planted(sdp, U, D, lam, sigma, e0):
+        a1, a2, _, a4 = real(sdp, U, D, lam, sigma, e0)
+        return a1, a2, 0.0, a4
+
+    monkeypatch.setattr(L, "quartic_coefficients", planted)
+    assert _quartic_error(sdp, np.random.default_rng(3)) > 1e-6      # the pin holds to 1e-9
+
+
+def _lbfgs_error(rng):
+    """The two-loop recursion against H_k g, H_k from the dense BFGS inverse updates of
+    H_0 = (s'y / y'y) I (Nocedal and Wright, eq. 7.19-7.20)."""
+    d = 6
+    A = rng.standard_normal((d, d))
+    A = A @ A.T + d * np.eye(d)
+    S = [rng.standard_normal((3, 2)) for _ in range(4)]
+    Y = [(A @ s.reshape(-1)).reshape(3, 2) for s in S]
+    g = rng.standard_normal((3, 2))
+    s_, y_ = S[-1].reshape(-1), Y[-1].reshape(-1)
+    H = (s_ @ y_) / (y_ @ y_) * np.eye(d)
+    for s, y in zip(S, Y):
+        s, y = s.reshape(-1), y.reshape(-1)
+        rho = 1.0 / (y @ s)
+        Vm = np.eye(d) - rho * np.outer(y, s)
+        H = Vm.T @ H @ Vm + rho * np.outer(s, s)
+    want = -(H @ g.reshape(-1)).reshape(3, 2)
+    return np.abs(L.lbfgs_direction(g, S, Y) - want).max() / np.abs(want).max()
+
+
+def test_lbfgs_without_initial_scaling(monkeypatch):
+    assert _lbfgs_error(np.random.default_rng(5)) <= 1e-10
+
+    def planted(g, S, Y):                      # H_0 = I instead of (s'y / y'y) I
+        q = g.copy()
+        alphas = []
+        for s, y in zip(reversed(S), reversed(Y)):
+            rho_i = 1.0 / float(np.vdot(y, s))
+            a = rho_i * float(np.vdot(s, q))
+            q = q - a * y
+            alphas.append((rho_i, a))
+        for (s, y), (rho_i, a) in zip(zip(S, Y), reversed(alphas)):
+            q = q + (a - rho_i * float(np.vdot(y, q))) * s
+        return -q
+
+    monkeypatch.setattr(L, "lbfgs_direction", planted)
+    assert _lbfgs_error(np.random.default_rng(5)) > 1e-2
+
+
+def _bm_gradient_error(sdp, rng):
+    """Central differences of phi against grad phi = 2 (C + A^T(lam + sigma e)) U."""
+    U = rng.standard_normal((sdp.n, 2))
+    lam = rng.standard_normal(sdp.m)
+    sigma = 0.8
+    _, g, _ = L.bm_objective_and_gradient(sdp, U, lam, sigma)
+    h = 1e-6
+    err = 0.0
+    for j in range(sdp.n):
+        for c in range(2):
+            E = np.zeros_like(U)
+            E[j, c] = h
+            fp, _, _ = L.bm_objective_and_gradient(sdp, U + E, lam, sigma)
+            fm, _, _ = L.bm_objective_and_gradient(sdp, U - E, lam, sigma)
+            err = max(err, abs((fp - fm) / (2 * h) - g[j, c]) / (1 + abs(g[j, c])))
+    return err
+
+
+def test_bm_gradient_without_factor_two(rng, monkeypatch):
+    sdp = SDP.from_instance(random_general_sdp(n=8, m=6, nnz_per_con=3, rng=rng))
+    assert _bm_gradient_error(sdp, np.random.default_rng(6)) <= 1e-5
+    real = L.bm_objective_and_gradient
+
+    def planted(sdp, U, lam, sigma):
+        phi, g, e = real(sdp, U, lam, sigma)
+        return phi, 0.5 * g, e
+
+    monkeypatch.setattr(L, "bm_objective_and_gradient", planted)
+    assert _bm_gradient_error(sdp, np.random.default_rng(6)) > 1e-2
