@@ -376,10 +376,13 @@ int lorads_set_state(lorads_problem *p, const lorads_state *st, const double *U,
  * loading a module allocates device memory, this array included) and looks up the array's
  * device address with cudaGetSymbolAddress.  The solve launches with the geometry
  * lorads_solve picks for the same parameters (grid, threads, team_mult), so the two give
- * the same iterates.  Every call shares the one array and leaves the last call's contents
- * in it; the call clears what must start at zero.  Calls that overlap on the GPU (several
- * streams or host threads at once) race on the array: serialize them.  The call blocks until
- * the solve has finished on stream. */
+ * the same iterates (an escape's eigenvector comes from the second Lanczos pass here and,
+ * within lanczos_store_mb, from the kept blocks there: the same products added in the same
+ * order).  Every call shares the one array and leaves the last call's contents in it; the
+ * call clears what must start at zero.  Calls that overlap on the GPU (several streams or
+ * host threads at once) race on the array: serialize them.  The call blocks until the solve
+ * has finished on stream and reads its report back, so it cannot be captured into a CUDA
+ * graph. */
 #define LORADS_STATIC_SCRATCH_BYTES (32ull << 20)
 int lorads_solve_static(lorads_problem *p, const lorads_params *prm, void *stream,
                         double *U_hat, int64_t ldu, double *y, lorads_result *res);
