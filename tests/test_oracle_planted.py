@@ -5,7 +5,8 @@ gamma term in the Hessian, a instead of a^2 in the row-block solve, the sign of 
 subproblem right-hand side, y = +lambda in the output, in Phase III the dropped curvature
 term of the Riemannian Hessian and the sign of the sphere multiplier, and in Phase I a dropped
 cubic term of the exact line search's quartic, L-BFGS without its initial scaling s'y / y'y,
-and the Burer-Monteiro gradient without its factor 2."""
+the Burer-Monteiro gradient without its factor 2, and a rank-one constraint s a a^T whose
+scale s is dropped from A^T(w) V."""
 import dataclasses
 import math
 
@@ -258,3 +259,26 @@ def test_bm_gradient_without_factor_two(rng, monkeypatch):
 
     monkeypatch.setattr(L, "bm_objective_and_gradient", planted)
     assert _bm_gradient_error(sdp, np.random.default_rng(6)) > 1e-2
+
+
+def _At_error(sdp, rng):
+    """A^T(w) V against sum_i w_i A_i V with each A_i written out densely (Section 1)."""
+    V = rng.standard_normal((sdp.n, 3))
+    w = rng.standard_normal(sdp.m)
+    want = sum(w[i] * (sdp.dense_A(i) @ V) for i in range(sdp.m))
+    return np.abs(sdp.At_times(w, V) - want).max() / np.abs(want).max()
+
+
+def test_rank_one_scale_dropped_in_At(monkeypatch):
+    idx = np.array([0, 3, 5])
+    sdp = SDP(7, 3, [0], [0], [1.0], [0, 2], [1, 2], [4, 6], [1.0, -0.5], np.ones(3),
+              rank1=[(1, idx, np.array([0.5, -2.0, 1.5]), 1.7)])
+    assert _At_error(sdp, np.random.default_rng(8)) <= 1e-13
+
+    def planted(self, w, V):
+        out = self.At_matrix(w) @ V
+        aV = self.R1 @ V
+        return np.asarray(out + self.R1.T @ (w[self.r1_con][:, None] * aV))
+
+    monkeypatch.setattr(S.SDP, "At_times", planted)
+    assert _At_error(sdp, np.random.default_rng(8)) > 1e-2
